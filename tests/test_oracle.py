@@ -1,0 +1,333 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test names the passage it checks.  Together they are chosen so that a
+plausible slip in the oracle (a wrong weight, a dropped equilibrium term, a
+flipped force sign, a transposed link vector, streaming the wrong way, a wrong
+relaxation factor) fails at least one of them.
+"""
+import json
+import os
+from fractions import Fraction as Q
+
+import numpy as np
+import pytest
+
+from oracle import exact, linear, oracle
+from paper_0707_2437_gb300 import workloads
+from tests.helpers import fit_damped_cos, fit_decay, harmonic_amplitudes, mode_sin_cos
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")
+
+
+def _series(f, tau, alpha, steps, every=1, field="rho", m=1):
+    """Runs the oracle and records the mode-m sine projection of a field."""
+    ts, amps = [], []
+    for t in range(0, steps + 1, every):
+        rho, ux, uy = oracle.moments(f)
+        fld = {"rho": rho - 1.0, "ux": ux, "uy": uy}[field]
+        ts.append(t)
+        amps.append(mode_sin_cos(fld, m))
+        if t < steps:
+            oracle.run(f, tau, alpha, every)
+    return np.array(ts, float), np.array(amps)
+
+
+# --- Section 2, Eq. 2-3: equilibrium and its moments -------------------------
+
+def test_equilibrium_moments_closed_form():
+    """sum fbar = rho, sum fbar e = rho u, sum fbar e e = rho/3 I + rho u u
+    (Section 2, Eq. 2 with the weights and links of Section 2)."""
+    rng = np.random.default_rng(11)
+    E = np.stack([oracle.EX, oracle.EY], axis=1).astype(float)
+    for _ in range(20):
+        rho = rng.uniform(0.5, 2.0)
+        u = rng.uniform(-0.2, 0.2, 2)
+        feq = oracle.equilibrium(rho, u[0], u[1])
+        assert abs(feq.sum() - rho) < 1e-14
+        np.testing.assert_allclose(feq @ E, rho * u, atol=1e-15)
+        second = np.einsum("i,ia,ib->ab", feq, E, E)
+        np.testing.assert_allclose(second, rho / 3 * np.eye(2) + rho * np.outer(u, u),
+                                   atol=1e-14)
+
+
+def test_weights_match_paper():
+    g = json.load(open(GOLDEN))
+    np.testing.assert_allclose(oracle.W, g["weights"]["w"], rtol=0, atol=1e-17)
+    # Link vectors of Section 2: e_i = (cos, sin)[pi (i-1)/2] for i = 1..4,
+    # sqrt(2) (cos, sin)[pi (i - 9/2)/2] for i = 5..8.
+    for i in range(1, 5):
+        a = np.pi * (i - 1) / 2
+        assert (oracle.EX[i], oracle.EY[i]) == (round(np.cos(a)), round(np.sin(a)))
+    for i in range(5, 9):
+        a = np.pi * (i - 4.5) / 2
+        assert (oracle.EX[i], oracle.EY[i]) == (round(np.sqrt(2) * np.cos(a)),
+                                              round(np.sqrt(2) * np.sin(a)))
+
+
+# --- Section 3, Eq. 5: the force term ----------------------------------------
+
+def test_force_moments_closed_form():
+    """The force 3 w_i alpha grad(rho).e_i adds no mass and adds momentum
+    alpha grad(rho) (Section 3, the body force alpha grad rho).  For
+    rho = 1 + A sin(kx) the central difference is A sin(k) cos(kx) exactly."""
+    nx, ny, A, tau, alpha = 32, 4, 1e-3, 0.8, -0.3
+    k = 2 * np.pi / nx
+    rho, ux, uy = workloads.sine_wave(nx, ny, A)
+    f0 = oracle.init(rho, ux, uy)
+    fa, fz = f0.copy(), f0.copy()
+    oracle.run(fa, tau, alpha, 1)
+    oracle.run(fz, tau, 0.0, 1)
+    # Pull the difference back to the site where the force was applied.
+    d = fa - fz
+    F = np.stack([np.roll(d[i], (-oracle.EY[i], -oracle.EX[i]), axis=(0, 1))
+                  for i in range(9)])
+    np.testing.assert_allclose(F.sum(axis=0), 0.0, atol=1e-18)
+    x = np.arange(nx)
+    gx = A * np.sin(k) * np.cos(k * x)
+    np.testing.assert_allclose(np.tensordot(oracle.EX, F, 1),
+                               np.broadcast_to(alpha * gx, (ny, nx)), rtol=1e-9, atol=1e-18)
+    np.testing.assert_allclose(np.tensordot(oracle.EY, F, 1), 0.0, atol=1e-18)
+
+
+# --- invariants --------------------------------------------------------------
+
+@pytest.mark.parametrize("c2", [1 / 3, 0.2, 0.05, 0.9])
+def test_conservation_mass_momentum(c2):
+    """Collision conserves rho and rho u per site (Eq. 2-3), the force has zero
+    mass and a periodic central difference sums to zero over the grid, so the
+    grid totals of mass and momentum stay fixed (FP64 rounding only)."""
+    rho, ux, uy = workloads.fourier_modes(24, 20, amp=1e-2, seed=7)
+    rng = np.random.default_rng(5)
+    ux = 1e-2 * rng.standard_normal(rho.shape)
+    uy = 1e-2 * rng.standard_normal(rho.shape)
+    f = oracle.init(rho, ux, uy)
+    s0 = oracle.sums(f)
+    for _ in range(10):
+        oracle.run(f, 0.7, oracle.alpha_from_c2(c2), 10)
+        s = oracle.sums(f)
+        assert abs(s[0] - s0[0]) <= 1e-13 * s0[0]
+        assert np.all(np.abs(s[1:] - s0[1:]) <= 1e-13 * s0[0])
+
+
+def test_exact_rational_brute_force():
+    """The oracle equals an exact rational evaluation of Eq. 5 (brute force on
+    tiny grids, written with pull streaming) to FP64 rounding."""
+    rng = np.random.default_rng(3)
+    for nx, ny, steps, tau, c2 in [(3, 3, 3, Q(4, 5), Q(1, 5)),
+                                   (4, 3, 3, Q(3, 5), Q(1, 20)),
+                                   (5, 4, 2, Q(3, 2), Q(9, 10))]:
+        rq = [[1 + Q(int(rng.integers(-80, 80)), 1000) for _ in range(nx)] for _ in range(ny)]
+        uxq = [[Q(int(rng.integers(-30, 30)), 1000) for _ in range(nx)] for _ in range(ny)]
+        uyq = [[Q(int(rng.integers(-30, 30)), 1000) for _ in range(nx)] for _ in range(ny)]
+        alpha = Q(1, 3) - c2
+        fq = exact.run(exact.init(rq, uxq, uyq), tau, alpha, steps)
+        r_ex, ux_ex, uy_ex = exact.moments(fq)
+        f = oracle.init(np.array(rq, float), np.array(uxq, float), np.array(uyq, float))
+        oracle.run(f, float(tau), float(alpha), steps)
+        fx = np.array([[[float(fq[y][x][i]) for x in range(nx)] for y in range(ny)]
+                       for i in range(9)])
+        np.testing.assert_allclose(f, fx, rtol=0, atol=4e-16)
+        r, u, v = oracle.moments(f)
+        np.testing.assert_allclose(r, np.array(r_ex, float), atol=2e-15)
+        np.testing.assert_allclose(u, np.array(ux_ex, float), atol=1e-15)
+        np.testing.assert_allclose(v, np.array(uy_ex, float), atol=1e-15)
+
+
+def test_translation_invariance_bitwise():
+    """The periodic update commutes with shifts of the grid (bitwise: every
+    site does the same FP64 arithmetic)."""
+    rho, ux, uy = workloads.fourier_modes(20, 16, amp=1e-2, seed=9)
+    f1 = oracle.init(rho, ux, uy)
+    sh = (3, 5)
+    f2 = oracle.init(np.roll(rho, sh, (0, 1)), ux, uy)
+    oracle.run(f1, 0.9, 0.1, 25)
+    oracle.run(f2, 0.9, 0.1, 25)
+    assert np.array_equal(np.roll(f1, sh, (1, 2)), f2)
+
+
+def test_transpose_symmetry():
+    """Swapping x and y (and u_x, u_y) swaps the result: the links of Section 2
+    are symmetric under the exchange."""
+    rng = np.random.default_rng(2)
+    rho, _, _ = workloads.fourier_modes(16, 16, amp=1e-2, seed=4)
+    ux = 1e-2 * rng.standard_normal((16, 16))
+    uy = 1e-2 * rng.standard_normal((16, 16))
+    fa = oracle.init(rho, ux, uy)
+    fb = oracle.init(rho.T.copy(), uy.T.copy(), ux.T.copy())
+    oracle.run(fa, 0.75, -0.2, 20)
+    oracle.run(fb, 0.75, -0.2, 20)
+    ra, uxa, uya = oracle.moments(fa)
+    rb, uxb, uyb = oracle.moments(fb)
+    np.testing.assert_allclose(rb, ra.T, atol=1e-15)
+    np.testing.assert_allclose(uxb, uya.T, atol=1e-15)
+    np.testing.assert_allclose(uyb, uxa.T, atol=1e-15)
+
+
+def test_threads_do_not_change_result():
+    rho, ux, uy = workloads.fourier_modes(40, 30, amp=1e-2, seed=1)
+    out = []
+    for n in (1, 3):
+        oracle.set_threads(n)
+        f = oracle.init(rho, ux, uy)
+        oracle.run(f, 0.8, 0.05, 20)
+        out.append(f)
+    oracle.set_threads(0)
+    assert np.array_equal(out[0], out[1])
+
+
+# --- Section 3, Eq. 8 and Section 4: the sound speed ---------------------------
+
+def test_paper_alpha_to_sound_speed_values():
+    """c_e = sqrt(c_1^2 - alpha) with c_1^2 = 1/3 reproduces every (alpha, c_e)
+    pair the paper prints (Section 4), and the shock distances of Eq. 9."""
+    g = json.load(open(GOLDEN))
+    for row in g["alpha_to_ce"]:
+        ce = np.sqrt(max(oracle.C1_SQ - row["alpha"], 0.0))
+        assert abs(ce - row["c_e"]) < 5e-4, row
+        assert abs(oracle.alpha_from_c2(row["c_e"] ** 2) - row["alpha"]) < 2e-4
+    sd = g["shock_distance"]
+    for row in sd["sigma_over_lambda"]:
+        k = 2 * np.pi / sd["lambda"]
+        sigma = 1.0 / (sd["epsilon"] * (sd["u0"] / row["c_e"]) * k)
+        assert abs(sigma / sd["lambda"] - row["approx"]) < 0.5
+    # nu = (2 tau - 1)/6 (Eq. 4/7): the decay runs' viscosities come from
+    # round relaxation times.
+    taus = [(6 * nu + 1) / 2 for nu in g["viscosity_runs"]["nu"]]
+    np.testing.assert_allclose(taus, [0.6, 2.0, 4.0], atol=1e-12)
+
+
+def test_linear_analysis_closed_forms():
+    """The linearised update at k = 0 has eigenvalue 1 three times (mass and
+    momentum) and 1 - 1/tau six times; at small k the sound speed tends to
+    sqrt(1/3 - alpha) and the shear damping to nu k^2 (Eq. 7-8)."""
+    for tau in (0.6, 0.8, 1.7):
+        lam = np.sort(np.linalg.eigvals(linear.update_matrix(0, 0, tau, 0.2)).real)
+        np.testing.assert_allclose(lam[:6], 1 - 1 / tau, atol=1e-12)
+        np.testing.assert_allclose(lam[6:], 1.0, atol=1e-12)
+    for c2 in (1 / 3, 0.2, 0.05, 0.81):
+        k = 2 * np.pi / 2048
+        m = linear.hydro_modes(k, 0, 0.8, 1 / 3 - c2)
+        assert abs(m["c"] / np.sqrt(c2) - 1) < 2e-5
+        nu = (2 * 0.8 - 1) / 6
+        assert abs(m["gamma_shear"] / (nu * k * k) - 1) < 2e-5
+    # The paper's wave (1) and (2) values: alpha = 0.2933, -0.47667.
+    for alpha, ce in ((0.2933, 0.2), (-0.47667, 0.9)):
+        m = linear.hydro_modes(2 * np.pi / 4000, 0, 0.53, alpha)
+        assert abs(m["c"] - ce) < 5e-4
+
+
+@pytest.mark.parametrize("c2", [1 / 3, 0.2, 0.05])
+def test_standing_wave_sound_speed(c2):
+    """A small standing wave oscillates at omega = c k with c^2 = c2
+    (Section 3, Eq. 8): the fitted frequency and damping of the oracle's
+    run match the linear analysis to 1e-5, and c matches sqrt(c2) to the
+    grid's O(k^2) offset (< 0.6 % at nx = 64, < 0.05 % at nx = 256)."""
+    tau = 0.8
+    for nx, tol in ((64, 6e-3), (256, 5e-4)):
+        k = 2 * np.pi / nx
+        alpha = oracle.alpha_from_c2(c2)
+        lin = linear.hydro_modes(k, 0, tau, alpha)
+        rho, ux, uy = workloads.sine_wave(nx, 2, 1e-6)
+        f = oracle.init(rho, ux, uy)
+        period = 2 * np.pi / lin["omega"]
+        steps = int(3 * period)
+        t, a = _series(f, tau, alpha, steps, every=max(1, int(period / 60)))
+        keep = t >= 20
+        w, g, _, _ = fit_damped_cos(t[keep], a[keep, 0], lin["omega"], lin["gamma_sound"])
+        assert abs(w / lin["omega"] - 1) < 1e-5
+        assert abs(g / lin["gamma_sound"] - 1) < 1e-3
+        assert abs(w / k / np.sqrt(c2) - 1) < tol
+
+
+def test_shear_wave_viscosity_independent_of_c():
+    """A shear wave decays at nu k^2 with nu = (2 tau - 1)/6 (Eq. 4/7), and the
+    rate does not depend on alpha (Section 4, Fig. 5-6 discussion)."""
+    nx, tau = 64, 0.9
+    k = 2 * np.pi / nx
+    nu = (2 * tau - 1) / 6
+    rates = []
+    for c2 in (1 / 3, 0.2, 0.05, 0.6):
+        rho = np.ones((2, nx))
+        ux = np.zeros((2, nx))
+        uy = np.broadcast_to(1e-6 * np.sin(k * np.arange(nx)), (2, nx)).copy()
+        f = oracle.init(rho, ux, uy)
+        t, a = _series(f, tau, oracle.alpha_from_c2(c2), 400, every=20, field="uy")
+        rates.append(fit_decay(t[2:], a[2:, 0]))
+        lin = linear.hydro_modes(k, 0, tau, oracle.alpha_from_c2(c2))
+        assert abs(rates[-1] / lin["gamma_shear"] - 1) < 1e-5
+    rates = np.array(rates)
+    assert np.all(np.abs(rates / (nu * k * k) - 1) < 1e-3)
+    assert np.ptp(rates) / rates.mean() < 1e-9
+
+
+def test_progressive_wave_direction_and_impedance():
+    """A right-running wave u = u0 sin(kx), rho = 1 + (u0/c) sin(kx)
+    (Section 4) keeps u/c = (rho - rho0)/rho0 (the plane-wave relation the
+    paper uses to measure c_e) and moves in +x at c."""
+    nx, tau, c2, u0 = 512, 0.55, 0.2, 1e-6
+    c = np.sqrt(c2)
+    k = 2 * np.pi / nx
+    rho, ux, uy = workloads.progressive_wave(nx, 2, u0, c)
+    f = oracle.init(rho, ux, uy)
+    steps = 200
+    oracle.run(f, tau, oracle.alpha_from_c2(c2), steps)
+    r, u, _ = oracle.moments(f)
+    rs, rc = mode_sin_cos(r - 1.0)
+    us, uc = mode_sin_cos(u)
+    # Phase: a profile sin(k(x - c t)) has sine part cos(k c t), cosine part
+    # -sin(k c t).
+    phase = np.arctan2(-rc, rs)
+    lin = linear.hydro_modes(k, 0, tau, oracle.alpha_from_c2(c2))
+    # The equilibrium start is only nearly a pure right-runner (the discrete
+    # impedance differs from sqrt(c2) at O(k^2)), so allow 1 % of the phase.
+    assert abs(phase / (lin["omega"] * steps) - 1) < 1e-2
+    ratio = np.hypot(us, uc) / np.hypot(rs, rc)
+    # The small counter-running part the start excites (O(nu k)) makes the
+    # ratio wobble by a few 1e-3 at this k.
+    assert abs(ratio / c - 1) < 5e-3
+
+
+def test_stability_central_vs_forward():
+    """Section 4: with a forward difference the model turns unstable as c_e
+    approaches 1; with the central difference it stays stable through c_e = 1,
+    and plane waves (k along x, as in the paper's runs, which stay exactly
+    uniform in y) stay stable up to the largest value the paper observed,
+    c_e = 1.125, turning unstable beyond it."""
+    g = json.load(open(GOLDEN))
+    ce_max = g["largest_stable_ce"]["value"]
+    ks = 2 * np.pi * np.arange(128) / 128
+
+    def plane(tau, ce, grad="central"):
+        return max(linear.spectral_radius(k, 0, tau, 1 / 3 - ce ** 2, grad) for k in ks)
+
+    for tau in (0.6, 0.8):
+        assert plane(tau, 0.95, "forward") > 1.01
+        assert plane(tau, 0.95) <= 1 + 1e-12
+        assert plane(tau, ce_max) <= 1 + 1e-12
+        assert plane(tau, 1.2) > 1 + 1e-4
+    for tau in (0.6, 0.8, 1.0):
+        for ce in (0.2, 0.5, 0.9, 1.0):
+            assert linear.max_growth(16, tau, 1 / 3 - ce ** 2) <= 1 + 1e-12
+
+
+def test_nonlinearity_grows_as_sound_speed_falls():
+    """Section 4-5: at equal velocity amplitude a wave in the fluid with the
+    lower sound speed steepens more (Eq. 9, sigma = c_e/(u0 k)): after the same
+    distance in wavelengths its second harmonic is larger, and for small u0
+    that harmonic grows in proportion to u0."""
+    nx, tau = 128, 0.52
+    k = 2 * np.pi / nx
+    h2 = {}
+    for ce in (0.2, 0.5):
+        for u0 in (2e-3, 4e-3):
+            rho, ux, uy = workloads.progressive_wave(nx, 2, u0, ce)
+            f = oracle.init(rho, ux, uy)
+            steps = int(round(2 * nx / ce))   # two wavelengths of travel
+            oracle.run(f, tau, oracle.alpha_from_c2(ce * ce), steps)
+            _, u, _ = oracle.moments(f)
+            a = harmonic_amplitudes(u.mean(axis=0), 3)
+            h2[(ce, u0)] = a[1] / a[0]
+    assert h2[(0.2, 2e-3)] > 2 * h2[(0.5, 2e-3)]
+    for ce in (0.2, 0.5):
+        r = h2[(ce, 4e-3)] / h2[(ce, 2e-3)]
+        assert 1.7 < r < 2.3, (ce, r)
