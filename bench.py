@@ -1,0 +1,349 @@
+"""Benchmark: MLUPS and fraction of the HBM roofline of the fused
+variable-speed-of-sound D2Q9 step on one GB300 (or N replicas under torchrun).
+
+Workload (N = 1): the 2048 x 2048 sweep: nine periodic FP32 grids with
+c^2 = 0.05, 0.10, ..., 0.45, tau ~ U[0.55, 1.5] (seed 1), a standing acoustic
+wave of amplitude log-spaced 1e-3 .. 5e-2 plus a shear wave
+u_y = 1e-3 sin(2 pi x / nx).  One bench step = one time step of all nine grids
+(9 launches of the step kernel).  Every grid's two buffers (2 x 151 MB) exceed
+the 129 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+the host cores on the same workload (one grid-step per bench step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_0707_2437_gb300 import workloads  # noqa: E402
+
+BYTES_PER_LU = {"f32": 72, "f16d": 36, "bf16d": 36}
+METRIC = "MLUPS (million lattice updates per second), D2Q9 variable-speed-of-sound step"
+WORKLOAD = "2048x2048 periodic D2Q9, 9 runs c2=0.05..0.45, tau~U[0.55,1.5], acoustic+shear wave"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "step_f32_2048_traffic.json")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_0707_2437_gb300", "csrc", f)
+                  for f in ("lbm_device.cuh", "lbm_kernels.cu")]
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_setup(n_gpus: int):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sms, maxes, reasons = [], [], set()
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                maxes.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                  "sw_power_cap"), f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxes),
+                "samples": len(sms), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(seconds: float = 12.0):
+    """The FP64 oracle as it stands, on the host cores, on one 2048^2 grid of
+    the sweep: runs whole steps until `seconds` have passed."""
+    from oracle import oracle
+    cores = os.cpu_count() or 1
+    used = oracle.set_threads(cores)
+    r = workloads.sweep_2048()[0]
+    f = oracle.init(*workloads.acoustic_shear(r.nx, r.ny, r.amp))
+    alpha = oracle.alpha_from_c2(r.c2)
+    oracle.run(f, r.tau, alpha, 1)  # warm-up
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        oracle.run(f, r.tau, alpha, 1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": r.nx * r.ny * steps / dt / 1e6, "unit": "MLUPS", "cores": used,
+            "kind": "oracle",
+            "sample": f"{steps} FP64 steps of one 2048x2048 grid of the sweep ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    from oracle import oracle
+    cores = os.cpu_count() or 1
+    used = oracle.set_threads(cores)
+    runs = workloads.sweep_2048()
+    r = runs[0]
+    f = oracle.init(*workloads.acoustic_shear(r.nx, r.ny, r.amp))
+    for k in range(args.warmup):
+        rr = runs[k % 9]
+        oracle.run(f, rr.tau, oracle.alpha_from_c2(rr.c2), 1)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        rr = runs[k % 9]
+        oracle.run(f, rr.tau, oracle.alpha_from_c2(rr.c2), 1)
+    dt = time.perf_counter() - t0
+    value = r.nx * r.ny * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "one 2048x2048 grid-step per bench step"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": used, "kind": "oracle",
+                         "sample": f"{args.steps} steps of one 2048x2048 grid, tau/c2 cycling "
+                                   "through the 9 runs"},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args):
+    import torch
+
+    from paper_0707_2437_gb300 import lbm
+
+    ws, rank, local = dist_setup(args.gpus)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device (the native path has no CPU fallback)")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    runs = workloads.sweep_2048()
+    storage = args.storage
+    grids = []
+    with torch.cuda.stream(stream):
+        for r in runs:
+            g = lbm.Grid(r.nx, r.ny, r.tau, r.c2, storage, stream=stream.cuda_stream)
+            g.init(*workloads.acoustic_shear(r.nx, r.ny, r.amp))
+            if args.config:
+                g.set_config(*args.config)
+            grids.append(g)
+    cfg = grids[0].get_config()
+    sites = sum(r.nx * r.ny for r in runs)
+
+    def one_step():
+        for g in grids:
+            g.step(1)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    # Timed region: events around every launch on the launching stream.
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps * len(grids))]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps * len(grids))]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    k = 0
+    for _ in range(args.steps):
+        for g in grids:
+            starts[k].record(stream)
+            g.step(1)
+            ends[k].record(stream)
+            k += 1
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    elapsed_ms = max_over_ranks(ws, elapsed_ms)
+    value = ws * sites * args.steps / (elapsed_ms * 1e-3) / 1e6
+
+    # Roofline of the step kernel: algorithmic bytes per launch / mean launch time.
+    per_launch_s = statistics.mean(launch_ms) * 1e-3
+    alg_bytes = BYTES_PER_LU[storage] * runs[0].nx * runs[0].ny
+    achieved = alg_bytes / per_launch_s / 1e9
+    peak, peak_kind = measured_peak()
+    traffic = None
+    if os.path.exists(PROFILE_TRAFFIC):
+        tj = json.load(open(PROFILE_TRAFFIC))
+        if tj.get("source_hash") == kernel_source_hash() and tj.get("storage") == storage:
+            traffic = tj.get("dram_bytes_per_launch")
+
+    # End to end through the C ABI with host buffers: one job = lbm_init from
+    # pinned host fields, e2e_steps steps, lbm_moments back to pinned host
+    # arrays, for all nine grids.
+    n = runs[0].nx * runs[0].ny
+    host_in = [[torch.from_numpy(a).pin_memory() for a in workloads.acoustic_shear(r.nx, r.ny, r.amp)]
+               for r in runs]
+    host_out = [[torch.empty((r.ny, r.nx), dtype=torch.float64).pin_memory() for _ in range(3)]
+                for r in runs]
+
+    def job(steps):
+        for g, hin, hout in zip(grids, host_in, host_out):
+            g.init(*[t.numpy() for t in hin])
+            g.step(steps)
+        for g, hout in zip(grids, host_out):
+            g.moments(out=[t.numpy() for t in hout])
+
+    job(10)  # warm-up (graphs, allocator)
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_jobs):
+        job(args.e2e_steps)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(ws, time.perf_counter() - t0)
+    e2e_value = ws * sites * args.e2e_steps * args.e2e_jobs / e2e_s / 1e6
+
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "MLUPS",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if storage == "f32" else f"{storage} storage, f32 math",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grids": len(runs), "nx": runs[0].nx,
+                   "ny": runs[0].ny, "storage": storage, "tile": {"vec": cfg[0],
+                   "rows": cfg[1], "warps": cfg[2]},
+                   "l2": "inputs larger than L2 (2 x 151 MB per grid, 129 MB L2), no flush",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                     if peak_kind == "measured" else "fallback 6.8 TB/s",
+                     "kernel": f"k_step<{storage},vec={cfg[0]}>",
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "mean_launch_ms": per_launch_s * 1e3},
+        "e2e": {"value": e2e_value, "unit": "MLUPS",
+                "h2d_bytes_per_step": 9 * 3 * n * 8, "d2h_bytes_per_step": 9 * 3 * n * 8,
+                "step": f"one job: lbm_init from pinned host fields, {args.e2e_steps} steps, "
+                        "lbm_moments to host, for all 9 grids",
+                "jobs": args.e2e_jobs},
+        "gpu_launches": args.steps * len(grids),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    for g in grids:
+        g.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--storage", default="f32", choices=list(BYTES_PER_LU))
+    ap.add_argument("--config", type=int, nargs=3, default=None,
+                    metavar=("VEC", "ROWS", "WARPS"))
+    ap.add_argument("--e2e-steps", type=int, default=1000)
+    ap.add_argument("--e2e-jobs", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

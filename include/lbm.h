@@ -1,0 +1,212 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) variable-speed-of-sound D2Q9 lattice
+ * Boltzmann library (liblbm.so).
+ *
+ * The method (Buick & Cosgrove, "Investigation of a Lattice Boltzmann Model
+ * with a Variable Speed of Sound"):
+ *
+ *   Section 3, Eq. 5 (nbm):
+ *     f_i(x + e_i, t + 1) - f_i(x, t) = -(f_i - fbar_i)/tau + 3 w_i alpha grad(rho).e_i
+ *   Section 2, Eq. 2: fbar_i = w_i rho [1 + 3 e_i.u + 9/2 (e_i.u)^2 - 3/2 u^2]
+ *   Section 2, Eq. 3: rho = sum_i f_i,  rho u = sum_i f_i e_i
+ *   Section 3, Eq. 8 (cef): effective sound speed c_e^2 = c_1^2 - alpha, with
+ *     c_1^2 = 1/3 on this lattice; the library takes c2 = c_e^2 and uses
+ *     alpha = 1/3 - c2, so the sound speed is set independently of tau.
+ *   Section 3, Eq. 7: viscosity nu = (2 tau - 1)/6, independent of alpha.
+ *   Section 4: grad(rho) by central differences, (rho(x+1) - rho(x-1))/2 along
+ *     x and y (the stable choice).
+ *
+ * Grids are periodic in x and y.  Fields passed in or out are row-major
+ * [ny][nx] arrays of double (x fastest): element (x, y) is at index y*nx + x.
+ *
+ * Ownership: a handle owns its device memory (two distribution buffers and a
+ * small reduction scratch area), freed by lbm_destroy.  Caller pointers are
+ * only read or written during the call that receives them.  No call keeps a
+ * caller pointer.
+ *
+ * Errors: every call returns a status (LBM_OK = 0, negative on error, positive
+ * for a warning); no C++ exception crosses this interface.  lbm_strerror maps
+ * a status to text; lbm_last_error gives the detail of the calling thread's
+ * most recent failure (for example the CUDA error string).
+ *
+ * Streams: work is queued on the handle's CUDA stream (the one passed to
+ * lbm_create, or the legacy default stream if NULL).  lbm_step only queues
+ * work; lbm_moments, lbm_sums, lbm_mode, lbm_get_state and lbm_sync wait for
+ * the stream.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define LBM_OK 0
+#define LBM_EINVAL (-1)      /* an argument is out of range or NULL */
+#define LBM_ENOMEM (-2)      /* device or host allocation failed */
+#define LBM_ECUDA (-3)       /* a CUDA runtime call failed (see lbm_last_error) */
+#define LBM_ENONFINITE (-4)  /* a reduction met NaN or Inf */
+#define LBM_ETIMEOUT (-5)    /* a bounded in-kernel wait ran out */
+#define LBM_WUNSTABLE 1      /* warning: c2 > 1.2656 (c_e > 1.125), beyond the
+                                largest sound speed the paper found stable
+                                (Section 4); the handle is still created */
+
+/* Storage of the distributions in device memory.  Arithmetic is FP32 in all
+ * cases.  Every storage keeps h_i = (f_i - w_i rho0) / w_i, the deviation from
+ * the rest equilibrium scaled by the weight, so that small waves keep their
+ * precision; the 16-bit kinds round h_i to nearest-even on every store. */
+#define LBM_F32 0
+#define LBM_F16D 1
+#define LBM_BF16D 2
+
+/* Fields for lbm_mode. */
+#define LBM_FIELD_RHO 0   /* rho - rho0 */
+#define LBM_FIELD_UX 1
+#define LBM_FIELD_UY 2
+
+typedef struct lbm_grid *lbm_t;
+typedef struct lbm_batch *lbm_batch_t;
+
+/* Creates a periodic nx x ny grid (Section 2-3).
+ *   nx, ny      >= 1, nx * ny <= 2^31 - 1
+ *   tau         relaxation time, > 0.5 (Section 4: the model turns unstable as
+ *               tau -> 0.5)
+ *   c2          squared sound speed c_e^2 > 0 (Eq. 8); alpha = 1/3 - c2
+ *   storage     LBM_F32, LBM_F16D or LBM_BF16D
+ *   cuda_stream a cudaStream_t (NULL: legacy default stream)
+ *   out         receives the handle
+ * The reference density rho0 of the stored deviations is 1 (the paper's
+ * ambient density).  The state is undefined until lbm_init or lbm_set_state.
+ * Returns LBM_OK, LBM_WUNSTABLE (created, see above), LBM_EINVAL, LBM_ENOMEM
+ * or LBM_ECUDA. */
+int lbm_create(int nx, int ny, double tau, double c2, int storage,
+               void *cuda_stream, lbm_t *out);
+
+/* As lbm_create with an explicit reference density rho0 > 0. */
+int lbm_create_ex(int nx, int ny, double tau, double c2, double rho0,
+                  int storage, void *cuda_stream, lbm_t *out);
+
+/* Frees the handle and its device memory (waits for its stream first).
+ * NULL is accepted. */
+int lbm_destroy(lbm_t h);
+
+/* Sets the state at t = 0 to the local equilibrium f_i = fbar_i(rho, u)
+ * (Eq. 2) of the given fields (the paper gives rho and u only).
+ *   rho, ux, uy  [ny][nx] doubles, rho > 0; host pointers if on_device == 0,
+ *                device pointers otherwise
+ * Resets the step counter to 0.  Returns after the fields have been read. */
+int lbm_init(lbm_t h, const double *rho, const double *ux, const double *uy,
+             int on_device);
+
+/* Queues n >= 0 time steps of Eq. 5 (stream, moments, central grad(rho),
+ * collide with force) on the handle's stream.  Steps are replayed from a CUDA
+ * graph when n is large enough for launch overhead to matter.  Asynchronous:
+ * errors of the kernels themselves surface at the next synchronising call. */
+int lbm_step(lbm_t h, long long n);
+
+/* Writes rho, ux, uy (Eq. 3) of the current state, computed in FP64 from the
+ * stored distributions.
+ *   rho, ux, uy  [ny][nx] doubles (host if on_device == 0, else device);
+ *                any of them may be NULL to skip it
+ * Waits for the stream. */
+int lbm_moments(lbm_t h, double *rho, double *ux, double *uy, int on_device);
+
+/* Grid totals of mass sum rho and momentum sum rho u (Eq. 3 summed over all
+ * sites), reduced in FP64 on the device in a fixed order (bitwise
+ * reproducible).  out3 (host) receives {mass, momentum_x, momentum_y}.
+ * Returns LBM_ENONFINITE if any total is NaN or Inf.  Waits for the stream. */
+int lbm_sums(lbm_t h, double *out3);
+
+/* FP64 Fourier coefficient of a field over the grid, used to measure the
+ * sound speed and the viscosity (Section 4, the plane-wave runs and the decay
+ * formula of Eq. 10):
+ *   out2[0] = (2/N) sum_x v(x) cos(2 pi (kx x/nx + ky y/ny))
+ *   out2[1] = (2/N) sum_x v(x) sin(2 pi (kx x/nx + ky y/ny))
+ * with v = rho - rho0, ux or uy (field = LBM_FIELD_*), N = nx * ny.  A field
+ * v = A sin(2 pi kx x / nx) gives out2 = {0, A}.  Waits for the stream. */
+int lbm_mode(lbm_t h, int field, int kx, int ky, double *out2);
+
+/* Steps taken since lbm_init / lbm_set_state. */
+long long lbm_time(lbm_t h);
+
+/* Waits for all work queued on the handle's stream. */
+int lbm_sync(lbm_t h);
+
+/* Bytes of device state (both distribution buffers) a grid of this size and
+ * storage needs; 0 for invalid arguments. */
+size_t lbm_bytes_required(int nx, int ny, int storage);
+
+/* Free and total device memory (cudaMemGetInfo) of the current device. */
+int lbm_mem_info(size_t *free_bytes, size_t *total_bytes);
+
+/* Checkpoint: the raw stored distributions (9 planes of nx*ny elements of the
+ * storage type, plane-major, each plane [ny][nx]) of the current state.
+ * lbm_state_bytes gives the size; lbm_get_state copies it to host memory and
+ * the step counter to *t (may be NULL); lbm_set_state restores both.  A run
+ * resumed from a checkpoint is bitwise identical to an uninterrupted one. */
+size_t lbm_state_bytes(lbm_t h);
+int lbm_get_state(lbm_t h, void *dst_host, long long *t);
+int lbm_set_state(lbm_t h, const void *src_host, long long t);
+
+/* Tile configuration of the step kernel: each warp walks a strip of 32*vec
+ * columns down `rows` rows; blocks hold `warps` warps.  vec is the number of
+ * adjacent sites per lane (vectorised loads of vec elements): 1, 2 or 4 for
+ * any storage, 8 for the 16-bit storages; nx must be a multiple of vec.
+ * rows in [1, 4096], warps in {1, 2, 4, 8}.  The result of a step does
+ * not depend on the configuration (bitwise). */
+int lbm_set_config(lbm_t h, int vec, int rows, int warps);
+int lbm_get_config(lbm_t h, int *vec, int *rows, int *warps);
+
+/* Autotuner: times the valid tile configurations on this grid (without
+ * changing its state) and keeps the fastest.  If cache_path is not NULL the
+ * choice is read from / stored in that JSON file, keyed by device, storage
+ * and grid size.  Waits for the stream. */
+int lbm_tune(lbm_t h, const char *cache_path);
+
+/* Mean device time in milliseconds of the step kernel over the last
+ * lbm_step call made with timing enabled (lbm_set_timing(h, 1)); the events
+ * are recorded on the handle's stream around each launch. */
+int lbm_set_timing(lbm_t h, int on);
+int lbm_kernel_ms(lbm_t h, double *ms, long long *launches);
+
+/* ---- Batches: many uneven grids advanced in one persistent launch ------- */
+
+/* Groups n >= 1 existing handles (any sizes, tau, c2 and storage; all on the
+ * same device) into a batch stepped by one persistent cooperative kernel over
+ * a tile work-list, with a grid-wide barrier between time steps.  The batch
+ * refers to the handles; they must outlive it and must not be stepped
+ * individually while it is being stepped.  The batch's work runs on the
+ * stream of grids[0]. */
+int lbm_batch_create(const lbm_t *grids, int n, lbm_batch_t *out);
+int lbm_batch_destroy(lbm_batch_t b);
+
+/* Advances grid g of the batch by min(n, limits[g]) steps (limits may be NULL:
+ * n steps each), all in one launch replayed from a CUDA graph.  Asynchronous.
+ * A barrier wait that exceeds its time limit makes the kernel stop and the
+ * next synchronising batch call return LBM_ETIMEOUT. */
+int lbm_batch_step(lbm_batch_t b, long long n, const long long *limits);
+
+/* Waits for the batch's stream and returns the kernel's status
+ * (LBM_OK or LBM_ETIMEOUT). */
+int lbm_batch_sync(lbm_batch_t b);
+
+/* Tile height (rows per warp) and persistent-grid occupancy of the batch
+ * kernel; the autotuner picks them with lbm_batch_tune. */
+int lbm_batch_set_config(lbm_batch_t b, int rows, int blocks_per_sm);
+int lbm_batch_tune(lbm_batch_t b);
+
+/* Barrier wait limit of the batch kernel in microseconds (default 1e6). */
+int lbm_batch_set_timeout_us(lbm_batch_t b, long long us);
+
+/* ---- Errors --------------------------------------------------------------- */
+const char *lbm_strerror(int status);
+const char *lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

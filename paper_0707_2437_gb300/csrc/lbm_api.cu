@@ -1,0 +1,538 @@
+// C ABI of liblbm.so: handles, validation, streams, ping-pong buffers, CUDA
+// graphs of step sequences, checkpoints, the tile autotuner and error codes.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using namespace vss;
+
+// ---------------------------------------------------------------------------
+// Errors.
+
+static thread_local std::string g_last_error;
+
+namespace vss {
+void set_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace vss
+
+static int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+static int cuda_fail(cudaError_t e, const char *where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+extern "C" const char *lbm_strerror(int status) {
+    switch (status) {
+        case LBM_OK:
+            return "ok";
+        case LBM_EINVAL:
+            return "invalid argument";
+        case LBM_ENOMEM:
+            return "out of memory";
+        case LBM_ECUDA:
+            return "CUDA error";
+        case LBM_ENONFINITE:
+            return "non-finite value in a reduction";
+        case LBM_ETIMEOUT:
+            return "in-kernel wait timed out";
+        case LBM_WUNSTABLE:
+            return "warning: sound speed above the largest stable value observed (c_e > 1.125)";
+        default:
+            return "unknown status";
+    }
+}
+
+extern "C" const char *lbm_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// Handle.
+
+static size_t state_bytes(const lbm_grid *h) { return 9 * h->P * (size_t)elem_bytes(h->storage); }
+
+static TileCfg default_cfg(int storage, int nx, int ny) {
+    TileCfg c;
+    int best = storage == ST_F32 ? 4 : 8;
+    c.vec = 1;
+    for (int v = best; v >= 1; v /= 2)
+        if (valid_vec(storage, nx, v)) {
+            c.vec = v;
+            break;
+        }
+    c.rows = 16;
+    c.warps = 4;
+    return c;
+}
+
+static void drop_graphs(lbm_grid *h) {
+    for (int k = 0; k < 2; ++k)
+        if (h->graph[k]) {
+            cudaGraphExecDestroy(h->graph[k]);
+            h->graph[k] = nullptr;
+        }
+    h->graph_pairs = 0;
+}
+
+extern "C" size_t lbm_bytes_required(int nx, int ny, int storage) {
+    if (nx < 1 || ny < 1 || storage < 0 || storage > 2) return 0;
+    if ((long long)nx * ny > 0x7fffffffLL) return 0;
+    return 2 * 9 * plane_elems(nx, ny) * (size_t)elem_bytes(storage);
+}
+
+extern "C" int lbm_mem_info(size_t *free_bytes, size_t *total_bytes) {
+    size_t f = 0, t = 0;
+    CK(cudaMemGetInfo(&f, &t));
+    if (free_bytes) *free_bytes = f;
+    if (total_bytes) *total_bytes = t;
+    return LBM_OK;
+}
+
+extern "C" int lbm_create_ex(int nx, int ny, double tau, double c2, double rho0, int storage,
+                             void *cuda_stream, lbm_t *out) {
+    if (!out) return fail(LBM_EINVAL, "lbm_create: out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || (long long)nx * ny > 0x7fffffffLL)
+        return fail(LBM_EINVAL, "lbm_create: need nx, ny >= 1 and nx*ny < 2^31");
+    if (!(tau > 0.5) || !isfinite(tau)) return fail(LBM_EINVAL, "lbm_create: need tau > 0.5");
+    if (!(c2 > 0.0) || !isfinite(c2)) return fail(LBM_EINVAL, "lbm_create: need c2 > 0");
+    if (!(rho0 > 0.0) || !isfinite(rho0)) return fail(LBM_EINVAL, "lbm_create: need rho0 > 0");
+    if (storage < 0 || storage > 2) return fail(LBM_EINVAL, "lbm_create: unknown storage");
+
+    lbm_grid *h = new (std::nothrow) lbm_grid();
+    if (!h) return fail(LBM_ENOMEM, "lbm_create: host allocation failed");
+    h->nx = nx;
+    h->ny = ny;
+    h->tau = tau;
+    h->c2 = c2;
+    h->rho0 = rho0;
+    h->storage = storage;
+    h->P = plane_elems(nx, ny);
+    h->stream = (cudaStream_t)cuda_stream;
+    h->coef = make_coef(tau, c2, rho0);
+    h->cfg = default_cfg(storage, nx, ny);
+    cudaError_t e = cudaGetDevice(&h->device);
+    size_t bytes = state_bytes(h);
+    if (e == cudaSuccess) e = cudaMalloc(&h->buf[0], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->buf[1], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->scratch, sizeof(double) * (3 * 1024 + 16));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->host_out, sizeof(double) * 8);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev[1]);
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(e, "lbm_create");
+        lbm_destroy(h);
+        cudaGetLastError();
+        return rc;
+    }
+    *out = h;
+    return c2 > 1.2656 ? LBM_WUNSTABLE : LBM_OK;
+}
+
+extern "C" int lbm_create(int nx, int ny, double tau, double c2, int storage, void *cuda_stream,
+                          lbm_t *out) {
+    return lbm_create_ex(nx, ny, tau, c2, 1.0, storage, cuda_stream, out);
+}
+
+extern "C" int lbm_destroy(lbm_t h) {
+    if (!h) return LBM_OK;
+    if (h->stream || h->buf[0]) cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
+    for (int k = 0; k < 2; ++k) {
+        if (h->buf[k]) cudaFree(h->buf[k]);
+        if (h->ev[k]) cudaEventDestroy(h->ev[k]);
+    }
+    if (h->scratch) cudaFree(h->scratch);
+    if (h->host_out) cudaFreeHost(h->host_out);
+    delete h;
+    return LBM_OK;
+}
+
+// Copies a [ny][nx] double field to device scratch if it is on the host.
+static int stage_field(lbm_grid *h, const double *src, int on_device, double **dev,
+                       std::vector<double *> &owned) {
+    if (on_device) {
+        *dev = const_cast<double *>(src);
+        return LBM_OK;
+    }
+    size_t n = (size_t)h->nx * h->ny;
+    double *d = nullptr;
+    CK(cudaMallocAsync(&d, n * sizeof(double), h->stream));
+    owned.push_back(d);
+    CK(cudaMemcpyAsync(d, src, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    *dev = d;
+    return LBM_OK;
+}
+
+extern "C" int lbm_init(lbm_t h, const double *rho, const double *ux, const double *uy,
+                        int on_device) {
+    if (!h || !rho || !ux || !uy) return fail(LBM_EINVAL, "lbm_init: NULL argument");
+    std::vector<double *> owned;
+    double *dr = nullptr, *du = nullptr, *dv = nullptr;
+    int rc = stage_field(h, rho, on_device, &dr, owned);
+    if (rc == LBM_OK) rc = stage_field(h, ux, on_device, &du, owned);
+    if (rc == LBM_OK) rc = stage_field(h, uy, on_device, &dv, owned);
+    if (rc == LBM_OK) {
+        cudaError_t e = launch_init(h->storage, h->buf[0], h->nx, h->ny, h->P, h->rho0, dr, du, dv,
+                                    h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "lbm_init kernel");
+    }
+    for (double *p : owned) cudaFreeAsync(p, h->stream);
+    if (rc != LBM_OK) return rc;
+    h->cur = 0;
+    h->t = 0;
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+// One step launch from buf[cur] to buf[cur ^ 1] (no bookkeeping).
+static cudaError_t launch_one(lbm_grid *h, int from) {
+    return launch_step(h->storage, h->cfg, h->buf[from], h->buf[from ^ 1], h->nx, h->ny, h->P,
+                       h->coef, h->stream);
+}
+
+static const int kGraphPairs = 16;   // a graph holds 32 steps
+static const long long kGraphMin = 8; // use graphs from this many steps on
+
+static int build_graphs(lbm_grid *h) {
+    drop_graphs(h);
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    for (int start = 0; start < 2; ++start) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            for (int k = 0; k < 2 * kGraphPairs && e == cudaSuccess; ++k)
+                e = launch_step(h->storage, h->cfg, h->buf[(start + k) & 1],
+                                h->buf[(start + k + 1) & 1], h->nx, h->ny, h->P, h->coef, cs);
+            cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph[start], g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cs);
+            drop_graphs(h);
+            return cuda_fail(e, "lbm_step: graph capture");
+        }
+    }
+    cudaStreamDestroy(cs);
+    h->graph_pairs = kGraphPairs;
+    return LBM_OK;
+}
+
+extern "C" int lbm_step(lbm_t h, long long n) {
+    if (!h || n < 0) return fail(LBM_EINVAL, "lbm_step: bad handle or n < 0");
+    if (n == 0) return LBM_OK;
+    if (h->timing) {
+        // Per-launch events: accumulate device time of every launch.
+        double total = 0.0;
+        for (long long k = 0; k < n; ++k) {
+            CK(cudaEventRecord(h->ev[0], h->stream));
+            cudaError_t e = launch_one(h, h->cur);
+            if (e != cudaSuccess) return cuda_fail(e, "lbm_step kernel");
+            CK(cudaEventRecord(h->ev[1], h->stream));
+            CK(cudaEventSynchronize(h->ev[1]));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+            total += ms;
+            h->cur ^= 1;
+            h->t += 1;
+        }
+        h->kernel_ms = total / (double)n;
+        h->kernel_launches = n;
+        return LBM_OK;
+    }
+    if (n >= kGraphMin) {
+        if (!h->graph_pairs) {
+            int rc = build_graphs(h);
+            if (rc != LBM_OK) return rc;
+        }
+        long long per = 2LL * h->graph_pairs;
+        while (n >= per) {
+            CK(cudaGraphLaunch(h->graph[h->cur], h->stream));
+            n -= per;
+            h->t += per;  // an even number of steps leaves cur unchanged
+        }
+    }
+    for (long long k = 0; k < n; ++k) {
+        cudaError_t e = launch_one(h, h->cur);
+        if (e != cudaSuccess) return cuda_fail(e, "lbm_step kernel");
+        h->cur ^= 1;
+        h->t += 1;
+    }
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_timing(lbm_t h, int on) {
+    if (!h) return fail(LBM_EINVAL, "lbm_set_timing: NULL handle");
+    h->timing = on != 0;
+    return LBM_OK;
+}
+
+extern "C" int lbm_kernel_ms(lbm_t h, double *ms, long long *launches) {
+    if (!h) return fail(LBM_EINVAL, "lbm_kernel_ms: NULL handle");
+    if (ms) *ms = h->kernel_ms;
+    if (launches) *launches = h->kernel_launches;
+    return LBM_OK;
+}
+
+extern "C" int lbm_moments(lbm_t h, double *rho, double *ux, double *uy, int on_device) {
+    if (!h) return fail(LBM_EINVAL, "lbm_moments: NULL handle");
+    size_t n = (size_t)h->nx * h->ny;
+    if (on_device) {
+        cudaError_t e = launch_moments(h->storage, h->buf[h->cur], h->nx, h->ny, h->P, h->rho0,
+                                       rho, ux, uy, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "lbm_moments kernel");
+        CK(cudaStreamSynchronize(h->stream));
+        return LBM_OK;
+    }
+    double *d = nullptr;
+    CK(cudaMallocAsync(&d, 3 * n * sizeof(double), h->stream));
+    cudaError_t e = launch_moments(h->storage, h->buf[h->cur], h->nx, h->ny, h->P, h->rho0,
+                                   rho ? d : nullptr, ux ? d + n : nullptr,
+                                   uy ? d + 2 * n : nullptr, h->stream);
+    if (e == cudaSuccess && rho)
+        e = cudaMemcpyAsync(rho, d, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && ux)
+        e = cudaMemcpyAsync(ux, d + n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && uy)
+        e = cudaMemcpyAsync(uy, d + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream);
+    cudaFreeAsync(d, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_moments");
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+extern "C" int lbm_sums(lbm_t h, double *out3) {
+    if (!h || !out3) return fail(LBM_EINVAL, "lbm_sums: NULL argument");
+    double *partials = h->scratch + 16;
+    cudaError_t e = launch_sums(h->storage, h->buf[h->cur], h->nx, h->ny, h->P, partials,
+                                h->scratch, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_sums kernel");
+    CK(cudaMemcpyAsync(h->host_out, h->scratch, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    out3[0] = (double)h->nx * (double)h->ny * h->rho0 + h->host_out[0];
+    out3[1] = h->host_out[1];
+    out3[2] = h->host_out[2];
+    for (int k = 0; k < 3; ++k)
+        if (!isfinite(out3[k])) return fail(LBM_ENONFINITE, "lbm_sums: non-finite total");
+    return LBM_OK;
+}
+
+extern "C" int lbm_mode(lbm_t h, int field, int kx, int ky, double *out2) {
+    if (!h || !out2 || field < 0 || field > 2)
+        return fail(LBM_EINVAL, "lbm_mode: bad argument");
+    double *partials = h->scratch + 16;
+    cudaError_t e = launch_mode(h->storage, h->buf[h->cur], h->nx, h->ny, h->P, h->rho0, field, kx,
+                                ky, partials, h->scratch, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_mode kernel");
+    CK(cudaMemcpyAsync(h->host_out, h->scratch, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    out2[0] = h->host_out[0];
+    out2[1] = h->host_out[1];
+    if (!isfinite(out2[0]) || !isfinite(out2[1]))
+        return fail(LBM_ENONFINITE, "lbm_mode: non-finite value");
+    return LBM_OK;
+}
+
+extern "C" long long lbm_time(lbm_t h) { return h ? h->t : -1; }
+
+extern "C" int lbm_sync(lbm_t h) {
+    if (!h) return fail(LBM_EINVAL, "lbm_sync: NULL handle");
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoints.
+
+extern "C" size_t lbm_state_bytes(lbm_t h) {
+    return h ? 9 * (size_t)h->nx * h->ny * elem_bytes(h->storage) : 0;
+}
+
+extern "C" int lbm_get_state(lbm_t h, void *dst_host, long long *t) {
+    if (!h || !dst_host) return fail(LBM_EINVAL, "lbm_get_state: NULL argument");
+    size_t row = (size_t)h->nx * h->ny * elem_bytes(h->storage);
+    size_t pitch = h->P * elem_bytes(h->storage);
+    CK(cudaMemcpy2DAsync(dst_host, row, h->buf[h->cur], pitch, row, 9, cudaMemcpyDeviceToHost,
+                         h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (t) *t = h->t;
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_state(lbm_t h, const void *src_host, long long t) {
+    if (!h || !src_host || t < 0) return fail(LBM_EINVAL, "lbm_set_state: bad argument");
+    size_t row = (size_t)h->nx * h->ny * elem_bytes(h->storage);
+    size_t pitch = h->P * elem_bytes(h->storage);
+    CK(cudaMemcpy2DAsync(h->buf[0], pitch, src_host, row, row, 9, cudaMemcpyHostToDevice,
+                         h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->cur = 0;
+    h->t = t;
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tile configuration and autotuner.
+
+extern "C" int lbm_set_config(lbm_t h, int vec, int rows, int warps) {
+    if (!h) return fail(LBM_EINVAL, "lbm_set_config: NULL handle");
+    if (!valid_vec(h->storage, h->nx, vec))
+        return fail(LBM_EINVAL, "lbm_set_config: vec must be 1, 2, 4 (or 8 for 16-bit) and divide nx");
+    if (rows < 1 || rows > 4096) return fail(LBM_EINVAL, "lbm_set_config: rows in [1, 4096]");
+    if (warps != 1 && warps != 2 && warps != 4 && warps != 8)
+        return fail(LBM_EINVAL, "lbm_set_config: warps in {1, 2, 4, 8}");
+    if (h->cfg.vec != vec || h->cfg.rows != rows || h->cfg.warps != warps) {
+        CK(cudaStreamSynchronize(h->stream));
+        drop_graphs(h);
+    }
+    h->cfg.vec = vec;
+    h->cfg.rows = rows;
+    h->cfg.warps = warps;
+    return LBM_OK;
+}
+
+extern "C" int lbm_get_config(lbm_t h, int *vec, int *rows, int *warps) {
+    if (!h) return fail(LBM_EINVAL, "lbm_get_config: NULL handle");
+    if (vec) *vec = h->cfg.vec;
+    if (rows) *rows = h->cfg.rows;
+    if (warps) *warps = h->cfg.warps;
+    return LBM_OK;
+}
+
+static std::string tune_key(const lbm_grid *h) {
+    cudaDeviceProp p;
+    std::string dev = "dev";
+    if (cudaGetDeviceProperties(&p, h->device) == cudaSuccess) dev = p.name;
+    std::ostringstream k;
+    k << dev << "|s" << h->storage << "|" << h->nx << "x" << h->ny;
+    return k.str();
+}
+
+// The cache file is a flat JSON object {"key": [vec, rows, warps], ...}.
+static std::map<std::string, TileCfg> read_cache(const char *path) {
+    std::map<std::string, TileCfg> m;
+    std::ifstream in(path);
+    if (!in) return m;
+    std::stringstream ss;
+    ss << in.rdbuf();
+    std::string s = ss.str();
+    size_t pos = 0;
+    while ((pos = s.find('"', pos)) != std::string::npos) {
+        size_t end = s.find('"', pos + 1);
+        if (end == std::string::npos) break;
+        std::string key = s.substr(pos + 1, end - pos - 1);
+        size_t lb = s.find('[', end), rb = s.find(']', end);
+        if (lb == std::string::npos || rb == std::string::npos) break;
+        TileCfg c;
+        if (sscanf(s.c_str() + lb, "[%d , %d , %d]", &c.vec, &c.rows, &c.warps) == 3 ||
+            sscanf(s.c_str() + lb, "[%d,%d,%d]", &c.vec, &c.rows, &c.warps) == 3)
+            m[key] = c;
+        pos = rb + 1;
+    }
+    return m;
+}
+
+static void write_cache(const char *path, const std::map<std::string, TileCfg> &m) {
+    std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    fprintf(f, "{\n");
+    size_t k = 0;
+    for (auto &kv : m) {
+        fprintf(f, "  \"%s\": [%d, %d, %d]%s\n", kv.first.c_str(), kv.second.vec, kv.second.rows,
+                kv.second.warps, (++k < m.size()) ? "," : "");
+    }
+    fprintf(f, "}\n");
+    fclose(f);
+    rename(tmp.c_str(), path);
+}
+
+// Times one configuration: `reps` launches from buf[cur] into the other buffer
+// (the state itself is not changed).
+static int time_cfg(lbm_grid *h, const TileCfg &c, int reps, float *ms_out) {
+    TileCfg saved = h->cfg;
+    h->cfg = c;
+    cudaError_t e = launch_one(h, h->cur);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev[0], h->stream);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_one(h, h->cur);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev[1], h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(h->ev[1]);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+    h->cfg = saved;
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_tune");
+    *ms_out = ms / reps;
+    return LBM_OK;
+}
+
+extern "C" int lbm_tune(lbm_t h, const char *cache_path) {
+    if (!h) return fail(LBM_EINVAL, "lbm_tune: NULL handle");
+    std::string key = tune_key(h);
+    std::map<std::string, TileCfg> cache;
+    if (cache_path) {
+        cache = read_cache(cache_path);
+        auto it = cache.find(key);
+        if (it != cache.end() && valid_vec(h->storage, h->nx, it->second.vec)) {
+            return lbm_set_config(h, it->second.vec, it->second.rows, it->second.warps);
+        }
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    long long sites = (long long)h->nx * h->ny;
+    int reps = (int)std::max<long long>(3, std::min<long long>(50, 200000000LL / (sites + 1)));
+    TileCfg best = h->cfg;
+    float best_ms = 1e30f;
+    const int vecs[] = {1, 2, 4, 8};
+    const int rowss[] = {4, 8, 16, 32, 64, 128};
+    const int warpss[] = {2, 4, 8};
+    for (int v : vecs) {
+        if (!valid_vec(h->storage, h->nx, v)) continue;
+        for (int r : rowss) {
+            if (r > 2 * h->ny && r != 4) continue;
+            for (int w : warpss) {
+                TileCfg c;
+                c.vec = v;
+                c.rows = r;
+                c.warps = w;
+                float ms;
+                int rc = time_cfg(h, c, reps, &ms);
+                if (rc != LBM_OK) return rc;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = c;
+                }
+            }
+        }
+    }
+    int rc = lbm_set_config(h, best.vec, best.rows, best.warps);
+    if (rc != LBM_OK) return rc;
+    if (cache_path) {
+        cache[key] = best;
+        write_cache(cache_path, cache);
+    }
+    return LBM_OK;
+}

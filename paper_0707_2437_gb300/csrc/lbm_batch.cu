@@ -1,0 +1,448 @@
+// Batched form: many uneven grids (any size, tau, c2 and storage) advanced by
+// one persistent cooperative kernel over a tile work-list, with a grid-wide
+// barrier between time steps, replayed from a CUDA graph.
+//
+// Work-list: every grid is cut into tiles of (32*vec columns) x (rows rows),
+// one warp per tile per step; tile k is done by warp k mod W of the W resident
+// warps.  Within a time step tiles are independent (each reads its grid's
+// input buffer and writes the other one); between steps every block waits at
+// a barrier, because a tile's pull reaches two rows and one column into its
+// neighbours and its store overwrites what they read one step earlier.
+//
+// Every barrier wait is bounded (wall-clock limit read from %globaltimer): a
+// block that gives up sets a status word and returns, all other blocks see the
+// status at their next barrier and return too, so the kernel always ends.
+#include <algorithm>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using namespace vss;
+
+namespace {
+
+struct GridDesc {
+    void *buf[2];
+    size_t P;
+    int nx, ny;
+    int kind;  // storage * 16 + vec
+    int pad;
+    Coef c;
+};
+
+struct Tile {
+    int grid, x0, y0, y1;
+};
+
+constexpr int kBatchWarps = 8;  // warps per block of the persistent kernel
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier over all blocks of a cooperative launch.  bar[0] counts
+// arrivals, bar[1] is the generation.  Returns false if the wait ran out or
+// another block reported an error.
+__device__ bool grid_barrier(unsigned *bar, int *status, unsigned long long timeout_ns) {
+    __shared__ int ok_sh;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *vgen = bar + 1;
+        unsigned gen = *vgen;
+        __threadfence();
+        unsigned prev = atomicAdd(bar, 1u);
+        if (prev == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned long long t0 = global_ns();
+            while (*vgen == gen) {
+                if (*(volatile int *)status != 0) {
+                    ok = 0;
+                    break;
+                }
+                if (global_ns() - t0 > timeout_ns) {
+                    atomicCAS(status, 0, LBM_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(128);
+            }
+        }
+        __threadfence();
+        if (*(volatile int *)status != 0) ok = 0;
+        ok_sh = ok;
+    }
+    __syncthreads();
+    return ok_sh != 0;
+}
+
+template <int S, int V>
+__device__ __forceinline__ void do_tile(const GridDesc &g, int par, const Tile &t) {
+    Walker<S, V, LD_CG> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P, t.x0);
+    w.run(t.y0, t.y1, g.c);
+}
+
+__global__ void __launch_bounds__(32 * kBatchWarps, 2)
+    k_batch(const GridDesc *__restrict__ grids, const Tile *__restrict__ tiles, int ntiles,
+            const long long *__restrict__ limit, const int *__restrict__ parity0,
+            long long nsteps, unsigned *bar, int *status, unsigned long long timeout_ns) {
+    const int wpb = blockDim.x >> 5;
+    const int nwarps = gridDim.x * wpb;
+    const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+    for (long long k = 0; k < nsteps; ++k) {
+        for (int ti = gw; ti < ntiles; ti += nwarps) {
+            const Tile t = tiles[ti];
+            if (k >= limit[t.grid]) continue;
+            const GridDesc &g = grids[t.grid];
+            const int par = (parity0[t.grid] + (int)(k & 1)) & 1;
+            switch (g.kind) {
+                case ST_F32 * 16 + 1:
+                    do_tile<ST_F32, 1>(g, par, t);
+                    break;
+                case ST_F32 * 16 + 2:
+                    do_tile<ST_F32, 2>(g, par, t);
+                    break;
+                case ST_F32 * 16 + 4:
+                    do_tile<ST_F32, 4>(g, par, t);
+                    break;
+                case ST_F16 * 16 + 1:
+                    do_tile<ST_F16, 1>(g, par, t);
+                    break;
+                case ST_F16 * 16 + 2:
+                    do_tile<ST_F16, 2>(g, par, t);
+                    break;
+                case ST_F16 * 16 + 4:
+                    do_tile<ST_F16, 4>(g, par, t);
+                    break;
+                case ST_BF16 * 16 + 1:
+                    do_tile<ST_BF16, 1>(g, par, t);
+                    break;
+                case ST_BF16 * 16 + 2:
+                    do_tile<ST_BF16, 2>(g, par, t);
+                    break;
+                case ST_BF16 * 16 + 4:
+                    do_tile<ST_BF16, 4>(g, par, t);
+                    break;
+                default:
+                    break;
+            }
+        }
+        if (k + 1 < nsteps && !grid_barrier(bar, status, timeout_ns)) return;
+    }
+}
+
+}  // namespace
+
+struct lbm_batch {
+    std::vector<lbm_grid *> grids;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int rows = 16;
+    int blocks_per_sm = 0;  // 0: the occupancy limit
+    int max_blocks_per_sm = 1;
+    int sms = 1;
+    unsigned long long timeout_ns = 1000000000ULL;
+    // device
+    GridDesc *d_grids = nullptr;
+    Tile *d_tiles = nullptr;
+    int ntiles = 0;
+    long long *d_limit = nullptr;
+    int *d_parity = nullptr;
+    unsigned *d_bar = nullptr;
+    int *d_status = nullptr;
+    // pinned host mirrors of the per-call arrays
+    long long *h_limit = nullptr;
+    int *h_parity = nullptr;
+    int *h_status = nullptr;
+    cudaEvent_t copied = nullptr;  // the per-call arrays have been read
+    // graph cache (one step count)
+    cudaGraphExec_t graph = nullptr;
+    long long graph_n = -1;
+    bool use_graph = true;
+};
+
+static int bfail(int code, const std::string &m) {
+    set_error(m);
+    return code;
+}
+
+static int bcuda(cudaError_t e, const char *where) {
+    set_error(std::string(where) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+}
+
+#define BCK(call)                                           \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return bcuda(e_, #call);     \
+    } while (0)
+
+static void drop_graph(lbm_batch *b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_n = -1;
+}
+
+static int batch_vec(const lbm_grid *g) {
+    int v = std::min(g->cfg.vec, 4);
+    while (v > 1 && !valid_vec(g->storage, g->nx, v)) v /= 2;
+    return v;
+}
+
+// (Re)builds the device grid table and the tile work-list.
+static int build_worklist(lbm_batch *b) {
+    std::vector<GridDesc> gd(b->grids.size());
+    std::vector<Tile> tiles;
+    for (size_t k = 0; k < b->grids.size(); ++k) {
+        lbm_grid *g = b->grids[k];
+        GridDesc &d = gd[k];
+        d.buf[0] = g->buf[0];
+        d.buf[1] = g->buf[1];
+        d.P = g->P;
+        d.nx = g->nx;
+        d.ny = g->ny;
+        int v = batch_vec(g);
+        d.kind = g->storage * 16 + v;
+        d.pad = 0;
+        d.c = g->coef;
+        int w = 32 * v;
+        for (int y0 = 0; y0 < g->ny; y0 += b->rows)
+            for (int x0 = 0; x0 < g->nx; x0 += w)
+                tiles.push_back(Tile{(int)k, x0, y0, std::min(g->ny, y0 + b->rows)});
+    }
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    b->d_tiles = nullptr;
+    BCK(cudaMalloc(&b->d_tiles, sizeof(Tile) * std::max<size_t>(1, tiles.size())));
+    BCK(cudaMemcpy(b->d_grids, gd.data(), sizeof(GridDesc) * gd.size(), cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(b->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice));
+    b->ntiles = (int)tiles.size();
+    drop_graph(b);
+    return LBM_OK;
+}
+
+extern "C" int lbm_batch_destroy(lbm_batch_t b) {
+    if (!b) return LBM_OK;
+    if (b->stream || b->d_grids) cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    cudaFree(b->d_grids);
+    cudaFree(b->d_tiles);
+    cudaFree(b->d_limit);
+    cudaFree(b->d_parity);
+    cudaFree(b->d_bar);
+    cudaFree(b->d_status);
+    if (b->h_limit) cudaFreeHost(b->h_limit);
+    if (b->h_parity) cudaFreeHost(b->h_parity);
+    if (b->h_status) cudaFreeHost(b->h_status);
+    if (b->copied) cudaEventDestroy(b->copied);
+    delete b;
+    return LBM_OK;
+}
+
+extern "C" int lbm_batch_create(const lbm_t *grids, int n, lbm_batch_t *out) {
+    if (!out || !grids || n < 1) return bfail(LBM_EINVAL, "lbm_batch_create: bad argument");
+    *out = nullptr;
+    for (int k = 0; k < n; ++k)
+        if (!grids[k]) return bfail(LBM_EINVAL, "lbm_batch_create: NULL grid");
+    lbm_batch *b = new (std::nothrow) lbm_batch();
+    if (!b) return bfail(LBM_ENOMEM, "lbm_batch_create: host allocation failed");
+    b->grids.assign(grids, grids + n);
+    b->stream = grids[0]->stream;
+    b->device = grids[0]->device;
+    for (int k = 0; k < n; ++k)
+        if (grids[k]->device != b->device) {
+            delete b;
+            return bfail(LBM_EINVAL, "lbm_batch_create: grids on different devices");
+        }
+    cudaError_t e = cudaSuccess;
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, b->device);
+    if (e == cudaSuccess) {
+        b->sms = prop.multiProcessorCount;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->max_blocks_per_sm, k_batch,
+                                                          32 * kBatchWarps, 0);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_grids, sizeof(GridDesc) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_limit, sizeof(long long) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_parity, sizeof(int) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_bar, sizeof(unsigned) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_limit, sizeof(long long) * n);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_parity, sizeof(int) * n);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        int rc = bcuda(e, "lbm_batch_create");
+        lbm_batch_destroy(b);
+        return rc;
+    }
+    if (b->max_blocks_per_sm < 1) {
+        lbm_batch_destroy(b);
+        return bfail(LBM_ECUDA, "lbm_batch_create: batch kernel cannot be resident");
+    }
+    int rc = build_worklist(b);
+    if (rc != LBM_OK) {
+        lbm_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+static int grid_blocks(const lbm_batch *b) {
+    int per = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, b->max_blocks_per_sm)
+                                   : b->max_blocks_per_sm;
+    return per * b->sms;
+}
+
+// Queues: copy per-call arrays, reset barrier and status, cooperative launch.
+static cudaError_t enqueue(lbm_batch *b, long long n, cudaStream_t st) {
+    int ng = (int)b->grids.size();
+    cudaError_t e = cudaMemcpyAsync(b->d_limit, b->h_limit, sizeof(long long) * ng,
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_parity, b->h_parity, sizeof(int) * ng, cudaMemcpyHostToDevice,
+                            st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned) * 2, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    const GridDesc *grids = b->d_grids;
+    const Tile *tiles = b->d_tiles;
+    int ntiles = b->ntiles;
+    const long long *lim = b->d_limit;
+    const int *par = b->d_parity;
+    unsigned *bar = b->d_bar;
+    int *status = b->d_status;
+    unsigned long long to = b->timeout_ns;
+    void *args[] = {(void *)&grids, (void *)&tiles, (void *)&ntiles, (void *)&lim,
+                    (void *)&par,   (void *)&n,     (void *)&bar,    (void *)&status,
+                    (void *)&to};
+    return cudaLaunchCooperativeKernel((const void *)k_batch, dim3(grid_blocks(b)),
+                                       dim3(32 * kBatchWarps), args, 0, st);
+}
+
+static int run_batch(lbm_batch *b, long long n, const long long *limits, bool advance) {
+    int ng = (int)b->grids.size();
+    // The previous call's copies must have read the pinned arrays first.
+    BCK(cudaEventSynchronize(b->copied));
+    for (int k = 0; k < ng; ++k) {
+        long long lim = limits ? std::max(0LL, std::min(n, limits[k])) : n;
+        b->h_limit[k] = lim;
+        b->h_parity[k] = b->grids[k]->cur;
+    }
+    cudaError_t e = cudaSuccess;
+    if (b->use_graph) {
+        if (b->graph_n != n) {
+            drop_graph(b);
+            cudaStream_t cs;
+            BCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t e1 = enqueue(b, n, cs);
+                cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+                e = e1 != cudaSuccess ? e1 : e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+            if (g) cudaGraphDestroy(g);
+            cudaStreamDestroy(cs);
+            if (e != cudaSuccess) {
+                // Cooperative launches that cannot be captured run directly.
+                cudaGetLastError();
+                b->use_graph = false;
+                drop_graph(b);
+            } else {
+                b->graph_n = n;
+            }
+        }
+        if (b->use_graph) e = cudaGraphLaunch(b->graph, b->stream);
+    }
+    if (!b->use_graph) e = enqueue(b, n, b->stream);
+    if (e != cudaSuccess) return bcuda(e, "lbm_batch_step launch");
+    BCK(cudaEventRecord(b->copied, b->stream));
+    if (advance) {
+        for (int k = 0; k < ng; ++k) {
+            long long s = b->h_limit[k];
+            b->grids[k]->t += s;
+            if (s & 1) b->grids[k]->cur ^= 1;
+        }
+    }
+    return LBM_OK;
+}
+
+extern "C" int lbm_batch_step(lbm_batch_t b, long long n, const long long *limits) {
+    if (!b || n < 0) return bfail(LBM_EINVAL, "lbm_batch_step: bad argument");
+    if (n == 0) return LBM_OK;
+    return run_batch(b, n, limits, true);
+}
+
+extern "C" int lbm_batch_sync(lbm_batch_t b) {
+    if (!b) return bfail(LBM_EINVAL, "lbm_batch_sync: NULL batch");
+    BCK(cudaMemcpyAsync(b->h_status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost,
+                        b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    if (*b->h_status != 0)
+        return bfail(*b->h_status, "lbm_batch_sync: a barrier wait in the batch kernel ran out");
+    return LBM_OK;
+}
+
+extern "C" int lbm_batch_set_config(lbm_batch_t b, int rows, int blocks_per_sm) {
+    if (!b || rows < 1 || rows > 4096 || blocks_per_sm < 0)
+        return bfail(LBM_EINVAL, "lbm_batch_set_config: bad argument");
+    BCK(cudaStreamSynchronize(b->stream));
+    b->blocks_per_sm = blocks_per_sm;
+    if (rows != b->rows) {
+        b->rows = rows;
+        return build_worklist(b);
+    }
+    drop_graph(b);
+    return LBM_OK;
+}
+
+extern "C" int lbm_batch_set_timeout_us(lbm_batch_t b, long long us) {
+    if (!b || us < 1) return bfail(LBM_EINVAL, "lbm_batch_set_timeout_us: bad argument");
+    b->timeout_ns = (unsigned long long)us * 1000ULL;
+    drop_graph(b);
+    return LBM_OK;
+}
+
+// Times one-step dry runs (the state is not advanced: every grid writes its
+// other buffer) for a few tile heights and occupancies; keeps the fastest.
+extern "C" int lbm_batch_tune(lbm_batch_t b) {
+    if (!b) return bfail(LBM_EINVAL, "lbm_batch_tune: NULL batch");
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    int best_rows = b->rows, best_bps = b->blocks_per_sm;
+    float best = 1e30f;
+    const int rowss[] = {8, 16, 32, 64};
+    for (int r : rowss) {
+        for (int bps = 1; bps <= b->max_blocks_per_sm; bps *= 2) {
+            int rc = lbm_batch_set_config(b, r, bps);
+            if (rc != LBM_OK) return rc;
+            rc = run_batch(b, 1, nullptr, false);  // warm-up (and graph build)
+            if (rc != LBM_OK) return rc;
+            BCK(cudaEventRecord(e0, b->stream));
+            for (int k = 0; k < 3 && rc == LBM_OK; ++k) rc = run_batch(b, 1, nullptr, false);
+            if (rc != LBM_OK) return rc;
+            BCK(cudaEventRecord(e1, b->stream));
+            BCK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            BCK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                best_rows = r;
+                best_bps = bps;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return lbm_batch_set_config(b, best_rows, best_bps);
+}

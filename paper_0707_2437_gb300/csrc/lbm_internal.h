@@ -1,0 +1,91 @@
+// Host-side internals of liblbm.so shared by its translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "lbm_device.cuh"
+
+namespace vss {
+
+// Status of a launch helper: cudaSuccess or the CUDA error.
+using Err = cudaError_t;
+
+struct TileCfg {
+    int vec = 4;    // sites per lane
+    int rows = 16;  // rows per warp strip
+    int warps = 4;  // warps per block
+};
+
+struct StepGeom {
+    int nstrips, nsegs;
+    long long ntiles;
+};
+
+inline StepGeom step_geom(int nx, int ny, const TileCfg &c) {
+    StepGeom g;
+    int w = 32 * c.vec;
+    g.nstrips = (nx + w - 1) / w;
+    g.nsegs = (ny + c.rows - 1) / c.rows;
+    g.ntiles = (long long)g.nstrips * g.nsegs;
+    return g;
+}
+
+// Element size in bytes of a storage kind.
+inline int elem_bytes(int storage) { return storage == ST_F32 ? 4 : 2; }
+
+// Plane stride in elements: nx*ny rounded up to 64 elements.
+inline size_t plane_elems(int nx, int ny) {
+    size_t n = (size_t)nx * (size_t)ny;
+    return (n + 63) / 64 * 64;
+}
+
+Coef make_coef(double tau, double c2, double rho0);
+
+// Kernel launchers (lbm_kernels.cu).  All asynchronous on `st`.
+Err launch_step(int storage, const TileCfg &cfg, const void *fin, void *fout, int nx, int ny,
+                size_t P, const Coef &c, cudaStream_t st);
+Err launch_init(int storage, void *f, int nx, int ny, size_t P, double rho0, const double *rho,
+                const double *ux, const double *uy, cudaStream_t st);
+Err launch_moments(int storage, const void *f, int nx, int ny, size_t P, double rho0, double *rho,
+                   double *ux, double *uy, cudaStream_t st);
+// FP64 reductions: `partials` holds at least reduce_partials_needed() doubles
+// per output; `out` (device) receives the result values.
+int reduce_blocks(int nx, int ny);
+Err launch_sums(int storage, const void *f, int nx, int ny, size_t P, double *partials,
+                double *out3, cudaStream_t st);
+Err launch_mode(int storage, const void *f, int nx, int ny, size_t P, double rho0, int field,
+                int kx, int ky, double *partials, double *out2, cudaStream_t st);
+
+bool valid_vec(int storage, int nx, int vec);
+
+void set_error(const std::string &msg);
+
+}  // namespace vss
+
+// A grid handle (the opaque lbm_t of lbm.h).
+struct lbm_grid {
+    int nx = 0, ny = 0, storage = 0;
+    double tau = 0, c2 = 0, rho0 = 1;
+    size_t P = 0;                 // plane stride (elements)
+    void *buf[2] = {nullptr, nullptr};
+    int cur = 0;                  // buf[cur] holds the state
+    long long t = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    vss::Coef coef{};
+    vss::TileCfg cfg{};
+    double *scratch = nullptr;    // reduction partials + results
+    double *host_out = nullptr;   // pinned, 8 doubles
+    // CUDA graphs of 2*graph_pairs steps starting from buffer 0 or buffer 1
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_pairs = 0;
+    // timing
+    bool timing = false;
+    double kernel_ms = 0;
+    long long kernel_launches = 0;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+};

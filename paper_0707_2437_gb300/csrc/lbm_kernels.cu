@@ -1,0 +1,326 @@
+// Kernels of liblbm.so: the fused step, equilibrium initialisation, moments,
+// and the FP64 reductions (grid totals and Fourier coefficients).
+#include <math.h>
+
+#include "lbm_internal.h"
+
+namespace vss {
+
+Coef make_coef(double tau, double c2, double rho0) {
+    Coef c;
+    double om = 1.0 / tau;
+    double alpha = 1.0 / 3.0 - c2;  // Section 3, Eq. 8 with c_1^2 = 1/3
+    c.om = (float)om;
+    c.om1 = (float)(1.0 - om);
+    c.w3 = (float)(3.0 * om);
+    c.w45 = (float)(4.5 * om);
+    c.a15 = (float)(1.5 * alpha);
+    c.rho0 = (float)rho0;
+    return c;
+}
+
+bool valid_vec(int storage, int nx, int vec) {
+    if (vec != 1 && vec != 2 && vec != 4 && vec != 8) return false;
+    if (vec == 8 && storage == ST_F32) return false;
+    return nx % vec == 0;
+}
+
+// ---------------------------------------------------------------------------
+// Fused step: one warp per (strip, row segment) tile.
+
+template <int S, int V>
+__global__ void __launch_bounds__(256)
+    k_step(const void *__restrict__ fin, void *__restrict__ fout, int nx, int ny, size_t P,
+           int nstrips, long long ntiles, int rows, Coef c) {
+    long long tile = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (tile >= ntiles) return;  // whole warps leave together
+    int strip = (int)(tile % nstrips);
+    int seg = (int)(tile / nstrips);
+    int x0 = strip * 32 * V;
+    int y0 = seg * rows;
+    int y1 = min(ny, y0 + rows);
+    Walker<S, V> w(fin, fout, nx, ny, P, x0);
+    w.run(y0, y1, c);
+}
+
+template <int S, int V>
+static Err launch_step_t(const TileCfg &cfg, const void *fin, void *fout, int nx, int ny, size_t P,
+                         const Coef &c, cudaStream_t st) {
+    StepGeom g = step_geom(nx, ny, cfg);
+    long long blocks = (g.ntiles + cfg.warps - 1) / cfg.warps;
+    k_step<S, V><<<(unsigned)blocks, 32 * cfg.warps, 0, st>>>(fin, fout, nx, ny, P, g.nstrips,
+                                                             g.ntiles, cfg.rows, c);
+    return cudaGetLastError();
+}
+
+template <int S>
+static Err launch_step_s(const TileCfg &cfg, const void *fin, void *fout, int nx, int ny, size_t P,
+                         const Coef &c, cudaStream_t st) {
+    switch (cfg.vec) {
+        case 1:
+            return launch_step_t<S, 1>(cfg, fin, fout, nx, ny, P, c, st);
+        case 2:
+            return launch_step_t<S, 2>(cfg, fin, fout, nx, ny, P, c, st);
+        case 4:
+            return launch_step_t<S, 4>(cfg, fin, fout, nx, ny, P, c, st);
+        case 8:
+            if constexpr (S != ST_F32) return launch_step_t<S, 8>(cfg, fin, fout, nx, ny, P, c, st);
+            return cudaErrorInvalidValue;
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+Err launch_step(int storage, const TileCfg &cfg, const void *fin, void *fout, int nx, int ny,
+                size_t P, const Coef &c, cudaStream_t st) {
+    switch (storage) {
+        case ST_F32:
+            return launch_step_s<ST_F32>(cfg, fin, fout, nx, ny, P, c, st);
+        case ST_F16:
+            return launch_step_s<ST_F16>(cfg, fin, fout, nx, ny, P, c, st);
+        case ST_BF16:
+            return launch_step_s<ST_BF16>(cfg, fin, fout, nx, ny, P, c, st);
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Element conversions from / to double (not on the hot path).
+
+template <int S>
+__device__ __forceinline__ double ld_elem_d(const void *f, size_t idx) {
+    if constexpr (S == ST_F32)
+        return (double)reinterpret_cast<const float *>(f)[idx];
+    else if constexpr (S == ST_F16)
+        return (double)__half2float(reinterpret_cast<const __half *>(f)[idx]);
+    else
+        return (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(f)[idx]);
+}
+
+template <int S>
+__device__ __forceinline__ void st_elem_d(void *f, size_t idx, double v) {
+    if constexpr (S == ST_F32)
+        reinterpret_cast<float *>(f)[idx] = (float)v;
+    else if constexpr (S == ST_F16)
+        reinterpret_cast<__half *>(f)[idx] = __double2half(v);
+    else
+        reinterpret_cast<__nv_bfloat16 *>(f)[idx] = __double2bfloat16(v);
+}
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+// Weights and links in double for the FP64 side kernels.
+__device__ __forceinline__ double wd(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+// Equilibrium initialisation (Section 2, Eq. 2): the pre-collision value at
+// site x is plane i at x - e_i, so plane i at y holds the equilibrium of the
+// fields at y + e_i.  Stored as h_i = (fbar_i - w_i rho0)/w_i, computed in FP64.
+template <int S>
+__global__ void k_init(void *f, int nx, int ny, size_t P, double rho0, const double *rho,
+                       const double *ux, const double *uy) {
+    long long n = (long long)nx * ny;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (long long)gridDim.x * blockDim.x) {
+        int x = (int)(s % nx), y = (int)(s / nx);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            size_t src = (size_t)wrapi(y + EYi(i), ny) * nx + wrapi(x + EXi(i), nx);
+            double r = rho[src], u = ux[src], v = uy[src];
+            double eu = EXi(i) * u + EYi(i) * v;
+            double h = (r - rho0) + r * (3.0 * eu + 4.5 * eu * eu - 1.5 * (u * u + v * v));
+            st_elem_d<S>(f, (size_t)i * P + s, h);
+        }
+    }
+}
+
+// Moments (Section 2, Eq. 3) of the current state in FP64.
+template <int S>
+__device__ __forceinline__ void site_moments_d(const void *f, int nx, int ny, size_t P, int x,
+                                               int y, double rho0, double &dr, double &jx,
+                                               double &jy) {
+    dr = 0.0;
+    jx = 0.0;
+    jy = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        size_t src = (size_t)wrapi(y - EYi(i), ny) * nx + wrapi(x - EXi(i), nx);
+        double g = wd(i) * ld_elem_d<S>(f, (size_t)i * P + src);
+        dr += g;
+        jx += g * EXi(i);
+        jy += g * EYi(i);
+    }
+}
+
+template <int S>
+__global__ void k_moments(const void *f, int nx, int ny, size_t P, double rho0, double *rho,
+                          double *ux, double *uy) {
+    long long n = (long long)nx * ny;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (long long)gridDim.x * blockDim.x) {
+        int x = (int)(s % nx), y = (int)(s / nx);
+        double dr, jx, jy;
+        site_moments_d<S>(f, nx, ny, P, x, y, rho0, dr, jx, jy);
+        double r = rho0 + dr;
+        if (rho) rho[s] = r;
+        if (ux) ux[s] = jx / r;
+        if (uy) uy[s] = jy / r;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 reductions in a fixed order: RB blocks of RT threads; thread k of block
+// b takes sites b*RT + k, then + RB*RT, ...; each block sums its threads in a
+// fixed tree; a second one-block kernel sums the block partials in order.
+
+constexpr int RT = 256;
+constexpr int RB_MAX = 1024;
+
+int reduce_blocks(int nx, int ny) {
+    long long n = (long long)nx * ny;
+    long long b = (n + RT - 1) / RT;
+    return (int)(b < RB_MAX ? b : RB_MAX);
+}
+
+template <int K>
+__device__ __forceinline__ void block_sum_store(double (&v)[K], double *out_block) {
+    __shared__ double sh[K][RT];
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[k][threadIdx.x] = v[k];
+    __syncthreads();
+    for (int s = RT / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) out_block[k] = sh[k][0];
+    }
+}
+
+template <int K>
+__global__ void k_final(const double *partials, int nblocks, double *out) {
+    // One block: thread k sums partial k of every block in block order.
+    if (threadIdx.x < K) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks; ++b) s += partials[(size_t)b * K + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(RT)
+    k_sums(const void *f, int nx, int ny, size_t P, double *partials) {
+    long long n = (long long)nx * ny;
+    double v[3] = {0.0, 0.0, 0.0};
+    for (long long s = (long long)blockIdx.x * RT + threadIdx.x; s < n;
+         s += (long long)gridDim.x * RT) {
+        // Grid totals do not depend on streaming (each plane is permuted), so
+        // the stored planes are summed where they lie.
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            double g = wd(i) * ld_elem_d<S>(f, (size_t)i * P + s);
+            v[0] += g;
+            v[1] += g * EXi(i);
+            v[2] += g * EYi(i);
+        }
+    }
+    block_sum_store<3>(v, partials + (size_t)blockIdx.x * 3);
+}
+
+template <int S>
+__global__ void __launch_bounds__(RT)
+    k_mode(const void *f, int nx, int ny, size_t P, double rho0, int field, int kx, int ky,
+           double *partials) {
+    long long n = (long long)nx * ny;
+    double v[2] = {0.0, 0.0};
+    for (long long s = (long long)blockIdx.x * RT + threadIdx.x; s < n;
+         s += (long long)gridDim.x * RT) {
+        int x = (int)(s % nx), y = (int)(s / nx);
+        double dr, jx, jy;
+        site_moments_d<S>(f, nx, ny, P, x, y, rho0, dr, jx, jy);
+        double val = field == 0 ? dr : (field == 1 ? jx / (rho0 + dr) : jy / (rho0 + dr));
+        // Phase 2 pi (kx x / nx + ky y / ny), reduced exactly before scaling.
+        long long px = ((long long)kx * x) % nx;
+        long long py = ((long long)ky * y) % ny;
+        double ph = 2.0 * ((double)px / nx + (double)py / ny);
+        double sn, cs;
+        sincospi(ph, &sn, &cs);
+        v[0] += val * cs;
+        v[1] += val * sn;
+    }
+    block_sum_store<2>(v, partials + (size_t)blockIdx.x * 2);
+}
+
+__global__ void k_scale2(double *out, double s) {
+    if (threadIdx.x < 2) out[threadIdx.x] *= s;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+
+#define DISPATCH_S(storage, CALL)                  \
+    switch (storage) {                             \
+        case ST_F32: {                             \
+            constexpr int S_ = ST_F32;             \
+            CALL;                                  \
+        } break;                                   \
+        case ST_F16: {                             \
+            constexpr int S_ = ST_F16;             \
+            CALL;                                  \
+        } break;                                   \
+        case ST_BF16: {                            \
+            constexpr int S_ = ST_BF16;            \
+            CALL;                                  \
+        } break;                                   \
+        default:                                   \
+            return cudaErrorInvalidValue;          \
+    }
+
+static unsigned side_blocks(int nx, int ny) {
+    long long n = (long long)nx * ny;
+    long long b = (n + 255) / 256;
+    return (unsigned)(b < 4096 ? b : 4096);
+}
+
+Err launch_init(int storage, void *f, int nx, int ny, size_t P, double rho0, const double *rho,
+                const double *ux, const double *uy, cudaStream_t st) {
+    DISPATCH_S(storage, (k_init<S_><<<side_blocks(nx, ny), 256, 0, st>>>(f, nx, ny, P, rho0, rho,
+                                                                         ux, uy)));
+    return cudaGetLastError();
+}
+
+Err launch_moments(int storage, const void *f, int nx, int ny, size_t P, double rho0, double *rho,
+                   double *ux, double *uy, cudaStream_t st) {
+    DISPATCH_S(storage, (k_moments<S_><<<side_blocks(nx, ny), 256, 0, st>>>(f, nx, ny, P, rho0,
+                                                                            rho, ux, uy)));
+    return cudaGetLastError();
+}
+
+Err launch_sums(int storage, const void *f, int nx, int ny, size_t P, double *partials,
+                double *out3, cudaStream_t st) {
+    int nb = reduce_blocks(nx, ny);
+    DISPATCH_S(storage, (k_sums<S_><<<nb, RT, 0, st>>>(f, nx, ny, P, partials)));
+    k_final<3><<<1, 32, 0, st>>>(partials, nb, out3);
+    return cudaGetLastError();
+}
+
+Err launch_mode(int storage, const void *f, int nx, int ny, size_t P, double rho0, int field,
+                int kx, int ky, double *partials, double *out2, cudaStream_t st) {
+    int nb = reduce_blocks(nx, ny);
+    DISPATCH_S(storage,
+               (k_mode<S_><<<nb, RT, 0, st>>>(f, nx, ny, P, rho0, field, kx, ky, partials)));
+    k_final<2><<<1, 32, 0, st>>>(partials, nb, out2);
+    k_scale2<<<1, 32, 0, st>>>(out2, 2.0 / ((double)nx * ny));
+    return cudaGetLastError();
+}
+
+}  // namespace vss
