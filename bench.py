@@ -198,7 +198,7 @@ def run_native(args):
         raise SystemExit("bench.py: no CUDA device (the native path has no CPU fallback)")
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
-    runs = workloads.sweep_2048()
+    runs = workloads.sweep_2048()[:args.grids]
     storage = args.storage
     grids = []
     with torch.cuda.stream(stream):
@@ -260,10 +260,13 @@ def run_native(args):
     # pinned host fields, e2e_steps steps, lbm_moments back to pinned host
     # arrays, for all nine grids.
     n = runs[0].nx * runs[0].ny
-    host_in = [[torch.from_numpy(a).pin_memory() for a in workloads.acoustic_shear(r.nx, r.ny, r.amp)]
-               for r in runs]
+    if args.no_e2e:
+        args.e2e_jobs = 0
+    e2e_runs = runs if args.e2e_jobs else []
+    host_in = [[torch.from_numpy(a).pin_memory()
+                for a in workloads.acoustic_shear(r.nx, r.ny, r.amp)] for r in e2e_runs]
     host_out = [[torch.empty((r.ny, r.nx), dtype=torch.float64).pin_memory() for _ in range(3)]
-                for r in runs]
+                for r in e2e_runs]
 
     def job(steps):
         for g, hin, hout in zip(grids, host_in, host_out):
@@ -272,7 +275,8 @@ def run_native(args):
         for g, hout in zip(grids, host_out):
             g.moments(out=[t.numpy() for t in hout])
 
-    job(10)  # warm-up (graphs, allocator)
+    if args.e2e_jobs:
+        job(10)  # warm-up (graphs, allocator)
     barrier(ws)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -280,7 +284,8 @@ def run_native(args):
         job(args.e2e_steps)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(ws, time.perf_counter() - t0)
-    e2e_value = ws * sites * args.e2e_steps * args.e2e_jobs / e2e_s / 1e6
+    e2e_value = (ws * sites * args.e2e_steps * args.e2e_jobs / e2e_s / 1e6
+                 if args.e2e_jobs else None)
 
     line = {
         "metric": METRIC,
@@ -308,9 +313,10 @@ def run_native(args):
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "mean_launch_ms": per_launch_s * 1e3},
         "e2e": {"value": e2e_value, "unit": "MLUPS",
-                "h2d_bytes_per_step": 9 * 3 * n * 8, "d2h_bytes_per_step": 9 * 3 * n * 8,
+                "h2d_bytes_per_step": len(runs) * 3 * n * 8,
+                "d2h_bytes_per_step": len(runs) * 3 * n * 8,
                 "step": f"one job: lbm_init from pinned host fields, {args.e2e_steps} steps, "
-                        "lbm_moments to host, for all 9 grids",
+                        f"lbm_moments to host, for all {len(runs)} grids",
                 "jobs": args.e2e_jobs},
         "gpu_launches": args.steps * len(grids),
         "clocks": clk,
@@ -332,6 +338,9 @@ def main():
     ap.add_argument("--storage", default="f32", choices=list(BYTES_PER_LU))
     ap.add_argument("--config", type=int, nargs=3, default=None,
                     metavar=("VEC", "ROWS", "WARPS"))
+    ap.add_argument("--grids", type=int, default=9, choices=range(1, 10),
+                    help="use the first N of the nine 2048^2 runs (profiling)")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1000)
     ap.add_argument("--e2e-jobs", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
