@@ -201,6 +201,36 @@ int lbm_batch_tune(lbm_batch_t b);
 /* Barrier wait limit of the batch kernel in microseconds (default 1e6). */
 int lbm_batch_set_timeout_us(lbm_batch_t b, long long us);
 
+/* ---- Grid totals without allocation ------------------------------------- */
+
+/* The paper has no counterpart to this call; it is a service for callers that
+ * cannot allocate device memory at the point where they need the totals: code
+ * that runs inside its own memory pool or under an allocator that forbids
+ * outside cudaMalloc, code whose device memory is budgeted up front, or code
+ * that must not make an allocating CUDA call there.  It computes what
+ * lbm_sums computes, for a state buffer the caller already holds, and calls
+ * no cudaMalloc, cudaFree or other allocating routine.
+ *   f             device pointer to 9 planes of the stored distributions, plane
+ *                 i starting at element i * plane_stride (the checkpoint
+ *                 layout of lbm_get_state has plane_stride = nx * ny); element
+ *                 type per `storage`, h_i = (f_i - w_i rho0)/w_i
+ *   nx, ny        grid size, nx * ny <= 2^31 - 1 (larger grids: LBM_EINVAL)
+ *   plane_stride  elements between planes, >= nx * ny
+ *   storage       LBM_F32, LBM_F16D or LBM_BF16D; rho0 > 0 as at creation
+ *   cuda_stream   stream to run on (NULL: legacy default stream)
+ *   out3          host array receiving {mass, momentum_x, momentum_y}
+ * Scratch: a fixed 24.1 KiB array in the library's device memory (one partial
+ * triple for each of at most 1024 reduction blocks, plus the result), held on
+ * every GPU that loads the library until the process exits.  The first call on
+ * a device looks up that array's device address (once per device, with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the array and leave their values in it; each call writes every slot it
+ * reads, so nothing needs clearing, but calls that overlap on the GPU race and
+ * can return wrong totals.  Waits for the stream.  Returns LBM_OK,
+ * LBM_EINVAL, LBM_ECUDA or LBM_ENONFINITE. */
+int lbm_sums_noalloc(const void *f, int nx, int ny, size_t plane_stride,
+                     int storage, double rho0, void *cuda_stream, double *out3);
+
 /* ---- Errors --------------------------------------------------------------- */
 const char *lbm_strerror(int status);
 const char *lbm_last_error(void);

@@ -74,6 +74,7 @@ def load() -> ctypes.CDLL:
             "lbm_batch_set_config": ([vp, i, i], i),
             "lbm_batch_tune": ([vp], i),
             "lbm_batch_set_timeout_us": ([vp, ll], i),
+            "lbm_sums_noalloc": ([vp, i, i, sz, i, d, vp, dp], i),
             "lbm_strerror": ([i], ctypes.c_char_p),
             "lbm_last_error": ([], ctypes.c_char_p),
         }
@@ -117,6 +118,20 @@ def mem_info():
 
 def bytes_required(nx: int, ny: int, storage: str = "f32") -> int:
     return int(load().lbm_bytes_required(nx, ny, STORAGE[storage]))
+
+
+def sums_noalloc(f_dev_ptr: int, nx: int, ny: int, plane_stride: int, storage: str = "f32",
+                 rho0: float = 1.0, stream=None) -> np.ndarray:
+    """Grid totals {mass, momentum_x, momentum_y} of a state buffer already in
+    device memory, through lbm_sums_noalloc (no allocation by the library)."""
+    lib = load()
+    out = np.zeros(3)
+    _check(lib.lbm_sums_noalloc(ctypes.c_void_p(int(f_dev_ptr)), nx, ny, plane_stride,
+                                STORAGE[storage], rho0,
+                                ctypes.c_void_p(int(stream) if stream is not None else 0),
+                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+           "lbm_sums_noalloc")
+    return out
 
 
 class Grid:
