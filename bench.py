@@ -207,8 +207,11 @@ def run_native(args):
             g.init(*workloads.acoustic_shear(r.nx, r.ny, r.amp))
             if args.config:
                 g.set_config(*args.config)
+            if args.stages is not None:
+                g.set_pipeline(args.stages)
             grids.append(g)
     cfg = grids[0].get_config()
+    stages, pipelined = grids[0].get_pipeline()
     sites = sum(r.nx * r.ny for r in runs)
 
     def one_step():
@@ -302,14 +305,16 @@ def run_native(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grids": len(runs), "nx": runs[0].nx,
                    "ny": runs[0].ny, "storage": storage, "tile": {"vec": cfg[0],
-                   "rows": cfg[1], "warps": cfg[2]},
+                   "rows": cfg[1], "warps": cfg[2],
+                   "pipeline_stages": stages if pipelined else 0},
                    "l2": "inputs larger than L2 (2 x 151 MB per grid, 129 MB L2), no flush",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
-                     "kernel": f"k_step<{storage},vec={cfg[0]}>",
+                     "kernel": (f"k_step_tma<{storage},stages={stages}>" if pipelined
+                                else f"k_step<{storage},vec={cfg[0]}>"),
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "mean_launch_ms": per_launch_s * 1e3},
         "e2e": {"value": e2e_value, "unit": "MLUPS",
@@ -338,6 +343,8 @@ def main():
     ap.add_argument("--storage", default="f32", choices=list(BYTES_PER_LU))
     ap.add_argument("--config", type=int, nargs=3, default=None,
                     metavar=("VEC", "ROWS", "WARPS"))
+    ap.add_argument("--stages", type=int, default=None,
+                    help="row pipeline stages (0: register walk)")
     ap.add_argument("--grids", type=int, default=9, choices=range(1, 10),
                     help="use the first N of the nine 2048^2 runs (profiling)")
     ap.add_argument("--no-e2e", action="store_true")

@@ -160,6 +160,16 @@ int lbm_set_state(lbm_t h, const void *src_host, long long t);
 int lbm_set_config(lbm_t h, int vec, int rows, int warps);
 int lbm_get_config(lbm_t h, int *vec, int *rows, int *warps);
 
+/* Row pipeline of the step kernel.  stages = 2..4: each warp streams the rows
+ * it needs into that many shared-memory stages with asynchronous bulk copies
+ * (cp.async.bulk with mbarrier completion), which keeps stages - 1 rows of
+ * loads in flight per warp; used when vec is 4 (FP32) or 8 (16-bit), i.e. 16
+ * bytes of elements per lane.  stages = 0: the lanes load directly into
+ * registers.  Results are bitwise the same either way.  *active tells whether
+ * the pipeline is in use with the current vec. */
+int lbm_set_pipeline(lbm_t h, int stages);
+int lbm_get_pipeline(lbm_t h, int *stages, int *active);
+
 /* Autotuner: times the valid tile configurations on this grid (without
  * changing its state) and keeps the fastest.  If cache_path is not NULL the
  * choice is read from / stored in that JSON file, keyed by device, storage

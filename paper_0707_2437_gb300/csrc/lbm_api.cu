@@ -81,7 +81,23 @@ static TileCfg default_cfg(int storage, int nx, int ny) {
         }
     c.rows = 16;
     c.warps = 4;
+    c.stages = 0;  // register walk; the row pipeline is an autotuner option
     return c;
+}
+
+// Device status word written by kernels whose bounded waits ran out.
+static int *status_ptr(lbm_grid *h) { return reinterpret_cast<int *>(h->scratch + 8); }
+
+// Reads and clears the status word (the stream must be idle).
+static int take_status(lbm_grid *h) {
+    int st = 0;
+    cudaError_t e = cudaMemcpy(&st, status_ptr(h), sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (st != 0) {
+        cudaMemset(status_ptr(h), 0, sizeof(int));
+        return fail(st, "a bounded wait in the step kernel ran out");
+    }
+    return LBM_OK;
 }
 
 static void drop_graphs(lbm_grid *h) {
@@ -135,6 +151,8 @@ extern "C" int lbm_create_ex(int nx, int ny, double tau, double c2, double rho0,
     if (e == cudaSuccess) e = cudaMalloc(&h->buf[0], bytes);
     if (e == cudaSuccess) e = cudaMalloc(&h->buf[1], bytes);
     if (e == cudaSuccess) e = cudaMalloc(&h->scratch, sizeof(double) * (3 * 1024 + 16));
+    if (e == cudaSuccess) e = cudaMemset(h->scratch, 0, sizeof(double) * 16);
+    if (e == cudaSuccess) e = prepare_step(storage, h->cfg);
     if (e == cudaSuccess) e = cudaMallocHost(&h->host_out, sizeof(double) * 8);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev[1]);
@@ -207,7 +225,7 @@ extern "C" int lbm_init(lbm_t h, const double *rho, const double *ux, const doub
 // One step launch from buf[cur] to buf[cur ^ 1] (no bookkeeping).
 static cudaError_t launch_one(lbm_grid *h, int from) {
     return launch_step(h->storage, h->cfg, h->buf[from], h->buf[from ^ 1], h->nx, h->ny, h->P,
-                       h->coef, h->stream);
+                       h->coef, status_ptr(h), h->stream);
 }
 
 static const int kGraphPairs = 16;   // a graph holds 32 steps
@@ -223,7 +241,8 @@ static int build_graphs(lbm_grid *h) {
         if (e == cudaSuccess) {
             for (int k = 0; k < 2 * kGraphPairs && e == cudaSuccess; ++k)
                 e = launch_step(h->storage, h->cfg, h->buf[(start + k) & 1],
-                                h->buf[(start + k + 1) & 1], h->nx, h->ny, h->P, h->coef, cs);
+                                h->buf[(start + k + 1) & 1], h->nx, h->ny, h->P, h->coef,
+                                status_ptr(h), cs);
             cudaError_t e2 = cudaStreamEndCapture(cs, &g);
             if (e == cudaSuccess) e = e2;
         }
@@ -304,7 +323,7 @@ extern "C" int lbm_moments(lbm_t h, double *rho, double *ux, double *uy, int on_
                                        rho, ux, uy, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "lbm_moments kernel");
         CK(cudaStreamSynchronize(h->stream));
-        return LBM_OK;
+        return take_status(h);
     }
     double *d = nullptr;
     CK(cudaMallocAsync(&d, 3 * n * sizeof(double), h->stream));
@@ -321,7 +340,7 @@ extern "C" int lbm_moments(lbm_t h, double *rho, double *ux, double *uy, int on_
     cudaFreeAsync(d, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "lbm_moments");
     CK(cudaStreamSynchronize(h->stream));
-    return LBM_OK;
+    return take_status(h);
 }
 
 extern "C" int lbm_sums(lbm_t h, double *out3) {
@@ -333,6 +352,8 @@ extern "C" int lbm_sums(lbm_t h, double *out3) {
     CK(cudaMemcpyAsync(h->host_out, h->scratch, 3 * sizeof(double), cudaMemcpyDeviceToHost,
                        h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    int rs = take_status(h);
+    if (rs != LBM_OK) return rs;
     out3[0] = (double)h->nx * (double)h->ny * h->rho0 + h->host_out[0];
     out3[1] = h->host_out[1];
     out3[2] = h->host_out[2];
@@ -351,6 +372,8 @@ extern "C" int lbm_mode(lbm_t h, int field, int kx, int ky, double *out2) {
     CK(cudaMemcpyAsync(h->host_out, h->scratch, 2 * sizeof(double), cudaMemcpyDeviceToHost,
                        h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    int rs = take_status(h);
+    if (rs != LBM_OK) return rs;
     out2[0] = h->host_out[0];
     out2[1] = h->host_out[1];
     if (!isfinite(out2[0]) || !isfinite(out2[1]))
@@ -363,7 +386,7 @@ extern "C" long long lbm_time(lbm_t h) { return h ? h->t : -1; }
 extern "C" int lbm_sync(lbm_t h) {
     if (!h) return fail(LBM_EINVAL, "lbm_sync: NULL handle");
     CK(cudaStreamSynchronize(h->stream));
-    return LBM_OK;
+    return take_status(h);
 }
 
 // ---------------------------------------------------------------------------
@@ -381,7 +404,7 @@ extern "C" int lbm_get_state(lbm_t h, void *dst_host, long long *t) {
                          h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (t) *t = h->t;
-    return LBM_OK;
+    return take_status(h);
 }
 
 extern "C" int lbm_set_state(lbm_t h, const void *src_host, long long t) {
@@ -413,6 +436,27 @@ extern "C" int lbm_set_config(lbm_t h, int vec, int rows, int warps) {
     h->cfg.vec = vec;
     h->cfg.rows = rows;
     h->cfg.warps = warps;
+    CK(prepare_step(h->storage, h->cfg));
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_pipeline(lbm_t h, int stages) {
+    if (!h) return fail(LBM_EINVAL, "lbm_set_pipeline: NULL handle");
+    if (stages != 0 && (stages < 2 || stages > 4))
+        return fail(LBM_EINVAL, "lbm_set_pipeline: stages must be 0 or 2..4");
+    if (h->cfg.stages != stages) {
+        CK(cudaStreamSynchronize(h->stream));
+        drop_graphs(h);
+    }
+    h->cfg.stages = stages;
+    CK(prepare_step(h->storage, h->cfg));
+    return LBM_OK;
+}
+
+extern "C" int lbm_get_pipeline(lbm_t h, int *stages, int *active) {
+    if (!h) return fail(LBM_EINVAL, "lbm_get_pipeline: NULL handle");
+    if (stages) *stages = h->cfg.stages;
+    if (active) *active = uses_tma(h->storage, h->cfg) ? 1 : 0;
     return LBM_OK;
 }
 
@@ -433,7 +477,7 @@ static std::string tune_key(const lbm_grid *h) {
     return k.str();
 }
 
-// The cache file is a flat JSON object {"key": [vec, rows, warps], ...}.
+// The cache file is a flat JSON object {"key": [vec, rows, warps, stages], ...}.
 static std::map<std::string, TileCfg> read_cache(const char *path) {
     std::map<std::string, TileCfg> m;
     std::ifstream in(path);
@@ -449,8 +493,9 @@ static std::map<std::string, TileCfg> read_cache(const char *path) {
         size_t lb = s.find('[', end), rb = s.find(']', end);
         if (lb == std::string::npos || rb == std::string::npos) break;
         TileCfg c;
-        if (sscanf(s.c_str() + lb, "[%d , %d , %d]", &c.vec, &c.rows, &c.warps) == 3 ||
-            sscanf(s.c_str() + lb, "[%d,%d,%d]", &c.vec, &c.rows, &c.warps) == 3)
+        if (sscanf(s.c_str() + lb, "[%d , %d , %d , %d]", &c.vec, &c.rows, &c.warps, &c.stages) ==
+                4 ||
+            sscanf(s.c_str() + lb, "[%d,%d,%d,%d]", &c.vec, &c.rows, &c.warps, &c.stages) == 4)
             m[key] = c;
         pos = rb + 1;
     }
@@ -464,8 +509,8 @@ static void write_cache(const char *path, const std::map<std::string, TileCfg> &
     fprintf(f, "{\n");
     size_t k = 0;
     for (auto &kv : m) {
-        fprintf(f, "  \"%s\": [%d, %d, %d]%s\n", kv.first.c_str(), kv.second.vec, kv.second.rows,
-                kv.second.warps, (++k < m.size()) ? "," : "");
+        fprintf(f, "  \"%s\": [%d, %d, %d, %d]%s\n", kv.first.c_str(), kv.second.vec,
+                kv.second.rows, kv.second.warps, kv.second.stages, (++k < m.size()) ? "," : "");
     }
     fprintf(f, "}\n");
     fclose(f);
@@ -477,7 +522,8 @@ static void write_cache(const char *path, const std::map<std::string, TileCfg> &
 static int time_cfg(lbm_grid *h, const TileCfg &c, int reps, float *ms_out) {
     TileCfg saved = h->cfg;
     h->cfg = c;
-    cudaError_t e = launch_one(h, h->cur);  // warm-up
+    cudaError_t e = prepare_step(h->storage, c);
+    if (e == cudaSuccess) e = launch_one(h, h->cur);  // warm-up
     if (e == cudaSuccess) e = cudaEventRecord(h->ev[0], h->stream);
     for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_one(h, h->cur);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev[1], h->stream);
@@ -498,7 +544,9 @@ extern "C" int lbm_tune(lbm_t h, const char *cache_path) {
         cache = read_cache(cache_path);
         auto it = cache.find(key);
         if (it != cache.end() && valid_vec(h->storage, h->nx, it->second.vec)) {
-            return lbm_set_config(h, it->second.vec, it->second.rows, it->second.warps);
+            int rc = lbm_set_config(h, it->second.vec, it->second.rows, it->second.warps);
+            if (rc != LBM_OK) return rc;
+            return lbm_set_pipeline(h, it->second.stages);
         }
     }
     CK(cudaStreamSynchronize(h->stream));
@@ -514,21 +562,26 @@ extern "C" int lbm_tune(lbm_t h, const char *cache_path) {
         for (int r : rowss) {
             if (r > 2 * h->ny && r != 4) continue;
             for (int w : warpss) {
-                TileCfg c;
-                c.vec = v;
-                c.rows = r;
-                c.warps = w;
-                float ms;
-                int rc = time_cfg(h, c, reps, &ms);
-                if (rc != LBM_OK) return rc;
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best = c;
+                const int nst_max = (v == tma_vec(h->storage)) ? 4 : 0;
+                for (int nst = 0; nst <= nst_max; nst = (nst == 0 ? 2 : nst + 1)) {
+                    TileCfg c;
+                    c.vec = v;
+                    c.rows = r;
+                    c.warps = w;
+                    c.stages = nst;
+                    float ms;
+                    int rc = time_cfg(h, c, reps, &ms);
+                    if (rc != LBM_OK) return rc;
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best = c;
+                    }
                 }
             }
         }
     }
     int rc = lbm_set_config(h, best.vec, best.rows, best.warps);
+    if (rc == LBM_OK) rc = lbm_set_pipeline(h, best.stages);
     if (rc != LBM_OK) return rc;
     if (cache_path) {
         cache[key] = best;

@@ -32,7 +32,7 @@ struct GridDesc {
 };
 
 struct Tile {
-    int grid, x0, y0, y1;
+    int grid, x0, y0, y1, dir;
 };
 
 constexpr int kBatchWarps = 8;  // warps per block of the persistent kernel
@@ -85,7 +85,7 @@ __device__ bool grid_barrier(unsigned *bar, int *status, unsigned long long time
 template <int S, int V>
 __device__ __forceinline__ void do_tile(const GridDesc &g, int par, const Tile &t) {
     Walker<S, V, LD_CG> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P, t.x0);
-    w.run(t.y0, t.y1, g.c);
+    w.run(t.y0, t.y1, t.dir, g.c);
 }
 
 __global__ void __launch_bounds__(32 * kBatchWarps, 2)
@@ -212,9 +212,12 @@ static int build_worklist(lbm_batch *b) {
         d.pad = 0;
         d.c = g->coef;
         int w = 32 * v;
-        for (int y0 = 0; y0 < g->ny; y0 += b->rows)
+        // Neighbouring segments walk in opposite directions, so the rows they
+        // share are read by both at about the same time (from L2 the second time).
+        for (int y0 = 0, seg = 0; y0 < g->ny; y0 += b->rows, ++seg)
             for (int x0 = 0; x0 < g->nx; x0 += w)
-                tiles.push_back(Tile{(int)k, x0, y0, std::min(g->ny, y0 + b->rows)});
+                tiles.push_back(Tile{(int)k, x0, y0, std::min(g->ny, y0 + b->rows),
+                                     (seg & 1) ? -1 : 1});
     }
     if (b->d_tiles) cudaFree(b->d_tiles);
     b->d_tiles = nullptr;

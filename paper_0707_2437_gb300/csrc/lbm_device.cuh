@@ -33,6 +33,21 @@ namespace vss {
 
 enum Storage : int { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
 
+#ifdef VSS_BOUNDS_CHECK
+// Debug builds only: every global access of the walk checks its element
+// index against the buffer; a violation is counted (and its first index kept)
+// in this translation unit's record and the access is skipped.
+static __device__ unsigned long long vss_oob_record[2];
+__device__ __forceinline__ bool vss_in_bounds(size_t idx, size_t n, size_t lim) {
+    if (idx + n <= lim) return true;
+    if (atomicAdd(&vss_oob_record[0], 1ULL) == 0ULL) vss_oob_record[1] = idx;
+    return false;
+}
+#define VSS_IN_BOUNDS(idx, n, lim) vss_in_bounds((idx), (n), (lim))
+#else
+#define VSS_IN_BOUNDS(idx, n, lim) true
+#endif
+
 constexpr unsigned FULL = 0xffffffffu;
 
 // Link vectors of Section 2: e_1..4 along the axes, e_5..8 the diagonals.
@@ -188,6 +203,22 @@ __device__ __forceinline__ float get_elem(const uint32_t (&w)[Pack<S, V>::NW], i
     }
 }
 
+// Element v of a packed row set from a float (round to nearest even for the
+// 16-bit kinds; each element is rounded on its own).
+template <int S>
+__device__ __forceinline__ uint32_t pack1(float v);
+template <int S, int V>
+__device__ __forceinline__ void set_elem(uint32_t (&w)[Pack<S, V>::NW], int v, float x) {
+    if constexpr (S == ST_F32) {
+        w[v] = __float_as_uint(x);
+    } else if constexpr (V == 1) {
+        w[0] = pack1<S>(x);
+    } else {
+        const uint32_t b = pack1<S>(x);
+        w[v >> 1] = (v & 1) ? __byte_perm(w[v >> 1], b, 0x5410) : __byte_perm(w[v >> 1], b, 0x3254);
+    }
+}
+
 // Float pair to a packed word (round to nearest even).
 template <int S>
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
@@ -254,6 +285,15 @@ __device__ __forceinline__ float delta_rho(float h0, float h1, float h2, float h
     return __fmaf_rn(VSS_W0, h0, __fmaf_rn(VSS_W1, sa, __fmul_rn(VSS_W5, sd)));
 }
 
+// 1/x by the hardware reciprocal (rcp.approx.ftz.f32: about 1 ulp, one
+// instruction).  Only u = j/rho uses it; u is of the size of the wave's
+// velocity, so the absolute error stays near 1e-7 |u|.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Site quantities the nine outputs share.
 struct SiteQ {
     float jx, jy, ux, uy;  // momentum rho u and velocity u (Eq. 3)
@@ -270,7 +310,7 @@ __device__ __forceinline__ SiteQ site_quantities(float h1, float h2, float h3, f
     float b = __fsub_rn(h6, h8);  // e_6 = (-1, 1), e_8 = -e_6
     q.jx = __fmaf_rn(VSS_W1, __fsub_rn(h1, h3), __fmul_rn(VSS_W5, __fsub_rn(a, b)));
     q.jy = __fmaf_rn(VSS_W1, __fsub_rn(h2, h4), __fmul_rn(VSS_W5, __fadd_rn(a, b)));
-    float inv = __frcp_rn(__fadd_rn(c.rho0, dr));
+    float inv = rcp_approx(__fadd_rn(c.rho0, dr));
     q.ux = __fmul_rn(q.jx, inv);
     q.uy = __fmul_rn(q.jy, inv);
     float ju = __fmaf_rn(q.jx, q.ux, __fmul_rn(q.jy, q.uy));
@@ -315,10 +355,10 @@ struct Walker {
     T *__restrict__ fout;
     int nx, ny;
     size_t P;
-    int x0, nact, lane, xs;
+    int x0, wa, nact, lane, xs;
     bool act;
-    // helper lane
-    int gdir, gcol, gey;
+    // helper lane: direction, column offset from x0 (unwrapped), wrapped column
+    int gdir, goff, gcol, gey;
 
     __device__ __forceinline__ Walker(const void *fin_, void *fout_, int nx_, int ny_, size_t P_,
                                       int x0_)
@@ -329,30 +369,26 @@ struct Walker {
           P(P_),
           x0(x0_) {
         lane = threadIdx.x & 31;
-        int wa = min(32 * V, nx - x0);
+        wa = min(32 * V, nx - x0);
         nact = wa / V;
         act = lane < nact;
         xs = x0 + lane * V;
-        int xl = (x0 == 0) ? nx - 1 : x0 - 1;
-        int xr = (x0 + wa == nx) ? 0 : x0 + wa;
-        gdir = -1;
-        gcol = 0;
-        if (lane < 9) {
-            gdir = lane;
-            gcol = xl - EXi(lane);
-        } else if (lane < 12) {
-            gdir = (lane == 9) ? 1 : (lane == 10 ? 5 : 8);
-            gcol = xl;
-        } else if (lane >= 16 && lane < 25) {
-            gdir = lane - 16;
-            gcol = xr - EXi(gdir);
-        } else if (lane >= 25 && lane < 28) {
-            gdir = (lane == 25) ? 3 : (lane == 26 ? 6 : 7);
-            gcol = xr;
-        }
-        if (gcol < 0) gcol += nx;
-        if (gcol >= nx) gcol -= nx;
-        gey = gdir >= 0 ? EYi(gdir) : 0;
+        // Helper lane roles, read from packed per-lane tables without
+        // branches: direction (4 bits per lane) and kind (2 bits per lane).
+        //   kind 0: pulled f at the left halo site x0-1   (column x0-1-e_x)
+        //   kind 1: f at column x0-1 (left edge value; lanes without a
+        //           role also take kind 1, direction 0, and ignore it)
+        //   kind 2: pulled f at the right halo site x0+wa (column x0+wa-e_x)
+        //   kind 3: f at column x0+wa (right edge value)
+        const unsigned long long dir_tab = (lane < 16) ? 0x851876543210ULL : 0x763876543210ULL;
+        gdir = (int)((dir_tab >> (4 * (lane & 15))) & 15ULL);
+        const int kind = (int)((0x55feaaaa55540000ULL >> (2 * lane)) & 3ULL);
+        const int ex = (int)((0x20919u >> (2 * gdir)) & 3u) - 1;  // e_x of gdir
+        const int base = (kind < 2) ? -1 : wa;
+        goff = base - (((kind & 1) == 0) ? ex : 0);
+        gcol = ((x0 + goff) % nx + nx) % nx;
+        gey = (int)((0x2865u >> (2 * gdir)) & 3u) - 1;  // e_y of gdir
+        __syncwarp();
     }
 
     // Pulls row q (source rows qm = q-1, q0 = q, qp = q+1, already wrapped):
@@ -361,21 +397,32 @@ struct Walker {
     __device__ __forceinline__ void pull_row(int qm, int q0, int qp, uint32_t (&w)[9][NW],
                                              float (&d)[V], float &dl, float &dr) const {
         // Source row of direction i is q - e_y(i).
+        // Lanes past the end of a partial strip load the strip's first
+        // elements instead (unused), so that every lane issues the same loads.
+        const int xl = act ? xs : x0;
+        const size_t lim = 9 * P;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int sr = (EYi(i) > 0) ? qm : ((EYi(i) < 0) ? qp : q0);
-            if (act) {
-                load_words<S, V, LD>(fin + (size_t)i * P + (size_t)sr * nx + xs, w[i]);
+            const size_t idx = (size_t)i * P + (size_t)sr * nx + xl;
+            if (VSS_IN_BOUNDS(idx, V, lim)) {
+                load_words<S, V, LD>(fin + idx, w[i]);
             } else {
 #pragma unroll
                 for (int k = 0; k < NW; ++k) w[i][k] = 0u;
             }
         }
-        uint32_t g = 0u;
-        if (gdir >= 0) {
-            const int sr = (gey > 0) ? qm : ((gey < 0) ? qp : q0);
-            g = load_elem<S, LD>(fin + (size_t)gdir * P + (size_t)sr * nx + gcol);
-        }
+        const int gsr = (gey > 0) ? qm : ((gey < 0) ? qp : q0);
+        const size_t gidx = (size_t)gdir * P + (size_t)gsr * nx + gcol;
+        const uint32_t g = VSS_IN_BOUNDS(gidx, 1, lim) ? load_elem<S, LD>(fin + gidx) : 0u;
+        finish_pull(w, g, d, dl, dr);
+    }
+
+    // Shifts of the e_x = +-1 directions, drho of the lane's sites, and drho
+    // of the two halo sites, from the raw rows `w` and the helper value `g`.
+    __device__ __forceinline__ void finish_pull(uint32_t (&w)[9][NW], uint32_t g, float (&d)[V],
+                                                float &dl, float &dr) const {
+        __syncwarp();  // the exchanges below need every lane's loaded values
         // e_x = +1 directions take the left neighbour's last element.
         {
             uint32_t e1 = __shfl_sync(FULL, g, 9);
@@ -432,107 +479,379 @@ struct Walker {
         }
     }
 
-    // Collides row r (packed pulled values w, drho d of the row, du / dd of the
-    // rows above / below, dl / dr of the halo sites) and stores it.
-    __device__ __forceinline__ void collide_store(int r, const uint32_t (&w)[9][NW],
-                                                  const float (&d)[V], const float (&dym)[V],
-                                                  const float (&dyp)[V], float dl, float dr,
-                                                  const Coef &c) const {
+    // Collides row r and stores it.  w: the row's packed pulled values (the
+    // outputs are written back into it, site by site, and then stored); d:
+    // drho of the row; dym / dyp: drho of rows r-1 / r+1; dl / dr: drho of
+    // the halo sites left and right of the strip.
+    __device__ __forceinline__ void collide_store(int r, uint32_t (&w)[9][NW], const float (&d)[V],
+                                                  const float (&dym)[V], const float (&dyp)[V],
+                                                  float dl, float dr, const Coef &c) const {
         // x neighbours of drho: inside the lane, then the adjacent lanes, then
         // the halo sites at the strip edges.
         float lft = __shfl_up_sync(FULL, d[V - 1], 1);
         float rgt = __shfl_down_sync(FULL, d[0], 1);
         if (lane == 0) lft = dl;
         if (lane == nact - 1) rgt = dr;
-
-        SiteQ q[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            float dxm = (v == 0) ? lft : d[v - 1];
-            float dxp = (v == V - 1) ? rgt : d[v + 1];
-            q[v] = site_quantities(get_elem<S, V>(w[1], v), get_elem<S, V>(w[2], v),
-                                   get_elem<S, V>(w[3], v), get_elem<S, V>(w[4], v),
-                                   get_elem<S, V>(w[5], v), get_elem<S, V>(w[6], v),
-                                   get_elem<S, V>(w[7], v), get_elem<S, V>(w[8], v), d[v], dxm,
-                                   dxp, dym[v], dyp[v], c);
+            const float dxm = (v == 0) ? lft : d[v - 1];
+            const float dxp = (v == V - 1) ? rgt : d[v + 1];
+            float h[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) h[i] = get_elem<S, V>(w[i], v);
+            const SiteQ q = site_quantities(h[1], h[2], h[3], h[4], h[5], h[6], h[7], h[8], d[v],
+                                            dxm, dxp, dym[v], dyp[v], c);
+            float o[9];
+            o[0] = __fmaf_rn(c.om1, h[0], q.wB);                            // rest
+            pair_out(h[1], h[3], q.jx, q.ux, q.Ax, q.wB, c, o[1], o[3]);  // e = (1, 0)
+            pair_out(h[2], h[4], q.jy, q.uy, q.Ay, q.wB, c, o[2], o[4]);  // e = (0, 1)
+            pair_out(h[5], h[7], __fadd_rn(q.jx, q.jy), __fadd_rn(q.ux, q.uy),
+                     __fadd_rn(q.Ax, q.Ay), q.wB, c, o[5], o[7]);  // e = (1, 1)
+            pair_out(h[6], h[8], __fsub_rn(q.jy, q.jx), __fsub_rn(q.uy, q.ux),
+                     __fsub_rn(q.Ay, q.Ax), q.wB, c, o[6], o[8]);  // e = (-1, 1)
+#pragma unroll
+            for (int i = 0; i < 9; ++i) set_elem<S, V>(w[i], v, o[i]);
         }
-        const size_t row = (size_t)r * nx + xs;
-        float o0[V], oa[V], ob[V];
-        // Direction 0 (rest).
-#pragma unroll
-        for (int v = 0; v < V; ++v) o0[v] = __fmaf_rn(c.om1, get_elem<S, V>(w[0], v), q[v].wB);
-        store_dir(0, row, o0);
-        // (1, 3): e = (1, 0).
-#pragma unroll
-        for (int v = 0; v < V; ++v)
-            pair_out(get_elem<S, V>(w[1], v), get_elem<S, V>(w[3], v), q[v].jx, q[v].ux, q[v].Ax,
-                     q[v].wB, c, oa[v], ob[v]);
-        store_dir(1, row, oa);
-        store_dir(3, row, ob);
-        // (2, 4): e = (0, 1).
-#pragma unroll
-        for (int v = 0; v < V; ++v)
-            pair_out(get_elem<S, V>(w[2], v), get_elem<S, V>(w[4], v), q[v].jy, q[v].uy, q[v].Ay,
-                     q[v].wB, c, oa[v], ob[v]);
-        store_dir(2, row, oa);
-        store_dir(4, row, ob);
-        // (5, 7): e = (1, 1).
-#pragma unroll
-        for (int v = 0; v < V; ++v)
-            pair_out(get_elem<S, V>(w[5], v), get_elem<S, V>(w[7], v),
-                     __fadd_rn(q[v].jx, q[v].jy), __fadd_rn(q[v].ux, q[v].uy),
-                     __fadd_rn(q[v].Ax, q[v].Ay), q[v].wB, c, oa[v], ob[v]);
-        store_dir(5, row, oa);
-        store_dir(7, row, ob);
-        // (6, 8): e = (-1, 1).
-#pragma unroll
-        for (int v = 0; v < V; ++v)
-            pair_out(get_elem<S, V>(w[6], v), get_elem<S, V>(w[8], v),
-                     __fsub_rn(q[v].jy, q[v].jx), __fsub_rn(q[v].uy, q[v].ux),
-                     __fsub_rn(q[v].Ay, q[v].Ax), q[v].wB, c, oa[v], ob[v]);
-        store_dir(6, row, oa);
-        store_dir(8, row, ob);
-    }
-
-    __device__ __forceinline__ void store_dir(int i, size_t row, const float (&o)[V]) const {
         if (!act) return;
-        uint32_t pw[NW];
-        if constexpr (S == ST_F32 || V == 1) {
+        const size_t row = (size_t)r * nx + xs;
 #pragma unroll
-            for (int v = 0; v < V; ++v) pw[v] = pack1<S>(o[v]);
-        } else {
-#pragma unroll
-            for (int k = 0; k < NW; ++k) pw[k] = pack2<S>(o[2 * k], o[2 * k + 1]);
+        for (int i = 0; i < 9; ++i) {
+            const size_t idx = (size_t)i * P + row;
+            if (VSS_IN_BOUNDS(idx, V, 9 * P)) store_words<S, V>(fout + idx, w[i]);
         }
-        store_words<S, V>(fout + (size_t)i * P + row, pw);
     }
 
-    // Advances rows y0 .. y1-1 (0 <= y0 < y1 <= ny) by one step.
-    __device__ __forceinline__ void run(int y0, int y1, const Coef &c) const {
-        // Pulled-row cursor: q and its source rows q-1, q+1, all wrapped.
-        int q0 = (y0 == 0) ? ny - 1 : y0 - 1;
+    // Advances rows y0 .. y1-1 (0 <= y0 < y1 <= ny) by one step, walking
+    // down (dir = +1, rows in increasing y) or up (dir = -1).  The direction
+    // changes only the order of the rows, not any result.  The walk pulls
+    // n + 2 rows (one beyond each end of the segment, for drho only) and
+    // collides the row before the one just pulled.
+    __device__ __forceinline__ void run(int y0, int y1, int dir, const Coef &c) const {
+        // Pulled-row cursor q and its source rows q-1, q+1, all wrapped.
+        int q0 = dir > 0 ? ((y0 == 0) ? ny - 1 : y0 - 1) : (y1 == ny ? 0 : y1);
         int qm = (q0 == 0) ? ny - 1 : q0 - 1;
         int qp = (q0 + 1 == ny) ? 0 : q0 + 1;
 
         uint32_t wc[9][NW], wn[9][NW];
-        float dprev[V], dcur[V], dnext[V];
-        float dlc, drc, dln, drn;
-
-        pull_row(qm, q0, qp, wn, dprev, dln, drn);  // row y0 - 1: drho only
-        qm = q0;
-        q0 = qp;
-        qp = (qp + 1 == ny) ? 0 : qp + 1;
-        pull_row(qm, q0, qp, wc, dcur, dlc, drc);  // row y0
-        for (int r = y0; r < y1; ++r) {
-            qm = q0;
-            q0 = qp;
-            qp = (qp + 1 == ny) ? 0 : qp + 1;
-            pull_row(qm, q0, qp, wn, dnext, dln, drn);  // row r + 1
-            collide_store(r, wc, dcur, dprev, dnext, dlc, drc, c);
+        float d2[V], d1[V], d0[V];  // drho of the rows pulled two, one and zero pulls ago
+        float l1 = 0.f, r1 = 0.f, l0, r0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            d2[v] = 0.f;
+            d1[v] = 0.f;
+        }
+        const int n = y1 - y0;
+        for (int k = 0; k < n + 2; ++k) {
+            pull_row(qm, q0, qp, wn, d0, l0, r0);
+            if (k >= 2) {
+                const int r = dir > 0 ? y0 + (k - 2) : y1 - 1 - (k - 2);
+                if (dir > 0)
+                    collide_store(r, wc, d1, d2, d0, l1, r1, c);
+                else
+                    collide_store(r, wc, d1, d0, d2, l1, r1, c);
+            }
 #pragma unroll
             for (int i = 0; i < 9; ++i)
 #pragma unroll
-                for (int k = 0; k < NW; ++k) wc[i][k] = wn[i][k];
+                for (int kk = 0; kk < NW; ++kk) wc[i][kk] = wn[i][kk];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                d2[v] = d1[v];
+                d1[v] = d0[v];
+            }
+            l1 = l0;
+            r1 = r0;
+            advance(qm, q0, qp, dir);
+        }
+    }
+
+    __device__ __forceinline__ void advance(int &qm, int &q0, int &qp, int dir) const {
+        if (dir > 0) {
+            qm = q0;
+            q0 = qp;
+            qp = (qp + 1 == ny) ? 0 : qp + 1;
+        } else {
+            qp = q0;
+            q0 = qm;
+            qm = (qm == 0) ? ny - 1 : qm - 1;
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Asynchronous row pipeline.  Each warp streams the rows its walk needs into a
+// ring of NST shared-memory stages with bulk copies (cp.async.bulk, the TMA
+// engine, no tensor map: every stage row is one to three contiguous pieces of
+// a plane row), one mbarrier per stage.  A stage row holds the strip's columns
+// plus PAD = 16 bytes of elements on each side (x0-PAD .. x0+wa+PAD-1, wrapped),
+// which covers the shifted pulls and both halo sites, so all reads of a row
+// come from shared memory.  The warp keeps NST-1 rows in flight ahead of the
+// row it is pulling: the loads no longer wait in registers, and the number of
+// bytes in flight is set by the stage count instead of by occupancy.  The
+// arithmetic is the Walker's (finish_pull, collide_store): results are bitwise
+// the same as the register walk.
+
+constexpr int STATUS_TIMEOUT = -5;  // written to the status word when a wait runs out
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint32_t bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                              uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// Waits for phase `parity` of barrier `bar` with a wall-clock limit; every
+// lane polls, and the warp agrees on the outcome.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  unsigned long long limit_ns) {
+    bool ok = mbar_try_wait(bar, parity);
+    if (!__all_sync(FULL, ok)) {
+        const unsigned long long t0 = globaltimer_ns();
+        while (!ok) {
+            ok = mbar_try_wait(bar, parity);
+            if (!ok && globaltimer_ns() - t0 > limit_ns) break;
+        }
+    }
+    return __all_sync(FULL, ok);
+}
+
+template <int S>
+struct TmaGeom {
+    static constexpr int V = (S == ST_F32) ? 4 : 8;  // 16 bytes of elements per lane
+    static constexpr int EB = (S == ST_F32) ? 4 : 2;
+    static constexpr int PAD = 16 / EB;
+    static constexpr int RW = 32 * V + 2 * PAD;  // elements per stage row
+    static constexpr int RWB = RW * EB;          // 544 bytes
+    static constexpr int STAGE_B = 9 * RWB;      // nine directions
+};
+
+// Dynamic shared memory of a block of `warps` warps with NST stages each.
+__host__ __device__ constexpr int tma_bar_bytes(int warps, int nst) {
+    return ((warps * nst * 8) + 127) / 128 * 128;
+}
+template <int S>
+__host__ __device__ constexpr int tma_smem_bytes(int warps, int nst) {
+    return tma_bar_bytes(warps, nst) + warps * nst * TmaGeom<S>::STAGE_B;
+}
+
+template <int S, int NST>
+struct TmaWalker {
+    using G = TmaGeom<S>;
+    static constexpr int V = G::V;
+    static constexpr int EB = G::EB;
+    static constexpr int PAD = G::PAD;
+    static constexpr int NW = Pack<S, V>::NW;
+    using Wk = Walker<S, V, LD_NC>;
+
+    Wk wk;
+    unsigned char *stages;  // NST * STAGE_B bytes
+    uint32_t bars;          // NST mbarriers, 8 bytes apart
+    int np;                 // pieces per stage row
+    int ps[3], pd[3], pc[3];  // piece: source column, stage offset, length (elements)
+    uint32_t stage_tx;      // bytes one stage receives
+    unsigned long long limit_ns;
+
+    __device__ __forceinline__ TmaWalker(const void *fin, void *fout, int nx, int ny, size_t P,
+                                         int x0, unsigned char *stages_, uint32_t bars_,
+                                         unsigned long long limit)
+        : wk(fin, fout, nx, ny, P, x0), stages(stages_), bars(bars_), limit_ns(limit) {
+        // Columns x0-PAD .. x0+wa+PAD-1 in up to three wrapped pieces.  With
+        // nx a multiple of V (>= PAD) every piece starts and ends on 16 bytes.
+        int lo = x0 - PAD, hi = x0 + wk.wa + PAD;
+        np = 0;
+        if (lo < 0) {
+            ps[np] = nx + lo;
+            pd[np] = 0;
+            pc[np] = -lo;
+            ++np;
+            lo = 0;
+        }
+        int mhi = hi < nx ? hi : nx;
+        ps[np] = lo;
+        pd[np] = lo - (x0 - PAD);
+        pc[np] = mhi - lo;
+        ++np;
+        if (hi > nx) {
+            ps[np] = 0;
+            pd[np] = mhi - (x0 - PAD);
+            pc[np] = hi - nx;
+            ++np;
+        }
+        stage_tx = 9u * (uint32_t)(wk.wa + 2 * PAD) * EB;
+    }
+
+    __device__ __forceinline__ uint32_t bar(int s) const { return bars + 8u * s; }
+
+    // Starts the copies of pulled row index k (row q) into stage k % NST.
+    // Lane 0 announces the bytes; lanes 0..8 copy direction i = lane.
+    __device__ __forceinline__ void issue(int k, int q) const {
+        const int s = k % NST;
+        const uint32_t b = bar(s);
+        if (wk.lane == 0) mbar_arrive_expect_tx(b, stage_tx);
+        __syncwarp();
+        if (wk.lane < 9) {
+            const int i = wk.lane;
+            int sr = q - EYi(i);
+            if (sr < 0) sr += wk.ny;
+            if (sr >= wk.ny) sr -= wk.ny;
+            const unsigned char *src =
+                reinterpret_cast<const unsigned char *>(wk.fin) +
+                ((size_t)i * wk.P + (size_t)sr * wk.nx) * EB;
+            const uint32_t dst = smem_u32(stages + (size_t)s * G::STAGE_B + (size_t)i * G::RWB);
+            fence_proxy_async_smem();
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+                if (p < np)
+                    bulk_copy_g2s(dst + pd[p] * EB, src + (size_t)ps[p] * EB,
+                                  (uint32_t)pc[p] * EB, b);
+        }
+    }
+
+    // Reads the lane's words and helper value of row index k from its stage.
+    __device__ __forceinline__ void read(int k, uint32_t (&w)[9][NW], uint32_t &g) const {
+        const unsigned char *st = stages + (size_t)(k % NST) * G::STAGE_B;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if (wk.act) {
+                const unsigned char *p = st + i * G::RWB + (PAD + wk.lane * V) * EB;
+                uint4 r = *reinterpret_cast<const uint4 *>(p);
+                w[i][0] = r.x;
+                w[i][1] = r.y;
+                w[i][2] = r.z;
+                w[i][3] = r.w;
+            } else {
+#pragma unroll
+                for (int kk = 0; kk < NW; ++kk) w[i][kk] = 0u;
+            }
+        }
+        {
+            const unsigned char *p = st + wk.gdir * G::RWB + (PAD + wk.goff) * EB;
+            if constexpr (S == ST_F32)
+                g = *reinterpret_cast<const uint32_t *>(p);
+            else
+                g = (uint32_t) * reinterpret_cast<const unsigned short *>(p);
+        }
+    }
+
+    // Waits for row index k; on a timeout records it, waits (bounded) for the
+    // copies still in flight and reports failure.
+    __device__ __forceinline__ bool wait_row(int k, int issued, int *status) const {
+        if (mbar_wait_bounded(bar(k % NST), (uint32_t)((k / NST) & 1), limit_ns)) return true;
+        if (wk.lane == 0) atomicCAS(status, 0, STATUS_TIMEOUT);
+        for (int kk = k; kk < issued; ++kk)
+            mbar_wait_bounded(bar(kk % NST), (uint32_t)((kk / NST) & 1), limit_ns);
+        return false;
+    }
+
+    __device__ __forceinline__ void run(int y0, int y1, int dir, const Coef &c, int *status) {
+        const int ny = wk.ny;
+        if (wk.lane == 0) {
+            for (int s = 0; s < NST; ++s) mbar_init(bar(s), 1);
+            fence_mbar_init();
+        }
+        __syncwarp();
+        const int n = y1 - y0;
+        const int K = n + 2;  // pulled rows: one beyond each end of the segment
+        int q = dir > 0 ? ((y0 == 0) ? ny - 1 : y0 - 1) : (y1 == ny ? 0 : y1);
+        // Issue the first NST rows; qi / ki track the next row to issue.
+        int qi = q, ki = 0;
+        for (; ki < NST && ki < K; ++ki) {
+            issue(ki, qi);
+            qi += dir;
+            if (qi < 0) qi += ny;
+            if (qi >= ny) qi -= ny;
+        }
+        uint32_t wc[9][NW], wn[9][NW];
+        float dprev[V], dcur[V], dnext[V];
+        float dlc, drc, dln, drn;
+        uint32_t g;
+        bool ok = true;
+        // Row index 0: drho only.  Row index 1: the first row of the segment.
+        ok = wait_row(0, ki, status);
+        if (ok) {
+            read(0, wn, g);
+            wk.finish_pull(wn, g, dprev, dln, drn);
+            __syncwarp();
+            if (ki < K) {
+                issue(ki, qi);
+                ++ki;
+                qi += dir;
+                if (qi < 0) qi += ny;
+                if (qi >= ny) qi -= ny;
+            }
+            ok = wait_row(1, ki, status);
+        }
+        if (ok) {
+            read(1, wc, g);
+            wk.finish_pull(wc, g, dcur, dlc, drc);
+            __syncwarp();
+            if (ki < K) {
+                issue(ki, qi);
+                ++ki;
+                qi += dir;
+                if (qi < 0) qi += ny;
+                if (qi >= ny) qi -= ny;
+            }
+        }
+        for (int k = 0; ok && k < n; ++k) {
+            const int r = dir > 0 ? y0 + k : y1 - 1 - k;
+            ok = wait_row(k + 2, ki, status);
+            if (!ok) break;
+            read(k + 2, wn, g);
+            wk.finish_pull(wn, g, dnext, dln, drn);
+            __syncwarp();
+            if (ki < K) {
+                issue(ki, qi);
+                ++ki;
+                qi += dir;
+                if (qi < 0) qi += ny;
+                if (qi >= ny) qi -= ny;
+            }
+            if (dir > 0)
+                wk.collide_store(r, wc, dcur, dprev, dnext, dlc, drc, c);
+            else
+                wk.collide_store(r, wc, dcur, dnext, dprev, dlc, drc, c);
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+#pragma unroll
+                for (int kk = 0; kk < NW; ++kk) wc[i][kk] = wn[i][kk];
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 dprev[v] = dcur[v];
@@ -541,6 +860,9 @@ struct Walker {
             dlc = dln;
             drc = drn;
         }
+        __syncwarp();
+        if (ok && wk.lane == 0)
+            for (int s = 0; s < NST; ++s) mbar_inval(bar(s));
     }
 };
 

@@ -15,10 +15,18 @@ namespace vss {
 using Err = cudaError_t;
 
 struct TileCfg {
-    int vec = 4;    // sites per lane
-    int rows = 16;  // rows per warp strip
-    int warps = 4;  // warps per block
+    int vec = 4;     // sites per lane
+    int rows = 16;   // rows per warp strip
+    int warps = 4;   // warps per block
+    int stages = 0;  // > 0: bulk-copy row pipeline with this many stages
+                     // (used when vec is 16 bytes of elements), 0: register walk
 };
+
+// Sites per lane of the bulk-copy pipeline (16 bytes of elements).
+inline int tma_vec(int storage) { return storage == ST_F32 ? 4 : 8; }
+inline bool uses_tma(int storage, const TileCfg &c) {
+    return c.stages > 0 && c.vec == tma_vec(storage);
+}
 
 struct StepGeom {
     int nstrips, nsegs;
@@ -46,8 +54,12 @@ inline size_t plane_elems(int nx, int ny) {
 Coef make_coef(double tau, double c2, double rho0);
 
 // Kernel launchers (lbm_kernels.cu).  All asynchronous on `st`.
+// `status` (device int) receives STATUS_TIMEOUT if a pipeline wait runs out.
 Err launch_step(int storage, const TileCfg &cfg, const void *fin, void *fout, int nx, int ny,
-                size_t P, const Coef &c, cudaStream_t st);
+                size_t P, const Coef &c, int *status, cudaStream_t st);
+// Sets the kernel attributes a configuration needs (dynamic shared memory);
+// call before the first launch or capture of that configuration.
+Err prepare_step(int storage, const TileCfg &cfg);
 Err launch_init(int storage, void *f, int nx, int ny, size_t P, double rho0, const double *rho,
                 const double *ux, const double *uy, cudaStream_t st);
 Err launch_moments(int storage, const void *f, int nx, int ny, size_t P, double rho0, double *rho,

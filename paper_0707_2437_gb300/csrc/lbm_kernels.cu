@@ -29,7 +29,7 @@ bool valid_vec(int storage, int nx, int vec) {
 // Fused step: one warp per (strip, row segment) tile.
 
 template <int S, int V>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
     k_step(const void *__restrict__ fin, void *__restrict__ fout, int nx, int ny, size_t P,
            int nstrips, long long ntiles, int rows, Coef c) {
     long long tile = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -40,7 +40,34 @@ __global__ void __launch_bounds__(256)
     int y0 = seg * rows;
     int y1 = min(ny, y0 + rows);
     Walker<S, V> w(fin, fout, nx, ny, P, x0);
-    w.run(y0, y1, c);
+    // Neighbouring segments walk in opposite directions so that the two rows
+    // they share are read by both at about the same time.
+    w.run(y0, y1, (seg & 1) ? -1 : 1, c);
+}
+
+// Bulk-copy pipeline variant: one warp per tile, NST shared-memory stages per
+// warp (dynamic shared memory: barriers first, then the stages).
+constexpr unsigned long long kWaitLimitNs = 1000000000ULL;  // 1 s per wait
+
+template <int S, int NST>
+__global__ void __launch_bounds__(256)
+    k_step_tma(const void *__restrict__ fin, void *__restrict__ fout, int nx, int ny, size_t P,
+               int nstrips, long long ntiles, int rows, Coef c, int *status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int nwb = blockDim.x >> 5;
+    const int wib = threadIdx.x >> 5;
+    long long tile = (long long)blockIdx.x * nwb + wib;
+    if (tile >= ntiles) return;
+    constexpr int V = TmaGeom<S>::V;
+    int strip = (int)(tile % nstrips);
+    int seg = (int)(tile / nstrips);
+    int x0 = strip * 32 * V;
+    int y0 = seg * rows;
+    int y1 = min(ny, y0 + rows);
+    uint32_t bars = smem_u32(smem) + (uint32_t)(wib * NST * 8);
+    unsigned char *st = smem + tma_bar_bytes(nwb, NST) + (size_t)wib * NST * TmaGeom<S>::STAGE_B;
+    TmaWalker<S, NST> w(fin, fout, nx, ny, P, x0, st, bars, kWaitLimitNs);
+    w.run(y0, y1, (seg & 1) ? -1 : 1, c, status);
 }
 
 template <int S, int V>
@@ -53,9 +80,68 @@ static Err launch_step_t(const TileCfg &cfg, const void *fin, void *fout, int nx
     return cudaGetLastError();
 }
 
+template <int S, int NST>
+static Err launch_tma_t(const TileCfg &cfg, const void *fin, void *fout, int nx, int ny, size_t P,
+                        const Coef &c, int *status, cudaStream_t st) {
+    StepGeom g = step_geom(nx, ny, cfg);
+    long long blocks = (g.ntiles + cfg.warps - 1) / cfg.warps;
+    int smem = tma_smem_bytes<S>(cfg.warps, NST);
+    k_step_tma<S, NST><<<(unsigned)blocks, 32 * cfg.warps, smem, st>>>(
+        fin, fout, nx, ny, P, g.nstrips, g.ntiles, cfg.rows, c, status);
+    return cudaGetLastError();
+}
+
+template <int S, int NST>
+static Err prepare_tma_t() {
+    // Enough dynamic shared memory for the largest block (8 warps).
+    return cudaFuncSetAttribute(k_step_tma<S, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tma_smem_bytes<S>(8, NST));
+}
+
+template <int S>
+static Err prepare_s(int stages) {
+    switch (stages) {
+        case 2:
+            return prepare_tma_t<S, 2>();
+        case 3:
+            return prepare_tma_t<S, 3>();
+        case 4:
+            return prepare_tma_t<S, 4>();
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+Err prepare_step(int storage, const TileCfg &cfg) {
+    if (!uses_tma(storage, cfg)) return cudaSuccess;
+    if (tma_smem_bytes<ST_F32>(cfg.warps, cfg.stages) > 227 * 1024) return cudaErrorInvalidValue;
+    switch (storage) {
+        case ST_F32:
+            return prepare_s<ST_F32>(cfg.stages);
+        case ST_F16:
+            return prepare_s<ST_F16>(cfg.stages);
+        case ST_BF16:
+            return prepare_s<ST_BF16>(cfg.stages);
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
 template <int S>
 static Err launch_step_s(const TileCfg &cfg, const void *fin, void *fout, int nx, int ny, size_t P,
-                         const Coef &c, cudaStream_t st) {
+                         const Coef &c, int *status, cudaStream_t st) {
+    if (uses_tma(S, cfg)) {
+        switch (cfg.stages) {
+            case 2:
+                return launch_tma_t<S, 2>(cfg, fin, fout, nx, ny, P, c, status, st);
+            case 3:
+                return launch_tma_t<S, 3>(cfg, fin, fout, nx, ny, P, c, status, st);
+            case 4:
+                return launch_tma_t<S, 4>(cfg, fin, fout, nx, ny, P, c, status, st);
+            default:
+                return cudaErrorInvalidValue;
+        }
+    }
     switch (cfg.vec) {
         case 1:
             return launch_step_t<S, 1>(cfg, fin, fout, nx, ny, P, c, st);
@@ -72,14 +158,14 @@ static Err launch_step_s(const TileCfg &cfg, const void *fin, void *fout, int nx
 }
 
 Err launch_step(int storage, const TileCfg &cfg, const void *fin, void *fout, int nx, int ny,
-                size_t P, const Coef &c, cudaStream_t st) {
+                size_t P, const Coef &c, int *status, cudaStream_t st) {
     switch (storage) {
         case ST_F32:
-            return launch_step_s<ST_F32>(cfg, fin, fout, nx, ny, P, c, st);
+            return launch_step_s<ST_F32>(cfg, fin, fout, nx, ny, P, c, status, st);
         case ST_F16:
-            return launch_step_s<ST_F16>(cfg, fin, fout, nx, ny, P, c, st);
+            return launch_step_s<ST_F16>(cfg, fin, fout, nx, ny, P, c, status, st);
         case ST_BF16:
-            return launch_step_s<ST_BF16>(cfg, fin, fout, nx, ny, P, c, st);
+            return launch_step_s<ST_BF16>(cfg, fin, fout, nx, ny, P, c, status, st);
         default:
             return cudaErrorInvalidValue;
     }
@@ -324,3 +410,13 @@ Err launch_mode(int storage, const void *f, int nx, int ny, size_t P, double rho
 }
 
 }  // namespace vss
+
+#ifdef VSS_BOUNDS_CHECK
+// Debug builds only: the bounds-check record of the step kernels.
+extern "C" int lbm_debug_oob(unsigned long long *out2) {
+    return cudaMemcpyFromSymbol(out2, vss::vss_oob_record, sizeof(unsigned long long) * 2) ==
+                   cudaSuccess
+               ? 0
+               : -3;
+}
+#endif

@@ -65,6 +65,8 @@ def load() -> ctypes.CDLL:
             "lbm_set_config": ([vp, i, i, i], i),
             "lbm_get_config": ([vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)], i),
             "lbm_tune": ([vp, ctypes.c_char_p], i),
+            "lbm_set_pipeline": ([vp, i], i),
+            "lbm_get_pipeline": ([vp, ctypes.POINTER(i), ctypes.POINTER(i)], i),
             "lbm_set_timing": ([vp, i], i),
             "lbm_kernel_ms": ([vp, dp, ctypes.POINTER(ll)], i),
             "lbm_batch_create": ([ctypes.POINTER(vp), i, ctypes.POINTER(vp)], i),
@@ -239,9 +241,18 @@ class Grid:
                "lbm_get_config")
         return v.value, r.value, w.value
 
+    def set_pipeline(self, stages: int):
+        _check(self.lib.lbm_set_pipeline(self.h, stages), "lbm_set_pipeline")
+
+    def get_pipeline(self):
+        st, act = ctypes.c_int(), ctypes.c_int()
+        _check(self.lib.lbm_get_pipeline(self.h, ctypes.byref(st), ctypes.byref(act)),
+               "lbm_get_pipeline")
+        return st.value, bool(act.value)
+
     def tune(self, cache_path: str | None = None):
         _check(self.lib.lbm_tune(self.h, cache_path.encode() if cache_path else None), "lbm_tune")
-        return self.get_config()
+        return self.get_config() + (self.get_pipeline()[0],)
 
     def set_timing(self, on: bool):
         _check(self.lib.lbm_set_timing(self.h, 1 if on else 0), "lbm_set_timing")

@@ -78,12 +78,15 @@ def test_every_tile_configuration_bitwise_identical(lbm):
     for vec in (1, 2, 4):
         for rows in (1, 3, 16, 64):
             for warps in (1, 4, 8):
-                with lbm.Grid(nx, ny, 0.7, 0.15, "f32") as g:
-                    g.set_config(vec, rows, warps)
-                    g.init(*f)
-                    g.step(13)
-                    states[(vec, rows, warps)] = g.get_state()[0]
-    ref = states[(4, 16, 4)]
+                for stages in ((0, 2, 3, 4) if vec == 4 else (0,)):
+                    with lbm.Grid(nx, ny, 0.7, 0.15, "f32") as g:
+                        g.set_config(vec, rows, warps)
+                        g.set_pipeline(stages)
+                        assert g.get_pipeline() == (stages, stages > 0)
+                        g.init(*f)
+                        g.step(13)
+                        states[(vec, rows, warps, stages)] = g.get_state()[0]
+    ref = states[(4, 16, 4, 0)]
     for k, s in states.items():
         assert np.array_equal(s, ref), k
 
@@ -93,14 +96,40 @@ def test_sixteen_bit_tile_configurations_bitwise(lbm, storage):
     nx, ny = 512, 20
     f = _fields(nx, ny, seed=6)
     states = []
-    for vec, rows, warps in ((8, 16, 4), (4, 7, 2), (2, 5, 8), (1, 64, 1)):
+    for vec, rows, warps, stages in ((8, 16, 4, 0), (8, 16, 4, 4), (8, 5, 8, 2), (8, 33, 1, 3),
+                                     (4, 7, 2, 0), (2, 5, 8, 0), (1, 64, 1, 0)):
         with lbm.Grid(nx, ny, 0.9, 0.3, storage) as g:
             g.set_config(vec, rows, warps)
+            g.set_pipeline(stages)
             g.init(*f)
             g.step(11)
             states.append(g.get_state()[0])
     for s in states[1:]:
         assert np.array_equal(s, states[0])
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16d", "bf16d"])
+@pytest.mark.parametrize("nx,ny", [(8, 3), (16, 5), (136, 9), (264, 17), (520, 33), (1032, 6)])
+def test_pipeline_strip_edges_match_register_walk(lbm, storage, nx, ny):
+    """The bulk-copy pipeline's wrapped row pieces (strips at x = 0, at the
+    right edge, strips that are the whole row, partial last strips) give the
+    register walk's bits."""
+    vec = 4 if storage == "f32" else 8
+    if nx % vec:
+        pytest.skip("vector width does not divide nx")
+    f = _fields(nx, ny, seed=nx + 3)
+    out = []
+    for stages in (0, 3):
+        with lbm.Grid(nx, ny, 0.8, 0.2, storage) as g:
+            g.set_config(vec, 4, 2)
+            g.set_pipeline(stages)
+            g.init(*f)
+            g.step(9)
+            out.append(g.get_state()[0])
+    assert np.array_equal(out[0], out[1])
+    if storage == "f32":
+        got = _run_gpu(lbm, nx, ny, 0.8, 0.2, f, 9, cfg=(vec, 4, 2))
+        assert _err(got, oracle.simulate(*f, 0.8, 0.2, 9)) <= F32_TOL
 
 
 def test_graph_replay_equals_single_launches(lbm):
