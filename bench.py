@@ -334,13 +334,120 @@ def run_native(args):
         print(json.dumps(line), flush=True)
 
 
+def run_batch_workload(args):
+    """512 uneven grids (64^2 .. 1024^2, aspect 2^U[-2,2]) stepped together:
+    `--steps K` time steps of every grid in ONE persistent launch (replayed
+    from a CUDA graph), after `--warmup` steps."""
+    import torch
+
+    from paper_0707_2437_gb300 import lbm
+
+    ws, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    runs = workloads.batch_grids(args.batch_count)
+    storages = ([args.storage] if args.storage != "mixed" else ["f32", "f16d"])
+    grids = []
+    for k, r in enumerate(runs):
+        st = storages[k % len(storages)]
+        g = lbm.Grid(r.nx, r.ny, r.tau, r.c2, st, stream=stream.cuda_stream)
+        g.init(*workloads.sine_wave(r.nx, r.ny, r.amp, r.mode))
+        grids.append(g)
+    b = lbm.Batch(grids)
+    if args.batch_rows:
+        b.set_config(args.batch_rows, 0)
+    if args.tune:
+        b.tune()
+    sites = sum(r.nx * r.ny for r in runs)
+    alg = sum(r.nx * r.ny * lbm.BYTES_PER_LU[g.storage] for r, g in zip(runs, grids))
+    b.step(args.warmup)
+    b.sync()
+    t0e = torch.cuda.Event(enable_timing=True)
+    t1e = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0e.record(stream)
+    b.step(args.steps)
+    t1e.record(stream)
+    torch.cuda.synchronize()
+    status = b.sync()
+    barrier(ws)
+    clk = clocks.stop()
+    ms = max_over_ranks(ws, t0e.elapsed_time(t1e))
+    value = ws * sites * args.steps / (ms * 1e-3) / 1e6
+    achieved = alg * args.steps / (ms * 1e-3) / 1e9
+    peak, kind = measured_peak()
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": f"{args.storage} storage, f32 math", "data": "synthetic",
+        "config": {"workload": f"batch of {len(runs)} uneven grids, sites log-uniform "
+                               "64^2..1024^2, aspect 2^U[-2,2]",
+                   "sites": sites, "storage": args.storage, "launch":
+                   "one persistent cooperative launch of all steps (CUDA graph)",
+                   "l2": f"working set {alg / 1e9:.1f} GB >> 129 MB L2, no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_batch",
+                     "algorithmic_bytes_per_step": alg},
+        "gpu_launches": 1, "clocks": clk, "batch_status": status,
+    }
+    b.close()
+    for g in grids:
+        g.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_serve_workload(args):
+    """The serving trace through the continuous-batching server and through
+    the plain FIFO single-grid FP32 baseline; p50/p99 time-to-result and
+    aggregate MLUPS of both."""
+    import torch
+
+    from paper_0707_2437_gb300 import serve
+
+    ws, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    trace = serve.scaled_trace(args.serve_count, args.serve_rate, steps_hi=args.serve_steps_hi)
+    warm = serve.scaled_trace(8, 1000.0, seed=99, hi=256, steps_hi=2000)
+    serve.Server(quantum=args.serve_quantum).run(warm, realtime=False)
+    clocks = ClockSampler(local)
+    clocks.start()
+    srv = serve.Server(quantum=args.serve_quantum).run(trace, realtime=True).summary()
+    fifo = serve.serve_fifo(trace, realtime=True).summary()
+    clk = clocks.stop()
+    line = {
+        "metric": "served p50/p99 time-to-result and aggregate MLUPS vs plain FP32 FIFO",
+        "value": srv["mlups"], "unit": "MLUPS", "n_gpus": ws, "steps": args.serve_count,
+        "warmup": 8, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "half f32, half f16d storage, f32 math", "data": "synthetic",
+        "config": {"workload": f"{args.serve_count} Poisson requests at {args.serve_rate}/s, "
+                               f"sites log-uniform 128^2..2048^2, steps U{{1000..{args.serve_steps_hi}}}",
+                   "quantum_steps": args.serve_quantum},
+        "served": srv, "fifo_f32": fifo, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--storage", default="f32", choices=list(BYTES_PER_LU))
+    ap.add_argument("--storage", default="f32", choices=list(BYTES_PER_LU) + ["mixed"])
+    ap.add_argument("--workload", default="sweep2048", choices=["sweep2048", "batch", "serve"])
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-rows", type=int, default=0)
+    ap.add_argument("--tune", action="store_true")
+    ap.add_argument("--serve-count", type=int, default=200)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-steps-hi", type=int, default=20000)
+    ap.add_argument("--serve-quantum", type=int, default=256)
     ap.add_argument("--config", type=int, nargs=3, default=None,
                     metavar=("VEC", "ROWS", "WARPS"))
     ap.add_argument("--stages", type=int, default=None,
@@ -357,7 +464,13 @@ def main():
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch_workload(args)
+    elif args.workload == "serve":
+        run_serve_workload(args)
     else:
+        if args.storage == "mixed":
+            ap.error("--storage mixed applies to the batch workload")
         run_native(args)
 
 

@@ -70,18 +70,29 @@ extern "C" const char *lbm_last_error(void) { return g_last_error.c_str(); }
 
 static size_t state_bytes(const lbm_grid *h) { return 9 * h->P * (size_t)elem_bytes(h->storage); }
 
+// Defaults from the measured sweep on 2048^2 (profiles/): FP32 runs fastest as
+// the plain register walk with 128-bit vectors; the 16-bit kinds as the
+// prefetching register walk with 64-bit vectors.  Narrower vectors serve grids
+// whose nx they do not divide.
 static TileCfg default_cfg(int storage, int nx, int ny) {
+    (void)ny;
     TileCfg c;
-    int best = storage == ST_F32 ? 4 : 8;
-    c.vec = 1;
-    for (int v = best; v >= 1; v /= 2)
-        if (valid_vec(storage, nx, v)) {
-            c.vec = v;
-            break;
-        }
     c.rows = 16;
     c.warps = 4;
-    c.stages = 0;  // register walk; the row pipeline is an autotuner option
+    c.stages = 0;
+    if (storage == ST_F32) {
+        c.vec = 1;
+        for (int v = 4; v >= 1; v /= 2)
+            if (valid_vec(storage, nx, v)) {
+                c.vec = v;
+                break;
+            }
+    } else if (valid_vec(storage, nx, prefetch_vec(storage))) {
+        c.vec = prefetch_vec(storage);
+        c.stages = 1;
+    } else {
+        c.vec = nx % 2 == 0 ? 2 : 1;
+    }
     return c;
 }
 
@@ -442,8 +453,8 @@ extern "C" int lbm_set_config(lbm_t h, int vec, int rows, int warps) {
 
 extern "C" int lbm_set_pipeline(lbm_t h, int stages) {
     if (!h) return fail(LBM_EINVAL, "lbm_set_pipeline: NULL handle");
-    if (stages != 0 && (stages < 2 || stages > 4))
-        return fail(LBM_EINVAL, "lbm_set_pipeline: stages must be 0 or 2..4");
+    if (stages < 0 || stages > 4)
+        return fail(LBM_EINVAL, "lbm_set_pipeline: stages must be 0..4");
     if (h->cfg.stages != stages) {
         CK(cudaStreamSynchronize(h->stream));
         drop_graphs(h);
@@ -456,7 +467,8 @@ extern "C" int lbm_set_pipeline(lbm_t h, int stages) {
 extern "C" int lbm_get_pipeline(lbm_t h, int *stages, int *active) {
     if (!h) return fail(LBM_EINVAL, "lbm_get_pipeline: NULL handle");
     if (stages) *stages = h->cfg.stages;
-    if (active) *active = uses_tma(h->storage, h->cfg) ? 1 : 0;
+    if (active)
+        *active = (uses_tma(h->storage, h->cfg) || uses_prefetch(h->storage, h->cfg)) ? 1 : 0;
     return LBM_OK;
 }
 
@@ -562,8 +574,11 @@ extern "C" int lbm_tune(lbm_t h, const char *cache_path) {
         for (int r : rowss) {
             if (r > 2 * h->ny && r != 4) continue;
             for (int w : warpss) {
-                const int nst_max = (v == tma_vec(h->storage)) ? 4 : 0;
-                for (int nst = 0; nst <= nst_max; nst = (nst == 0 ? 2 : nst + 1)) {
+                const bool tma_ok = v == tma_vec(h->storage);
+                const bool pf_ok = v == prefetch_vec(h->storage);
+                for (int nst = 0; nst <= 4; ++nst) {
+                    if (nst == 1 && !pf_ok) continue;
+                    if (nst >= 2 && !tma_ok) continue;
                     TileCfg c;
                     c.vec = v;
                     c.rows = r;

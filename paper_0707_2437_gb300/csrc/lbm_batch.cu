@@ -26,7 +26,7 @@ struct GridDesc {
     void *buf[2];
     size_t P;
     int nx, ny;
-    int kind;  // storage * 16 + vec
+    int kind;  // storage * 16 + vec (16-bit vec 4 uses the prefetching walk)
     int pad;
     Coef c;
 };
@@ -35,7 +35,7 @@ struct Tile {
     int grid, x0, y0, y1, dir;
 };
 
-constexpr int kBatchWarps = 8;  // warps per block of the persistent kernel
+constexpr int kBatchWarps = 4;  // warps per block of the persistent kernel
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -82,13 +82,16 @@ __device__ bool grid_barrier(unsigned *bar, int *status, unsigned long long time
     return ok_sh != 0;
 }
 
-template <int S, int V>
-__device__ __forceinline__ void do_tile(const GridDesc &g, int par, const Tile &t) {
+template <int S, int V, bool PF = false>
+__device__ __noinline__ void do_tile(const GridDesc &g, int par, const Tile &t) {
     Walker<S, V, LD_CG> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P, t.x0);
-    w.run(t.y0, t.y1, t.dir, g.c);
+    if constexpr (PF)
+        w.run_prefetch(t.y0, t.y1, t.dir, g.c);
+    else
+        w.run(t.y0, t.y1, t.dir, g.c);
 }
 
-__global__ void __launch_bounds__(32 * kBatchWarps, 2)
+__global__ void __launch_bounds__(32 * kBatchWarps, 3)
     k_batch(const GridDesc *__restrict__ grids, const Tile *__restrict__ tiles, int ntiles,
             const long long *__restrict__ limit, const int *__restrict__ parity0,
             long long nsteps, unsigned *bar, int *status, unsigned long long timeout_ns) {
@@ -102,32 +105,23 @@ __global__ void __launch_bounds__(32 * kBatchWarps, 2)
             const GridDesc &g = grids[t.grid];
             const int par = (parity0[t.grid] + (int)(k & 1)) & 1;
             switch (g.kind) {
+                case ST_F32 * 16 + 4:
+                    do_tile<ST_F32, 4>(g, par, t);
+                    break;
                 case ST_F32 * 16 + 1:
                     do_tile<ST_F32, 1>(g, par, t);
                     break;
-                case ST_F32 * 16 + 2:
-                    do_tile<ST_F32, 2>(g, par, t);
-                    break;
-                case ST_F32 * 16 + 4:
-                    do_tile<ST_F32, 4>(g, par, t);
+                case ST_F16 * 16 + 4:
+                    do_tile<ST_F16, 4, true>(g, par, t);
                     break;
                 case ST_F16 * 16 + 1:
                     do_tile<ST_F16, 1>(g, par, t);
                     break;
-                case ST_F16 * 16 + 2:
-                    do_tile<ST_F16, 2>(g, par, t);
-                    break;
-                case ST_F16 * 16 + 4:
-                    do_tile<ST_F16, 4>(g, par, t);
+                case ST_BF16 * 16 + 4:
+                    do_tile<ST_BF16, 4, true>(g, par, t);
                     break;
                 case ST_BF16 * 16 + 1:
                     do_tile<ST_BF16, 1>(g, par, t);
-                    break;
-                case ST_BF16 * 16 + 2:
-                    do_tile<ST_BF16, 2>(g, par, t);
-                    break;
-                case ST_BF16 * 16 + 4:
-                    do_tile<ST_BF16, 4>(g, par, t);
                     break;
                 default:
                     break;
@@ -189,11 +183,10 @@ static void drop_graph(lbm_batch *b) {
     b->graph_n = -1;
 }
 
-static int batch_vec(const lbm_grid *g) {
-    int v = std::min(g->cfg.vec, 4);
-    while (v > 1 && !valid_vec(g->storage, g->nx, v)) v /= 2;
-    return v;
-}
+// The batch kernel carries two walks per storage: 4 sites per lane (128-bit
+// loads for FP32; 64-bit loads with one row prefetched for 16-bit), used when
+// nx is a multiple of 4, and 1 site per lane for any other nx.
+static int batch_vec(const lbm_grid *g) { return g->nx % 4 == 0 ? 4 : 1; }
 
 // (Re)builds the device grid table and the tile work-list.
 static int build_worklist(lbm_batch *b) {

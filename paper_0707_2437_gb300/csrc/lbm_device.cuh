@@ -241,6 +241,23 @@ __device__ __forceinline__ uint32_t pack1(float v) {
     }
 }
 
+// Sites per packed word: the 16-bit kinds convert two sites at a time.
+template <int S, int V>
+struct SitesPerWord {
+    static constexpr int value = (S == ST_F32 || V == 1) ? 1 : 2;
+};
+
+// Both elements of a packed 16-bit word as floats (element 2k in .x).
+template <int S>
+__device__ __forceinline__ float2 unpack2(uint32_t w) {
+    if constexpr (S == ST_F16) {
+        __half2 h = *reinterpret_cast<__half2 *>(&w);
+        return __half22float2(h);
+    } else {
+        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    }
+}
+
 // Shifts of a lane's packed row by one element.  shift_from_left: element v
 // takes element v-1 and element 0 takes `in`, the word that holds the left
 // neighbour's last element (in its high half for 16-bit with V >= 2).
@@ -396,11 +413,20 @@ struct Walker {
     // its sites, and drho of the left / right halo sites (valid in every lane).
     __device__ __forceinline__ void pull_row(int qm, int q0, int qp, uint32_t (&w)[9][NW],
                                              float (&d)[V], float &dl, float &dr) const {
+        uint32_t g;
+        load_row(qm, q0, qp, w, g);
+        finish_pull(w, g, d, dl, dr);
+    }
+
+    // The loads of a pull: the lane's nine aligned vectors and the helper value.
+    __device__ __forceinline__ void load_row(int qm, int q0, int qp, uint32_t (&w)[9][NW],
+                                             uint32_t &g) const {
         // Source row of direction i is q - e_y(i).
         // Lanes past the end of a partial strip load the strip's first
         // elements instead (unused), so that every lane issues the same loads.
         const int xl = act ? xs : x0;
         const size_t lim = 9 * P;
+        (void)lim;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int sr = (EYi(i) > 0) ? qm : ((EYi(i) < 0) ? qp : q0);
@@ -414,8 +440,33 @@ struct Walker {
         }
         const int gsr = (gey > 0) ? qm : ((gey < 0) ? qp : q0);
         const size_t gidx = (size_t)gdir * P + (size_t)gsr * nx + gcol;
-        const uint32_t g = VSS_IN_BOUNDS(gidx, 1, lim) ? load_elem<S, LD>(fin + gidx) : 0u;
-        finish_pull(w, g, d, dl, dr);
+        g = VSS_IN_BOUNDS(gidx, 1, lim) ? load_elem<S, LD>(fin + gidx) : 0u;
+    }
+
+    // The nine values of sites v0 .. v0+SP-1 as floats, and back (the 16-bit
+    // kinds convert the two sites of a word together; rounding is per element).
+    __device__ __forceinline__ static void unpack_sites(
+        const uint32_t (&w)[9][NW], int v0, float (&h)[SitesPerWord<S, V>::value][9]) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if constexpr (SitesPerWord<S, V>::value == 2) {
+                const float2 f = unpack2<S>(w[i][v0 >> 1]);
+                h[0][i] = f.x;
+                h[1][i] = f.y;
+            } else {
+                h[0][i] = get_elem<S, V>(w[i], v0);
+            }
+        }
+    }
+    __device__ __forceinline__ static void pack_sites(
+        uint32_t (&w)[9][NW], int v0, const float (&h)[SitesPerWord<S, V>::value][9]) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if constexpr (SitesPerWord<S, V>::value == 2)
+                w[i][v0 >> 1] = pack2<S>(h[0][i], h[1][i]);
+            else
+                set_elem<S, V>(w[i], v0, h[0][i]);
+        }
     }
 
     // Shifts of the e_x = +-1 directions, drho of the lane's sites, and drho
@@ -458,13 +509,15 @@ struct Walker {
             shift_from_right<S, V>(w[6], n6);
             shift_from_right<S, V>(w[7], n7);
         }
+        constexpr int SP = SitesPerWord<S, V>::value;
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            d[v] = delta_rho(get_elem<S, V>(w[0], v), get_elem<S, V>(w[1], v),
-                             get_elem<S, V>(w[2], v), get_elem<S, V>(w[3], v),
-                             get_elem<S, V>(w[4], v), get_elem<S, V>(w[5], v),
-                             get_elem<S, V>(w[6], v), get_elem<S, V>(w[7], v),
-                             get_elem<S, V>(w[8], v));
+        for (int v0 = 0; v0 < V; v0 += SP) {
+            float h[SP][9];
+            unpack_sites(w, v0, h);
+#pragma unroll
+            for (int s = 0; s < SP; ++s)
+                d[v0 + s] = delta_rho(h[s][0], h[s][1], h[s][2], h[s][3], h[s][4], h[s][5],
+                                      h[s][6], h[s][7], h[s][8]);
         }
         // Halo drho: lanes 0..8 hold the left halo's nine values, 16..24 the
         // right halo's; gather them in direction order and sum as above.
@@ -492,25 +545,31 @@ struct Walker {
         float rgt = __shfl_down_sync(FULL, d[0], 1);
         if (lane == 0) lft = dl;
         if (lane == nact - 1) rgt = dr;
+        constexpr int SP = SitesPerWord<S, V>::value;
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const float dxm = (v == 0) ? lft : d[v - 1];
-            const float dxp = (v == V - 1) ? rgt : d[v + 1];
-            float h[9];
+        for (int v0 = 0; v0 < V; v0 += SP) {
+            float h[SP][9];
+            unpack_sites(w, v0, h);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) h[i] = get_elem<S, V>(w[i], v);
-            const SiteQ q = site_quantities(h[1], h[2], h[3], h[4], h[5], h[6], h[7], h[8], d[v],
-                                            dxm, dxp, dym[v], dyp[v], c);
-            float o[9];
-            o[0] = __fmaf_rn(c.om1, h[0], q.wB);                            // rest
-            pair_out(h[1], h[3], q.jx, q.ux, q.Ax, q.wB, c, o[1], o[3]);  // e = (1, 0)
-            pair_out(h[2], h[4], q.jy, q.uy, q.Ay, q.wB, c, o[2], o[4]);  // e = (0, 1)
-            pair_out(h[5], h[7], __fadd_rn(q.jx, q.jy), __fadd_rn(q.ux, q.uy),
-                     __fadd_rn(q.Ax, q.Ay), q.wB, c, o[5], o[7]);  // e = (1, 1)
-            pair_out(h[6], h[8], __fsub_rn(q.jy, q.jx), __fsub_rn(q.uy, q.ux),
-                     __fsub_rn(q.Ay, q.Ax), q.wB, c, o[6], o[8]);  // e = (-1, 1)
+            for (int s = 0; s < SP; ++s) {
+                const int v = v0 + s;
+                const float dxm = (v == 0) ? lft : d[v - 1];
+                const float dxp = (v == V - 1) ? rgt : d[v + 1];
+                float *hs = h[s];
+                const SiteQ q = site_quantities(hs[1], hs[2], hs[3], hs[4], hs[5], hs[6], hs[7],
+                                                hs[8], d[v], dxm, dxp, dym[v], dyp[v], c);
+                float o[9];
+                o[0] = __fmaf_rn(c.om1, hs[0], q.wB);                           // rest
+                pair_out(hs[1], hs[3], q.jx, q.ux, q.Ax, q.wB, c, o[1], o[3]);  // e = (1, 0)
+                pair_out(hs[2], hs[4], q.jy, q.uy, q.Ay, q.wB, c, o[2], o[4]);  // e = (0, 1)
+                pair_out(hs[5], hs[7], __fadd_rn(q.jx, q.jy), __fadd_rn(q.ux, q.uy),
+                         __fadd_rn(q.Ax, q.Ay), q.wB, c, o[5], o[7]);  // e = (1, 1)
+                pair_out(hs[6], hs[8], __fsub_rn(q.jy, q.jx), __fsub_rn(q.uy, q.ux),
+                         __fsub_rn(q.Ay, q.Ax), q.wB, c, o[6], o[8]);  // e = (-1, 1)
 #pragma unroll
-            for (int i = 0; i < 9; ++i) set_elem<S, V>(w[i], v, o[i]);
+                for (int i = 0; i < 9; ++i) hs[i] = o[i];
+            }
+            pack_sites(w, v0, h);
         }
         if (!act) return;
         const size_t row = (size_t)r * nx + xs;
@@ -565,6 +624,56 @@ struct Walker {
         }
     }
 
+    // As run(), with the loads of the next pulled row issued before the
+    // current row is finished and the row before it collided, so that every
+    // warp keeps one row of loads in flight while it computes.  Needs a third
+    // row of registers: used with 64-bit vectors (vec 2 FP32, vec 4 16-bit).
+    __device__ __forceinline__ void run_prefetch(int y0, int y1, int dir, const Coef &c) const {
+        int q0 = dir > 0 ? ((y0 == 0) ? ny - 1 : y0 - 1) : (y1 == ny ? 0 : y1);
+        int qm = (q0 == 0) ? ny - 1 : q0 - 1;
+        int qp = (q0 + 1 == ny) ? 0 : q0 + 1;
+
+        uint32_t wc[9][NW], wn[9][NW], wf[9][NW];
+        uint32_t gn, gf;
+        float d2[V], d1[V], d0[V];
+        float l1 = 0.f, r1 = 0.f, l0, r0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            d2[v] = 0.f;
+            d1[v] = 0.f;
+        }
+        const int n = y1 - y0;
+        const int K = n + 2;
+        load_row(qm, q0, qp, wn, gn);
+        for (int k = 0; k < K; ++k) {
+            advance(qm, q0, qp, dir);
+            if (k + 1 < K) load_row(qm, q0, qp, wf, gf);
+            finish_pull(wn, gn, d0, l0, r0);
+            if (k >= 2) {
+                const int r = dir > 0 ? y0 + (k - 2) : y1 - 1 - (k - 2);
+                if (dir > 0)
+                    collide_store(r, wc, d1, d2, d0, l1, r1, c);
+                else
+                    collide_store(r, wc, d1, d0, d2, l1, r1, c);
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+#pragma unroll
+                for (int kk = 0; kk < NW; ++kk) {
+                    wc[i][kk] = wn[i][kk];
+                    wn[i][kk] = wf[i][kk];
+                }
+            gn = gf;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                d2[v] = d1[v];
+                d1[v] = d0[v];
+            }
+            l1 = l0;
+            r1 = r0;
+        }
+    }
+
     __device__ __forceinline__ void advance(int &qm, int &q0, int &qp, int dir) const {
         if (dir > 0) {
             qm = q0;
@@ -613,12 +722,14 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
 }
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
+    // The suspend-time hint (ns) lets the thread sleep until the phase
+    // completes instead of spinning and taking issue slots from other warps.
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(1000000u)
         : "memory");
     return ok != 0;
 }
@@ -683,8 +794,10 @@ struct TmaWalker {
     Wk wk;
     unsigned char *stages;  // NST * STAGE_B bytes
     uint32_t bars;          // NST mbarriers, 8 bytes apart
-    int np;                 // pieces per stage row
-    int ps[3], pd[3], pc[3];  // piece: source column, stage offset, length (elements)
+    // pieces of a stage row: source column, stage offset and length (elements)
+    int ps0, pc0;            // left wrap piece (stage offset 0)
+    int ps1, pd1, pc1;       // main piece
+    int pd2, pc2;            // right wrap piece (source column 0)
     uint32_t stage_tx;      // bytes one stage receives
     unsigned long long limit_ns;
 
@@ -692,28 +805,20 @@ struct TmaWalker {
                                          int x0, unsigned char *stages_, uint32_t bars_,
                                          unsigned long long limit)
         : wk(fin, fout, nx, ny, P, x0), stages(stages_), bars(bars_), limit_ns(limit) {
-        // Columns x0-PAD .. x0+wa+PAD-1 in up to three wrapped pieces.  With
-        // nx a multiple of V (>= PAD) every piece starts and ends on 16 bytes.
-        int lo = x0 - PAD, hi = x0 + wk.wa + PAD;
-        np = 0;
-        if (lo < 0) {
-            ps[np] = nx + lo;
-            pd[np] = 0;
-            pc[np] = -lo;
-            ++np;
-            lo = 0;
-        }
-        int mhi = hi < nx ? hi : nx;
-        ps[np] = lo;
-        pd[np] = lo - (x0 - PAD);
-        pc[np] = mhi - lo;
-        ++np;
-        if (hi > nx) {
-            ps[np] = 0;
-            pd[np] = mhi - (x0 - PAD);
-            pc[np] = hi - nx;
-            ++np;
-        }
+        // Columns x0-PAD .. x0+wa+PAD-1 in three wrapped pieces (left wrap,
+        // main, right wrap; the wrap pieces are empty away from the grid's
+        // edges).  With nx a multiple of V (>= PAD) every piece starts and ends
+        // on 16 bytes.  Fixed slots keep the pieces in registers.
+        const int lo = x0 - PAD, hi = x0 + wk.wa + PAD;
+        const int mlo = lo < 0 ? 0 : lo;
+        const int mhi = hi < nx ? hi : nx;
+        ps0 = nx + lo;  // left wrap: columns nx-PAD .. nx-1 (used when lo < 0)
+        pc0 = lo < 0 ? -lo : 0;
+        ps1 = mlo;
+        pd1 = mlo - lo;
+        pc1 = mhi - mlo;
+        pd2 = mhi - lo;  // right wrap: columns 0 .. PAD-1 (used when hi > nx)
+        pc2 = hi > nx ? hi - nx : 0;
         stage_tx = 9u * (uint32_t)(wk.wa + 2 * PAD) * EB;
     }
 
@@ -736,11 +841,9 @@ struct TmaWalker {
                 ((size_t)i * wk.P + (size_t)sr * wk.nx) * EB;
             const uint32_t dst = smem_u32(stages + (size_t)s * G::STAGE_B + (size_t)i * G::RWB);
             fence_proxy_async_smem();
-#pragma unroll
-            for (int p = 0; p < 3; ++p)
-                if (p < np)
-                    bulk_copy_g2s(dst + pd[p] * EB, src + (size_t)ps[p] * EB,
-                                  (uint32_t)pc[p] * EB, b);
+            if (pc0) bulk_copy_g2s(dst, src + (size_t)ps0 * EB, (uint32_t)pc0 * EB, b);
+            bulk_copy_g2s(dst + pd1 * EB, src + (size_t)ps1 * EB, (uint32_t)pc1 * EB, b);
+            if (pc2) bulk_copy_g2s(dst + pd2 * EB, src, (uint32_t)pc2 * EB, b);
         }
     }
 

@@ -18,14 +18,21 @@ struct TileCfg {
     int vec = 4;     // sites per lane
     int rows = 16;   // rows per warp strip
     int warps = 4;   // warps per block
-    int stages = 0;  // > 0: bulk-copy row pipeline with this many stages
-                     // (used when vec is 16 bytes of elements), 0: register walk
+    int stages = 0;  // 2..4: bulk-copy row pipeline with this many stages (used
+                     // when vec is 16 bytes of elements); 1: register walk with
+                     // one row of loads prefetched (used when vec is 8 bytes of
+                     // elements); 0: register walk
 };
 
 // Sites per lane of the bulk-copy pipeline (16 bytes of elements).
 inline int tma_vec(int storage) { return storage == ST_F32 ? 4 : 8; }
 inline bool uses_tma(int storage, const TileCfg &c) {
-    return c.stages > 0 && c.vec == tma_vec(storage);
+    return c.stages >= 2 && c.vec == tma_vec(storage);
+}
+// Sites per lane of the prefetching register walk (8 bytes of elements).
+inline int prefetch_vec(int storage) { return storage == ST_F32 ? 2 : 4; }
+inline bool uses_prefetch(int storage, const TileCfg &c) {
+    return c.stages == 1 && c.vec == prefetch_vec(storage);
 }
 
 struct StepGeom {

@@ -28,7 +28,7 @@ bool valid_vec(int storage, int nx, int vec) {
 // ---------------------------------------------------------------------------
 // Fused step: one warp per (strip, row segment) tile.
 
-template <int S, int V>
+template <int S, int V, bool PF>
 __global__ void __launch_bounds__(256, 2)
     k_step(const void *__restrict__ fin, void *__restrict__ fout, int nx, int ny, size_t P,
            int nstrips, long long ntiles, int rows, Coef c) {
@@ -42,7 +42,10 @@ __global__ void __launch_bounds__(256, 2)
     Walker<S, V> w(fin, fout, nx, ny, P, x0);
     // Neighbouring segments walk in opposite directions so that the two rows
     // they share are read by both at about the same time.
-    w.run(y0, y1, (seg & 1) ? -1 : 1, c);
+    if constexpr (PF)
+        w.run_prefetch(y0, y1, (seg & 1) ? -1 : 1, c);
+    else
+        w.run(y0, y1, (seg & 1) ? -1 : 1, c);
 }
 
 // Bulk-copy pipeline variant: one warp per tile, NST shared-memory stages per
@@ -50,7 +53,7 @@ __global__ void __launch_bounds__(256, 2)
 constexpr unsigned long long kWaitLimitNs = 1000000000ULL;  // 1 s per wait
 
 template <int S, int NST>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
     k_step_tma(const void *__restrict__ fin, void *__restrict__ fout, int nx, int ny, size_t P,
                int nstrips, long long ntiles, int rows, Coef c, int *status) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -75,8 +78,16 @@ static Err launch_step_t(const TileCfg &cfg, const void *fin, void *fout, int nx
                          const Coef &c, cudaStream_t st) {
     StepGeom g = step_geom(nx, ny, cfg);
     long long blocks = (g.ntiles + cfg.warps - 1) / cfg.warps;
-    k_step<S, V><<<(unsigned)blocks, 32 * cfg.warps, 0, st>>>(fin, fout, nx, ny, P, g.nstrips,
-                                                             g.ntiles, cfg.rows, c);
+    if (uses_prefetch(S, cfg)) {
+        if constexpr (Pack<S, V>::BYTES == 8)
+            k_step<S, V, true><<<(unsigned)blocks, 32 * cfg.warps, 0, st>>>(
+                fin, fout, nx, ny, P, g.nstrips, g.ntiles, cfg.rows, c);
+        else
+            return cudaErrorInvalidValue;
+    } else {
+        k_step<S, V, false><<<(unsigned)blocks, 32 * cfg.warps, 0, st>>>(
+            fin, fout, nx, ny, P, g.nstrips, g.ntiles, cfg.rows, c);
+    }
     return cudaGetLastError();
 }
 

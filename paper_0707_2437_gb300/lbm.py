@@ -18,6 +18,7 @@ import numpy as np
 from . import build as _build
 
 STORAGE = {"f32": 0, "f16d": 1, "bf16d": 2}
+BYTES_PER_LU = {"f32": 72, "f16d": 36, "bf16d": 36}  # algorithmic bytes per lattice update
 FIELD = {"rho": 0, "ux": 1, "uy": 2}
 LBM_OK, LBM_WUNSTABLE = 0, 1
 LBM_ETIMEOUT = -5

@@ -1,0 +1,196 @@
+"""Continuous-batching serving loop for variable-speed-of-sound simulations.
+
+Requests (grid size, tau, c^2, step count, storage) arrive over time.  The
+server keeps every admitted grid's distributions resident in HBM and advances
+all of them together with the batch API (one persistent launch per quantum of
+steps, each grid limited to its remaining steps).  Between quanta it retires
+finished grids (their moments are the result), frees their memory, and admits
+waiting requests, in arrival order, as long as the free device memory
+(lbm_mem_info) minus a reserve covers the new grid (lbm_bytes_required plus the
+staging of its initial fields) and a slot is free.  So requests that arrive
+while others are on the GPU join the running set as memory frees up, and their
+work overlaps on the device.
+
+``serve_fifo`` is the plain baseline: one grid at a time, in arrival order,
+with the single-grid FP32 kernel.
+
+All stepping runs in the CUDA library; this module only schedules.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import lbm, workloads
+
+
+@dataclass
+class Result:
+    rid: int
+    arrival_s: float
+    admitted_s: float
+    finished_s: float
+    steps: int
+    sites: int
+    storage: str
+    fields: tuple | None = None
+
+    @property
+    def latency_s(self) -> float:
+        return self.finished_s - self.arrival_s
+
+
+@dataclass
+class ServeStats:
+    results: list = field(default_factory=list)
+    makespan_s: float = 0.0
+    lattice_updates: int = 0
+    quanta: int = 0
+    max_active: int = 0
+
+    def summary(self) -> dict:
+        lat = np.array([r.latency_s for r in self.results]) if self.results else np.zeros(1)
+        return {
+            "requests": len(self.results),
+            "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()),
+            "makespan_s": self.makespan_s,
+            "mlups": self.lattice_updates / self.makespan_s / 1e6 if self.makespan_s else 0.0,
+            "quanta": self.quanta,
+            "max_active": self.max_active,
+        }
+
+
+def _fields(req: workloads.Request):
+    m = 1 + req.rid % 3
+    return workloads.sine_wave(req.nx, req.ny, req.amp, m)
+
+
+class Server:
+    """Continuous batching over the batch API."""
+
+    def __init__(self, quantum: int = 256, reserve_bytes: int = 4 << 30,
+                 max_slots: int = 512, keep_fields: bool = False, stream=None):
+        self.quantum = quantum
+        self.reserve = reserve_bytes
+        self.max_slots = max_slots
+        self.keep_fields = keep_fields
+        self.stream = stream
+        lbm.load()
+
+    def _need(self, req) -> int:
+        # distributions + the staging of three FP64 fields during lbm_init
+        return lbm.bytes_required(req.nx, req.ny, req.storage) + 24 * req.nx * req.ny
+
+    def run(self, requests, realtime: bool = True) -> ServeStats:
+        """Serves `requests` (sorted by arrival).  With realtime=True arrivals
+        follow the wall clock from the start of the call; otherwise every
+        request is present at time 0."""
+        pending = sorted(requests, key=lambda r: r.arrival_s)
+        active = []  # (req, grid, remaining, admitted_s)
+        stats = ServeStats()
+        batch = None
+        members = None
+        t0 = time.perf_counter()
+        i = 0
+
+        def now():
+            return time.perf_counter() - t0
+
+        while i < len(pending) or active:
+            # Admit arrived requests while memory and slots allow.
+            free, _ = lbm.mem_info()
+            changed = False
+            while i < len(pending) and len(active) < self.max_slots:
+                req = pending[i]
+                if realtime and req.arrival_s > now():
+                    break
+                need = self._need(req)
+                if need > free - self.reserve:
+                    if not active:
+                        raise MemoryError(f"request {req.rid} needs {need} bytes, "
+                                          f"{free} free")
+                    break
+                g = lbm.Grid(req.nx, req.ny, req.tau, req.c2, req.storage,
+                             stream=self.stream)
+                g.init(*_fields(req))
+                active.append([req, g, req.steps, now()])
+                free -= need
+                changed = True
+                i += 1
+            if not active:
+                # Idle until the next arrival.
+                wait = pending[i].arrival_s - now()
+                if wait > 0:
+                    time.sleep(min(wait, 0.05))
+                continue
+            if changed or batch is None or members != [id(a[1]) for a in active]:
+                if batch is not None:
+                    batch.close()
+                batch = lbm.Batch([a[1] for a in active])
+                members = [id(a[1]) for a in active]
+            stats.max_active = max(stats.max_active, len(active))
+            q = min(self.quantum, max(a[2] for a in active))
+            limits = [min(q, a[2]) for a in active]
+            batch.step(q, limits)
+            batch.sync()
+            stats.quanta += 1
+            for a, lim in zip(active, limits):
+                a[2] -= lim
+                stats.lattice_updates += lim * a[0].nx * a[0].ny
+            keep = []
+            for a in active:
+                req, g, rem, adm = a
+                if rem > 0:
+                    keep.append(a)
+                    continue
+                fields = g.moments() if self.keep_fields else None
+                if not self.keep_fields:
+                    g.sync()
+                stats.results.append(Result(req.rid, req.arrival_s, adm, now(), req.steps,
+                                            req.nx * req.ny, req.storage, fields))
+                g.close()
+            if len(keep) != len(active):
+                batch.close()
+                batch = None
+                members = None
+            active = keep
+        if batch is not None:
+            batch.close()
+        stats.makespan_s = now()
+        return stats
+
+
+def serve_fifo(requests, realtime: bool = True, storage: str = "f32",
+               keep_fields: bool = False, stream=None) -> ServeStats:
+    """Plain baseline: each request alone, in arrival order, single-grid
+    kernel, stored as `storage` (FP32 by default) whatever it asked for."""
+    lbm.load()
+    stats = ServeStats()
+    t0 = time.perf_counter()
+    for req in sorted(requests, key=lambda r: r.arrival_s):
+        if realtime:
+            wait = req.arrival_s - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+        start = time.perf_counter() - t0
+        with lbm.Grid(req.nx, req.ny, req.tau, req.c2, storage, stream=stream) as g:
+            g.init(*_fields(req))
+            g.step(req.steps)
+            fields = g.moments() if keep_fields else None
+            if not keep_fields:
+                g.sync()
+        stats.results.append(Result(req.rid, req.arrival_s, start, time.perf_counter() - t0,
+                                    req.steps, req.nx * req.ny, storage, fields))
+        stats.lattice_updates += req.steps * req.nx * req.ny
+        stats.max_active = 1
+    stats.makespan_s = time.perf_counter() - t0
+    return stats
+
+
+def scaled_trace(count: int, rate_hz: float, seed: int = 5, **kw):
+    """The serving trace with a chosen arrival rate (for a load below capacity)."""
+    return workloads.serve_trace(count=count, rate_hz=rate_hz, seed=seed, **kw)

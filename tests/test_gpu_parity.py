@@ -78,7 +78,7 @@ def test_every_tile_configuration_bitwise_identical(lbm):
     for vec in (1, 2, 4):
         for rows in (1, 3, 16, 64):
             for warps in (1, 4, 8):
-                for stages in ((0, 2, 3, 4) if vec == 4 else (0,)):
+                for stages in {4: (0, 2, 3, 4), 2: (0, 1)}.get(vec, (0,)):
                     with lbm.Grid(nx, ny, 0.7, 0.15, "f32") as g:
                         g.set_config(vec, rows, warps)
                         g.set_pipeline(stages)
@@ -97,7 +97,8 @@ def test_sixteen_bit_tile_configurations_bitwise(lbm, storage):
     f = _fields(nx, ny, seed=6)
     states = []
     for vec, rows, warps, stages in ((8, 16, 4, 0), (8, 16, 4, 4), (8, 5, 8, 2), (8, 33, 1, 3),
-                                     (4, 7, 2, 0), (2, 5, 8, 0), (1, 64, 1, 0)):
+                                     (4, 7, 2, 0), (4, 7, 2, 1), (4, 16, 8, 1), (2, 5, 8, 0),
+                                     (1, 64, 1, 0)):
         with lbm.Grid(nx, ny, 0.9, 0.3, storage) as g:
             g.set_config(vec, rows, warps)
             g.set_pipeline(stages)
