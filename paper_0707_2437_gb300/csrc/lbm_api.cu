@@ -575,7 +575,8 @@ extern "C" int lbm_tune(lbm_t h, const char *cache_path) {
             if (r > 2 * h->ny && r != 4) continue;
             for (int w : warpss) {
                 const bool tma_ok = v == tma_vec(h->storage);
-                const bool pf_ok = v == prefetch_vec(h->storage);
+                const bool pf_ok =
+                    v == prefetch_vec(h->storage) || (h->storage != ST_F32 && v == 8);
                 for (int nst = 0; nst <= 4; ++nst) {
                     if (nst == 1 && !pf_ok) continue;
                     if (nst >= 2 && !tma_ok) continue;

@@ -473,7 +473,6 @@ struct Walker {
     // of the two halo sites, from the raw rows `w` and the helper value `g`.
     __device__ __forceinline__ void finish_pull(uint32_t (&w)[9][NW], uint32_t g, float (&d)[V],
                                                 float &dl, float &dr) const {
-        __syncwarp();  // the exchanges below need every lane's loaded values
         // e_x = +1 directions take the left neighbour's last element.
         {
             uint32_t e1 = __shfl_sync(FULL, g, 9);

@@ -32,7 +32,7 @@ inline bool uses_tma(int storage, const TileCfg &c) {
 // Sites per lane of the prefetching register walk (8 bytes of elements).
 inline int prefetch_vec(int storage) { return storage == ST_F32 ? 2 : 4; }
 inline bool uses_prefetch(int storage, const TileCfg &c) {
-    return c.stages == 1 && c.vec == prefetch_vec(storage);
+    return c.stages == 1 && (c.vec == prefetch_vec(storage) || (storage != ST_F32 && c.vec == 8));
 }
 
 struct StepGeom {

@@ -48,6 +48,24 @@ __global__ void __launch_bounds__(256, 2)
         w.run(y0, y1, (seg & 1) ? -1 : 1, c);
 }
 
+// Wide prefetching walk for the 16-bit kinds: 8 sites per lane (128-bit
+// loads) with one row prefetched; three rows of 8 sites need more than 128
+// registers, so this kernel runs one 8-warp block per SM (up to 255 registers).
+template <int S>
+__global__ void __launch_bounds__(256, 1)
+    k_step_wide(const void *__restrict__ fin, void *__restrict__ fout, int nx, int ny, size_t P,
+                int nstrips, long long ntiles, int rows, Coef c) {
+    long long tile = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (tile >= ntiles) return;
+    int strip = (int)(tile % nstrips);
+    int seg = (int)(tile / nstrips);
+    int x0 = strip * 32 * 8;
+    int y0 = seg * rows;
+    int y1 = min(ny, y0 + rows);
+    Walker<S, 8> w(fin, fout, nx, ny, P, x0);
+    w.run_prefetch(y0, y1, (seg & 1) ? -1 : 1, c);
+}
+
 // Bulk-copy pipeline variant: one warp per tile, NST shared-memory stages per
 // warp (dynamic shared memory: barriers first, then the stages).
 constexpr unsigned long long kWaitLimitNs = 1000000000ULL;  // 1 s per wait
@@ -78,7 +96,13 @@ static Err launch_step_t(const TileCfg &cfg, const void *fin, void *fout, int nx
                          const Coef &c, cudaStream_t st) {
     StepGeom g = step_geom(nx, ny, cfg);
     long long blocks = (g.ntiles + cfg.warps - 1) / cfg.warps;
-    if (uses_prefetch(S, cfg)) {
+    if (uses_prefetch(S, cfg) && V == 8) {
+        if constexpr (S != ST_F32 && V == 8)
+            k_step_wide<S><<<(unsigned)blocks, 32 * cfg.warps, 0, st>>>(
+                fin, fout, nx, ny, P, g.nstrips, g.ntiles, cfg.rows, c);
+        else
+            return cudaErrorInvalidValue;
+    } else if (uses_prefetch(S, cfg)) {
         if constexpr (Pack<S, V>::BYTES == 8)
             k_step<S, V, true><<<(unsigned)blocks, 32 * cfg.warps, 0, st>>>(
                 fin, fout, nx, ny, P, g.nstrips, g.ntiles, cfg.rows, c);

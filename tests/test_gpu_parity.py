@@ -97,7 +97,8 @@ def test_sixteen_bit_tile_configurations_bitwise(lbm, storage):
     f = _fields(nx, ny, seed=6)
     states = []
     for vec, rows, warps, stages in ((8, 16, 4, 0), (8, 16, 4, 4), (8, 5, 8, 2), (8, 33, 1, 3),
-                                     (4, 7, 2, 0), (4, 7, 2, 1), (4, 16, 8, 1), (2, 5, 8, 0),
+                                     (4, 7, 2, 0), (4, 7, 2, 1), (4, 16, 8, 1), (8, 9, 8, 1), (8, 3, 2, 1),
+                                     (2, 5, 8, 0),
                                      (1, 64, 1, 0)):
         with lbm.Grid(nx, ny, 0.9, 0.3, storage) as g:
             g.set_config(vec, rows, warps)
