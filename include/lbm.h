@@ -62,6 +62,10 @@ extern "C" {
 #define LBM_F16D 1
 #define LBM_BF16D 2
 
+/* Rounding of the 16-bit stores (lbm_set_rounding). */
+#define LBM_ROUND_NEAREST 0     /* round to nearest even (default) */
+#define LBM_ROUND_STOCHASTIC 1  /* unbiased stochastic rounding */
+
 /* Fields for lbm_mode. */
 #define LBM_FIELD_RHO 0   /* rho - rho0 */
 #define LBM_FIELD_UX 1
@@ -169,6 +173,20 @@ int lbm_get_config(lbm_t h, int *vec, int *rows, int *warps);
  * the pipeline is in use with the current vec. */
 int lbm_set_pipeline(lbm_t h, int stages);
 int lbm_get_pipeline(lbm_t h, int *stages, int *active);
+
+/* Rounding of the 16-bit stores.  With LBM_ROUND_NEAREST a stored value whose
+ * per-step change is below half a unit in the last place never changes, so
+ * slow processes freeze: the viscous decay of a shear wave of amplitude 1e-3
+ * and wavelength 256 (tau = 0.9) stops completely in FP16 storage.
+ * LBM_ROUND_STOCHASTIC rounds up with probability equal to the discarded
+ * fraction (1/256 resolution), so each stored value is the FP32 result in
+ * expectation; the random bits are a hash of (site, direction, step), so runs
+ * stay deterministic and independent of the tile configuration and of
+ * batching.  Stochastic rounding uses the register walks (vec 1, 2 or 4; it
+ * moves a vec of 8 to 4 and turns the bulk-copy pipeline off).  FP32 storage
+ * accepts only LBM_ROUND_NEAREST. */
+int lbm_set_rounding(lbm_t h, int mode);
+int lbm_get_rounding(lbm_t h, int *mode);
 
 /* Autotuner: times the valid tile configurations on this grid (without
  * changing its state) and keeps the fastest.  If cache_path is not NULL the

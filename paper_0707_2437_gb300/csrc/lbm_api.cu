@@ -98,6 +98,8 @@ static TileCfg default_cfg(int storage, int nx, int ny) {
 
 // Device status word written by kernels whose bounded waits ran out.
 static int *status_ptr(lbm_grid *h) { return reinterpret_cast<int *>(h->scratch + 8); }
+// Device step counter that seeds stochastic rounding inside graph replays.
+static uint32_t *step_ptr(lbm_grid *h) { return reinterpret_cast<uint32_t *>(h->scratch + 9); }
 
 // Reads and clears the status word (the stream must be idle).
 static int take_status(lbm_grid *h) {
@@ -236,7 +238,7 @@ extern "C" int lbm_init(lbm_t h, const double *rho, const double *ux, const doub
 // One step launch from buf[cur] to buf[cur ^ 1] (no bookkeeping).
 static cudaError_t launch_one(lbm_grid *h, int from) {
     return launch_step(h->storage, h->cfg, h->buf[from], h->buf[from ^ 1], h->nx, h->ny, h->P,
-                       h->coef, status_ptr(h), h->stream);
+                       h->coef, status_ptr(h), h->rounding, nullptr, (uint32_t)h->t, h->stream);
 }
 
 static const int kGraphPairs = 16;   // a graph holds 32 steps
@@ -253,7 +255,7 @@ static int build_graphs(lbm_grid *h) {
             for (int k = 0; k < 2 * kGraphPairs && e == cudaSuccess; ++k)
                 e = launch_step(h->storage, h->cfg, h->buf[(start + k) & 1],
                                 h->buf[(start + k + 1) & 1], h->nx, h->ny, h->P, h->coef,
-                                status_ptr(h), cs);
+                                status_ptr(h), h->rounding, step_ptr(h), (uint32_t)k, cs);
             cudaError_t e2 = cudaStreamEndCapture(cs, &g);
             if (e == cudaSuccess) e = e2;
         }
@@ -299,6 +301,7 @@ extern "C" int lbm_step(lbm_t h, long long n) {
         }
         long long per = 2LL * h->graph_pairs;
         while (n >= per) {
+            if (h->rounding) CK(launch_set_u32(step_ptr(h), (uint32_t)h->t, h->stream));
             CK(cudaGraphLaunch(h->graph[h->cur], h->stream));
             n -= per;
             h->t += per;  // an even number of steps leaves cur unchanged
@@ -438,6 +441,8 @@ extern "C" int lbm_set_config(lbm_t h, int vec, int rows, int warps) {
     if (!valid_vec(h->storage, h->nx, vec))
         return fail(LBM_EINVAL, "lbm_set_config: vec must be 1, 2, 4 (or 8 for 16-bit) and divide nx");
     if (rows < 1 || rows > 4096) return fail(LBM_EINVAL, "lbm_set_config: rows in [1, 4096]");
+    if (h->rounding && vec == 8)
+        return fail(LBM_EINVAL, "lbm_set_config: stochastic rounding uses vec 1, 2 or 4");
     if (warps != 1 && warps != 2 && warps != 4 && warps != 8)
         return fail(LBM_EINVAL, "lbm_set_config: warps in {1, 2, 4, 8}");
     if (h->cfg.vec != vec || h->cfg.rows != rows || h->cfg.warps != warps) {
@@ -455,12 +460,38 @@ extern "C" int lbm_set_pipeline(lbm_t h, int stages) {
     if (!h) return fail(LBM_EINVAL, "lbm_set_pipeline: NULL handle");
     if (stages < 0 || stages > 4)
         return fail(LBM_EINVAL, "lbm_set_pipeline: stages must be 0..4");
+    if (h->rounding && stages >= 2)
+        return fail(LBM_EINVAL, "lbm_set_pipeline: stochastic rounding uses the register walk");
     if (h->cfg.stages != stages) {
         CK(cudaStreamSynchronize(h->stream));
         drop_graphs(h);
     }
     h->cfg.stages = stages;
     CK(prepare_step(h->storage, h->cfg));
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_rounding(lbm_t h, int mode) {
+    if (!h) return fail(LBM_EINVAL, "lbm_set_rounding: NULL handle");
+    if (mode != LBM_ROUND_NEAREST && mode != LBM_ROUND_STOCHASTIC)
+        return fail(LBM_EINVAL, "lbm_set_rounding: unknown mode");
+    if (mode == LBM_ROUND_STOCHASTIC && h->storage == ST_F32)
+        return fail(LBM_EINVAL, "lbm_set_rounding: stochastic rounding needs 16-bit storage");
+    CK(cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
+    h->rounding = mode;
+    if (mode == LBM_ROUND_STOCHASTIC) {
+        // The stochastic-rounding walks are the register walks with vec <= 4.
+        if (h->cfg.vec == 8) h->cfg.vec = 4;
+        if (h->cfg.stages >= 2) h->cfg.stages = 0;
+    }
+    CK(prepare_step(h->storage, h->cfg));
+    return LBM_OK;
+}
+
+extern "C" int lbm_get_rounding(lbm_t h, int *mode) {
+    if (!h || !mode) return fail(LBM_EINVAL, "lbm_get_rounding: NULL argument");
+    *mode = h->rounding;
     return LBM_OK;
 }
 
@@ -571,6 +602,7 @@ extern "C" int lbm_tune(lbm_t h, const char *cache_path) {
     const int warpss[] = {2, 4, 8};
     for (int v : vecs) {
         if (!valid_vec(h->storage, h->nx, v)) continue;
+        if (h->rounding && v == 8) continue;
         for (int r : rowss) {
             if (r > 2 * h->ny && r != 4) continue;
             for (int w : warpss) {
@@ -579,7 +611,7 @@ extern "C" int lbm_tune(lbm_t h, const char *cache_path) {
                     v == prefetch_vec(h->storage) || (h->storage != ST_F32 && v == 8);
                 for (int nst = 0; nst <= 4; ++nst) {
                     if (nst == 1 && !pf_ok) continue;
-                    if (nst >= 2 && !tma_ok) continue;
+                    if (nst >= 2 && (!tma_ok || h->rounding)) continue;
                     TileCfg c;
                     c.vec = v;
                     c.rows = r;

@@ -26,7 +26,8 @@ struct GridDesc {
     void *buf[2];
     size_t P;
     int nx, ny;
-    int kind;  // storage * 16 + vec (16-bit vec 4 uses the prefetching walk)
+    int kind;  // storage * 16 + vec, + 8 for stochastic rounding (16-bit vec 4
+               // uses the prefetching walk)
     int pad;
     Coef c;
 };
@@ -82,9 +83,10 @@ __device__ bool grid_barrier(unsigned *bar, int *status, unsigned long long time
     return ok_sh != 0;
 }
 
-template <int S, int V, bool PF = false>
-__device__ __noinline__ void do_tile(const GridDesc &g, int par, const Tile &t) {
-    Walker<S, V, LD_CG> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P, t.x0);
+template <int S, int V, bool PF = false, int RND = 0>
+__device__ __noinline__ void do_tile(const GridDesc &g, int par, const Tile &t, uint32_t step) {
+    Walker<S, V, LD_CG, RND> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P, t.x0);
+    if constexpr (RND) w.rstep = step;
     if constexpr (PF)
         w.run_prefetch(t.y0, t.y1, t.dir, g.c);
     else
@@ -94,7 +96,8 @@ __device__ __noinline__ void do_tile(const GridDesc &g, int par, const Tile &t) 
 __global__ void __launch_bounds__(32 * kBatchWarps, 3)
     k_batch(const GridDesc *__restrict__ grids, const Tile *__restrict__ tiles, int ntiles,
             const long long *__restrict__ limit, const int *__restrict__ parity0,
-            long long nsteps, unsigned *bar, int *status, unsigned long long timeout_ns) {
+            const uint32_t *__restrict__ t0, long long nsteps, unsigned *bar, int *status,
+            unsigned long long timeout_ns) {
     const int wpb = blockDim.x >> 5;
     const int nwarps = gridDim.x * wpb;
     const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
@@ -104,24 +107,37 @@ __global__ void __launch_bounds__(32 * kBatchWarps, 3)
             if (k >= limit[t.grid]) continue;
             const GridDesc &g = grids[t.grid];
             const int par = (parity0[t.grid] + (int)(k & 1)) & 1;
+            const uint32_t step = t0[t.grid] + (uint32_t)k;
             switch (g.kind) {
                 case ST_F32 * 16 + 4:
-                    do_tile<ST_F32, 4>(g, par, t);
+                    do_tile<ST_F32, 4>(g, par, t, step);
                     break;
                 case ST_F32 * 16 + 1:
-                    do_tile<ST_F32, 1>(g, par, t);
+                    do_tile<ST_F32, 1>(g, par, t, step);
                     break;
                 case ST_F16 * 16 + 4:
-                    do_tile<ST_F16, 4, true>(g, par, t);
+                    do_tile<ST_F16, 4, true>(g, par, t, step);
                     break;
                 case ST_F16 * 16 + 1:
-                    do_tile<ST_F16, 1>(g, par, t);
+                    do_tile<ST_F16, 1>(g, par, t, step);
                     break;
                 case ST_BF16 * 16 + 4:
-                    do_tile<ST_BF16, 4, true>(g, par, t);
+                    do_tile<ST_BF16, 4, true>(g, par, t, step);
                     break;
                 case ST_BF16 * 16 + 1:
-                    do_tile<ST_BF16, 1>(g, par, t);
+                    do_tile<ST_BF16, 1>(g, par, t, step);
+                    break;
+                case ST_F16 * 16 + 8 + 4:
+                    do_tile<ST_F16, 4, true, 1>(g, par, t, step);
+                    break;
+                case ST_F16 * 16 + 8 + 1:
+                    do_tile<ST_F16, 1, false, 1>(g, par, t, step);
+                    break;
+                case ST_BF16 * 16 + 8 + 4:
+                    do_tile<ST_BF16, 4, true, 1>(g, par, t, step);
+                    break;
+                case ST_BF16 * 16 + 8 + 1:
+                    do_tile<ST_BF16, 1, false, 1>(g, par, t, step);
                     break;
                 default:
                     break;
@@ -148,11 +164,13 @@ struct lbm_batch {
     int ntiles = 0;
     long long *d_limit = nullptr;
     int *d_parity = nullptr;
+    uint32_t *d_t0 = nullptr;
     unsigned *d_bar = nullptr;
     int *d_status = nullptr;
     // pinned host mirrors of the per-call arrays
     long long *h_limit = nullptr;
     int *h_parity = nullptr;
+    uint32_t *h_t0 = nullptr;
     int *h_status = nullptr;
     cudaEvent_t copied = nullptr;  // the per-call arrays have been read
     // graph cache (one step count)
@@ -201,7 +219,7 @@ static int build_worklist(lbm_batch *b) {
         d.nx = g->nx;
         d.ny = g->ny;
         int v = batch_vec(g);
-        d.kind = g->storage * 16 + v;
+        d.kind = g->storage * 16 + v + (g->rounding ? 8 : 0);
         d.pad = 0;
         d.c = g->coef;
         int w = 32 * v;
@@ -230,10 +248,12 @@ extern "C" int lbm_batch_destroy(lbm_batch_t b) {
     cudaFree(b->d_tiles);
     cudaFree(b->d_limit);
     cudaFree(b->d_parity);
+    cudaFree(b->d_t0);
     cudaFree(b->d_bar);
     cudaFree(b->d_status);
     if (b->h_limit) cudaFreeHost(b->h_limit);
     if (b->h_parity) cudaFreeHost(b->h_parity);
+    if (b->h_t0) cudaFreeHost(b->h_t0);
     if (b->h_status) cudaFreeHost(b->h_status);
     if (b->copied) cudaEventDestroy(b->copied);
     delete b;
@@ -266,10 +286,12 @@ extern "C" int lbm_batch_create(const lbm_t *grids, int n, lbm_batch_t *out) {
     if (e == cudaSuccess) e = cudaMalloc(&b->d_grids, sizeof(GridDesc) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_limit, sizeof(long long) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_parity, sizeof(int) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_t0, sizeof(uint32_t) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_bar, sizeof(unsigned) * 2);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_limit, sizeof(long long) * n);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_parity, sizeof(int) * n);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_t0, sizeof(uint32_t) * n);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_status, sizeof(int));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
@@ -305,6 +327,8 @@ static cudaError_t enqueue(lbm_batch *b, long long n, cudaStream_t st) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_parity, b->h_parity, sizeof(int) * ng, cudaMemcpyHostToDevice,
                             st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_t0, b->h_t0, sizeof(uint32_t) * ng, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned) * 2, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -313,12 +337,13 @@ static cudaError_t enqueue(lbm_batch *b, long long n, cudaStream_t st) {
     int ntiles = b->ntiles;
     const long long *lim = b->d_limit;
     const int *par = b->d_parity;
+    const uint32_t *t0 = b->d_t0;
     unsigned *bar = b->d_bar;
     int *status = b->d_status;
     unsigned long long to = b->timeout_ns;
     void *args[] = {(void *)&grids, (void *)&tiles, (void *)&ntiles, (void *)&lim,
-                    (void *)&par,   (void *)&n,     (void *)&bar,    (void *)&status,
-                    (void *)&to};
+                    (void *)&par,   (void *)&t0,    (void *)&n,      (void *)&bar,
+                    (void *)&status, (void *)&to};
     return cudaLaunchCooperativeKernel((const void *)k_batch, dim3(grid_blocks(b)),
                                        dim3(32 * kBatchWarps), args, 0, st);
 }
@@ -331,6 +356,7 @@ static int run_batch(lbm_batch *b, long long n, const long long *limits, bool ad
         long long lim = limits ? std::max(0LL, std::min(n, limits[k])) : n;
         b->h_limit[k] = lim;
         b->h_parity[k] = b->grids[k]->cur;
+        b->h_t0[k] = (uint32_t)b->grids[k]->t;
     }
     cudaError_t e = cudaSuccess;
     if (b->use_graph) {

@@ -241,6 +241,62 @@ __device__ __forceinline__ uint32_t pack1(float v) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Stochastic rounding of the 16-bit stores (optional).  With round to nearest
+// a stored value that changes by less than half a unit in the last place per
+// step never changes at all, which freezes slow processes such as the viscous
+// decay of long shear waves.  Stochastic rounding rounds up with probability
+// equal to the discarded fraction (resolved to 1/256 here), so the expected
+// stored value equals the FP32 result.  The random bits are a counter-based
+// hash of (site, step): deterministic, and independent of the tile
+// configuration and of batching, so results stay bitwise reproducible.
+
+// 32-bit integer mixing function (xor-shift / multiply, the "lowbias32"
+// constants found by Wellons' hash prospector).
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// Nine 8-bit dithers (one per direction) for a site and step, packed in 3 words.
+struct Dither {
+    uint32_t w0, w1, w2;
+    __device__ __forceinline__ uint32_t get(int i) const {
+        const uint32_t w = i < 4 ? w0 : (i < 8 ? w1 : w2);
+        return (w >> (8 * (i & 3))) & 0xffu;
+    }
+};
+__device__ __forceinline__ Dither site_dither(uint32_t site, uint32_t step) {
+    const uint32_t b = mix32(site ^ mix32(step * 0x9e3779b9u + 0x632be5abu));
+    Dither d;
+    d.w0 = b;
+    d.w1 = mix32(b + 0x85157af5u);
+    d.w2 = mix32(b + 0x3c6ef372u);
+    return d;
+}
+
+// FP32 -> 16-bit with round up probability equal to the discarded fraction:
+// add the dither below the kept bits of the magnitude, then truncate.  FP16
+// values below the smallest normal (2^-14) round to nearest instead (their
+// spacing is fixed, so a shift of the dither would not match it).
+template <int S>
+__device__ __forceinline__ uint32_t sr_round(float x, uint32_t d) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t sgn = b & 0x80000000u;
+    const uint32_t mag = b & 0x7fffffffu;
+    if constexpr (S == ST_BF16) {
+        return (sgn | (mag + (d << 8))) >> 16;  // 16 discarded bits
+    } else {
+        if (mag < 0x38800000u) return (uint32_t)__half_as_ushort(__float2half_rn(x));
+        const float y = __uint_as_float(sgn | (mag + (d << 5)));  // 13 discarded bits
+        return (uint32_t)__half_as_ushort(__float2half_rz(y));
+    }
+}
+
 // Sites per packed word: the 16-bit kinds convert two sites at a time.
 template <int S, int V>
 struct SitesPerWord {
@@ -363,10 +419,12 @@ __device__ __forceinline__ void pair_out(float hi, float hopp, float ej, float e
 //                  (the left neighbour value lane 0 needs for its pull)
 //   lanes 16..24 : pulled f_i at the column after the strip, i = lane - 16
 //   lanes 25..27 : f_i at that column for the directions with e_x = -1
-template <int S, int V, int LD = LD_NC>
+template <int S, int V, int LD = LD_NC, int RND = 0>
 struct Walker {
     static constexpr int NW = Pack<S, V>::NW;
     using T = typename StoreT<S>::T;
+    static_assert(RND == 0 || S != ST_F32, "stochastic rounding applies to 16-bit storage");
+    uint32_t rstep = 0;  // step number that seeds stochastic rounding
 
     const T *__restrict__ fin;
     T *__restrict__ fout;
@@ -458,14 +516,38 @@ struct Walker {
             }
         }
     }
-    __device__ __forceinline__ static void pack_sites(
-        uint32_t (&w)[9][NW], int v0, const float (&h)[SitesPerWord<S, V>::value][9]) {
+    __device__ __forceinline__ void pack_sites(
+        uint32_t (&w)[9][NW], int v0, const float (&h)[SitesPerWord<S, V>::value][9],
+        int r) const {
+        constexpr int SP = SitesPerWord<S, V>::value;
+        if constexpr (RND == 0) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            if constexpr (SitesPerWord<S, V>::value == 2)
-                w[i][v0 >> 1] = pack2<S>(h[0][i], h[1][i]);
-            else
-                set_elem<S, V>(w[i], v0, h[0][i]);
+            for (int i = 0; i < 9; ++i) {
+                if constexpr (SP == 2)
+                    w[i][v0 >> 1] = pack2<S>(h[0][i], h[1][i]);
+                else
+                    set_elem<S, V>(w[i], v0, h[0][i]);
+            }
+        } else {
+            const uint32_t site = (uint32_t)r * (uint32_t)nx + (uint32_t)(xs + v0);
+            const Dither da = site_dither(site, rstep);
+            if constexpr (SP == 2) {
+                const Dither db = site_dither(site + 1u, rstep);
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    w[i][v0 >> 1] = sr_round<S>(h[0][i], da.get(i)) |
+                                    (sr_round<S>(h[1][i], db.get(i)) << 16);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const uint32_t b = sr_round<S>(h[0][i], da.get(i));
+                    if constexpr (V == 1)
+                        w[i][0] = b;
+                    else
+                        w[i][v0 >> 1] = (v0 & 1) ? __byte_perm(w[i][v0 >> 1], b, 0x5410)
+                                                 : __byte_perm(w[i][v0 >> 1], b, 0x3254);
+                }
+            }
         }
     }
 
@@ -568,7 +650,7 @@ struct Walker {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) hs[i] = o[i];
             }
-            pack_sites(w, v0, h);
+            pack_sites(w, v0, h, r);
         }
         if (!act) return;
         const size_t row = (size_t)r * nx + xs;

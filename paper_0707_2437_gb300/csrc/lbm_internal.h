@@ -62,8 +62,12 @@ Coef make_coef(double tau, double c2, double rho0);
 
 // Kernel launchers (lbm_kernels.cu).  All asynchronous on `st`.
 // `status` (device int) receives STATUS_TIMEOUT if a pipeline wait runs out.
+// rnd = 1: stochastic rounding of 16-bit stores, seeded by the step number
+// (*tdev if tdev is not NULL, plus toff).
 Err launch_step(int storage, const TileCfg &cfg, const void *fin, void *fout, int nx, int ny,
-                size_t P, const Coef &c, int *status, cudaStream_t st);
+                size_t P, const Coef &c, int *status, int rnd, const uint32_t *tdev, uint32_t toff,
+                cudaStream_t st);
+Err launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t st);
 // Sets the kernel attributes a configuration needs (dynamic shared memory);
 // call before the first launch or capture of that configuration.
 Err prepare_step(int storage, const TileCfg &cfg);
@@ -97,6 +101,7 @@ struct lbm_grid {
     int device = 0;
     vss::Coef coef{};
     vss::TileCfg cfg{};
+    int rounding = 0;             // 1: stochastic rounding of 16-bit stores
     double *scratch = nullptr;    // reduction partials + results
     double *host_out = nullptr;   // pinned, 8 doubles
     // CUDA graphs of 2*graph_pairs steps starting from buffer 0 or buffer 1

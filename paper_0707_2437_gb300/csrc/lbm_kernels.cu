@@ -28,10 +28,11 @@ bool valid_vec(int storage, int nx, int vec) {
 // ---------------------------------------------------------------------------
 // Fused step: one warp per (strip, row segment) tile.
 
-template <int S, int V, bool PF>
+template <int S, int V, bool PF, int RND = 0>
 __global__ void __launch_bounds__(256, 2)
     k_step(const void *__restrict__ fin, void *__restrict__ fout, int nx, int ny, size_t P,
-           int nstrips, long long ntiles, int rows, Coef c) {
+           int nstrips, long long ntiles, int rows, Coef c, const uint32_t *tdev,
+           uint32_t toff) {
     long long tile = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (tile >= ntiles) return;  // whole warps leave together
     int strip = (int)(tile % nstrips);
@@ -39,7 +40,10 @@ __global__ void __launch_bounds__(256, 2)
     int x0 = strip * 32 * V;
     int y0 = seg * rows;
     int y1 = min(ny, y0 + rows);
-    Walker<S, V> w(fin, fout, nx, ny, P, x0);
+    Walker<S, V, LD_NC, RND> w(fin, fout, nx, ny, P, x0);
+    // Stochastic rounding is seeded by the step being computed: a device
+    // counter (set before each graph replay) plus this launch's offset.
+    if constexpr (RND) w.rstep = (tdev ? *tdev : 0u) + toff;
     // Neighbouring segments walk in opposite directions so that the two rows
     // they share are read by both at about the same time.
     if constexpr (PF)
@@ -91,26 +95,26 @@ __global__ void __launch_bounds__(256, 2)
     w.run(y0, y1, (seg & 1) ? -1 : 1, c, status);
 }
 
-template <int S, int V>
+template <int S, int V, int RND>
 static Err launch_step_t(const TileCfg &cfg, const void *fin, void *fout, int nx, int ny, size_t P,
-                         const Coef &c, cudaStream_t st) {
+                         const Coef &c, const uint32_t *tdev, uint32_t toff, cudaStream_t st) {
     StepGeom g = step_geom(nx, ny, cfg);
     long long blocks = (g.ntiles + cfg.warps - 1) / cfg.warps;
     if (uses_prefetch(S, cfg) && V == 8) {
-        if constexpr (S != ST_F32 && V == 8)
+        if constexpr (S != ST_F32 && V == 8 && RND == 0)
             k_step_wide<S><<<(unsigned)blocks, 32 * cfg.warps, 0, st>>>(
                 fin, fout, nx, ny, P, g.nstrips, g.ntiles, cfg.rows, c);
         else
             return cudaErrorInvalidValue;
     } else if (uses_prefetch(S, cfg)) {
         if constexpr (Pack<S, V>::BYTES == 8)
-            k_step<S, V, true><<<(unsigned)blocks, 32 * cfg.warps, 0, st>>>(
-                fin, fout, nx, ny, P, g.nstrips, g.ntiles, cfg.rows, c);
+            k_step<S, V, true, RND><<<(unsigned)blocks, 32 * cfg.warps, 0, st>>>(
+                fin, fout, nx, ny, P, g.nstrips, g.ntiles, cfg.rows, c, tdev, toff);
         else
             return cudaErrorInvalidValue;
     } else {
-        k_step<S, V, false><<<(unsigned)blocks, 32 * cfg.warps, 0, st>>>(
-            fin, fout, nx, ny, P, g.nstrips, g.ntiles, cfg.rows, c);
+        k_step<S, V, false, RND><<<(unsigned)blocks, 32 * cfg.warps, 0, st>>>(
+            fin, fout, nx, ny, P, g.nstrips, g.ntiles, cfg.rows, c, tdev, toff);
     }
     return cudaGetLastError();
 }
@@ -164,7 +168,25 @@ Err prepare_step(int storage, const TileCfg &cfg) {
 
 template <int S>
 static Err launch_step_s(const TileCfg &cfg, const void *fin, void *fout, int nx, int ny, size_t P,
-                         const Coef &c, int *status, cudaStream_t st) {
+                         const Coef &c, int *status, int rnd, const uint32_t *tdev,
+                         uint32_t toff, cudaStream_t st) {
+    if (rnd) {
+        // Stochastic rounding: register walks with vec 1, 2 or 4.
+        if constexpr (S == ST_F32) {
+            return cudaErrorInvalidValue;
+        } else {
+            switch (cfg.vec) {
+                case 1:
+                    return launch_step_t<S, 1, 1>(cfg, fin, fout, nx, ny, P, c, tdev, toff, st);
+                case 2:
+                    return launch_step_t<S, 2, 1>(cfg, fin, fout, nx, ny, P, c, tdev, toff, st);
+                case 4:
+                    return launch_step_t<S, 4, 1>(cfg, fin, fout, nx, ny, P, c, tdev, toff, st);
+                default:
+                    return cudaErrorInvalidValue;
+            }
+        }
+    }
     if (uses_tma(S, cfg)) {
         switch (cfg.stages) {
             case 2:
@@ -179,13 +201,14 @@ static Err launch_step_s(const TileCfg &cfg, const void *fin, void *fout, int nx
     }
     switch (cfg.vec) {
         case 1:
-            return launch_step_t<S, 1>(cfg, fin, fout, nx, ny, P, c, st);
+            return launch_step_t<S, 1, 0>(cfg, fin, fout, nx, ny, P, c, tdev, toff, st);
         case 2:
-            return launch_step_t<S, 2>(cfg, fin, fout, nx, ny, P, c, st);
+            return launch_step_t<S, 2, 0>(cfg, fin, fout, nx, ny, P, c, tdev, toff, st);
         case 4:
-            return launch_step_t<S, 4>(cfg, fin, fout, nx, ny, P, c, st);
+            return launch_step_t<S, 4, 0>(cfg, fin, fout, nx, ny, P, c, tdev, toff, st);
         case 8:
-            if constexpr (S != ST_F32) return launch_step_t<S, 8>(cfg, fin, fout, nx, ny, P, c, st);
+            if constexpr (S != ST_F32)
+                return launch_step_t<S, 8, 0>(cfg, fin, fout, nx, ny, P, c, tdev, toff, st);
             return cudaErrorInvalidValue;
         default:
             return cudaErrorInvalidValue;
@@ -193,17 +216,26 @@ static Err launch_step_s(const TileCfg &cfg, const void *fin, void *fout, int nx
 }
 
 Err launch_step(int storage, const TileCfg &cfg, const void *fin, void *fout, int nx, int ny,
-                size_t P, const Coef &c, int *status, cudaStream_t st) {
+                size_t P, const Coef &c, int *status, int rnd, const uint32_t *tdev, uint32_t toff,
+                cudaStream_t st) {
     switch (storage) {
         case ST_F32:
-            return launch_step_s<ST_F32>(cfg, fin, fout, nx, ny, P, c, status, st);
+            return launch_step_s<ST_F32>(cfg, fin, fout, nx, ny, P, c, status, rnd, tdev, toff, st);
         case ST_F16:
-            return launch_step_s<ST_F16>(cfg, fin, fout, nx, ny, P, c, status, st);
+            return launch_step_s<ST_F16>(cfg, fin, fout, nx, ny, P, c, status, rnd, tdev, toff, st);
         case ST_BF16:
-            return launch_step_s<ST_BF16>(cfg, fin, fout, nx, ny, P, c, status, st);
+            return launch_step_s<ST_BF16>(cfg, fin, fout, nx, ny, P, c, status, rnd, tdev, toff,
+                                          st);
         default:
             return cudaErrorInvalidValue;
     }
+}
+
+__global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
+
+Err launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t st) {
+    k_set_u32<<<1, 1, 0, st>>>(p, v);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

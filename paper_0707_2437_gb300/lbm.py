@@ -67,6 +67,8 @@ def load() -> ctypes.CDLL:
             "lbm_get_config": ([vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)], i),
             "lbm_tune": ([vp, ctypes.c_char_p], i),
             "lbm_set_pipeline": ([vp, i], i),
+            "lbm_set_rounding": ([vp, i], i),
+            "lbm_get_rounding": ([vp, ctypes.POINTER(i)], i),
             "lbm_get_pipeline": ([vp, ctypes.POINTER(i), ctypes.POINTER(i)], i),
             "lbm_set_timing": ([vp, i], i),
             "lbm_kernel_ms": ([vp, dp, ctypes.POINTER(ll)], i),
@@ -241,6 +243,16 @@ class Grid:
         _check(self.lib.lbm_get_config(self.h, ctypes.byref(v), ctypes.byref(r), ctypes.byref(w)),
                "lbm_get_config")
         return v.value, r.value, w.value
+
+    def set_rounding(self, mode: str):
+        """'nearest' or 'stochastic' (16-bit storage only)."""
+        _check(self.lib.lbm_set_rounding(self.h, {"nearest": 0, "stochastic": 1}[mode]),
+               "lbm_set_rounding")
+
+    def get_rounding(self) -> str:
+        m = ctypes.c_int()
+        _check(self.lib.lbm_get_rounding(self.h, ctypes.byref(m)), "lbm_get_rounding")
+        return ["nearest", "stochastic"][m.value]
 
     def set_pipeline(self, stages: int):
         _check(self.lib.lbm_set_pipeline(self.h, stages), "lbm_set_pipeline")

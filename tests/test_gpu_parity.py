@@ -134,6 +134,64 @@ def test_pipeline_strip_edges_match_register_walk(lbm, storage, nx, ny):
         assert _err(got, oracle.simulate(*f, 0.8, 0.2, 9)) <= F32_TOL
 
 
+@pytest.mark.parametrize("storage", ["f16d", "bf16d"])
+def test_stochastic_rounding_configs_graphs_and_batch_bitwise(lbm, storage):
+    """Stochastic rounding is seeded by (site, direction, step) only: every
+    register-walk configuration, graph replay against single launches, and
+    the batched kernel give the same bits."""
+    nx, ny = 256, 40
+    f = _fields(nx, ny, seed=21)
+    states = []
+    for vec, rows, warps, stages in ((4, 16, 4, 1), (4, 7, 2, 0), (2, 5, 8, 0), (1, 64, 1, 0)):
+        with lbm.Grid(nx, ny, 0.7, 0.12, storage) as g:
+            g.set_rounding("stochastic")
+            g.set_config(vec, rows, warps)
+            g.set_pipeline(stages)
+            g.init(*f)
+            g.step(37)  # one graph of 32 steps plus single launches
+            states.append(g.get_state()[0])
+    for st in states[1:]:
+        assert np.array_equal(st, states[0])
+    with lbm.Grid(nx, ny, 0.7, 0.12, storage) as g:
+        g.set_rounding("stochastic")
+        g.init(*f)
+        for _ in range(37):
+            g.step(1)
+        assert np.array_equal(g.get_state()[0], states[0])
+    g = lbm.Grid(nx, ny, 0.7, 0.12, storage)
+    g.set_rounding("stochastic")
+    g.init(*f)
+    other = lbm.Grid(64, 64, 0.8, 0.2, "f32")
+    other.init(*_fields(64, 64, seed=3))
+    b = lbm.Batch([g, other])
+    b.step(37)
+    assert b.sync() == 0
+    assert np.array_equal(g.get_state()[0], states[0])
+    b.close()
+    g.close()
+    other.close()
+    # Nearest and stochastic rounding differ (the setting takes effect).
+    with lbm.Grid(nx, ny, 0.7, 0.12, storage) as h:
+        h.init(*f)
+        h.step(37)
+        assert not np.array_equal(h.get_state()[0], states[0])
+
+
+def test_rounding_mode_validation(lbm):
+    with lbm.Grid(64, 8, 0.8, 0.2, "f32") as g:
+        with pytest.raises(lbm.LbmError):
+            g.set_rounding("stochastic")
+    with lbm.Grid(64, 8, 0.8, 0.2, "f16d") as g:
+        g.set_config(8, 16, 4)
+        g.set_rounding("stochastic")
+        assert g.get_config()[0] == 4
+        assert g.get_rounding() == "stochastic"
+        with pytest.raises(lbm.LbmError):
+            g.set_config(8, 16, 4)
+        with pytest.raises(lbm.LbmError):
+            g.set_pipeline(3)
+
+
 def test_graph_replay_equals_single_launches(lbm):
     nx, ny = 96, 64
     f = _fields(nx, ny, seed=7)
