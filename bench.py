@@ -207,6 +207,8 @@ def run_native(args):
             g.init(*workloads.acoustic_shear(r.nx, r.ny, r.amp))
             if args.config:
                 g.set_config(*args.config)
+            if args.rounding != "nearest":
+                g.set_rounding(args.rounding)
             if args.stages is not None:
                 g.set_pipeline(args.stages)
             grids.append(g)
@@ -301,7 +303,7 @@ def run_native(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if storage == "f32" else f"{storage} storage, f32 math",
+        "dtype": "f32" if storage == "f32" else f"{storage} storage ({args.rounding} rounding), f32 math",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grids": len(runs), "nx": runs[0].nx,
                    "ny": runs[0].ny, "storage": storage, "tile": {"vec": cfg[0],
@@ -351,6 +353,8 @@ def run_batch_workload(args):
     for k, r in enumerate(runs):
         st = storages[k % len(storages)]
         g = lbm.Grid(r.nx, r.ny, r.tau, r.c2, st, stream=stream.cuda_stream)
+        if args.rounding != "nearest" and st != "f32":
+            g.set_rounding(args.rounding)
         g.init(*workloads.sine_wave(r.nx, r.ny, r.amp, r.mode))
         grids.append(g)
     b = lbm.Batch(grids)
@@ -358,6 +362,7 @@ def run_batch_workload(args):
         b.set_config(args.batch_rows, 0)
     if args.tune:
         b.tune()
+    bcfg = b.get_config()
     sites = sum(r.nx * r.ny for r in runs)
     alg = sum(r.nx * r.ny * lbm.BYTES_PER_LU[g.storage] for r, g in zip(runs, grids))
     b.step(args.warmup)
@@ -386,7 +391,9 @@ def run_batch_workload(args):
         "dtype": f"{args.storage} storage, f32 math", "data": "synthetic",
         "config": {"workload": f"batch of {len(runs)} uneven grids, sites log-uniform "
                                "64^2..1024^2, aspect 2^U[-2,2]",
-                   "sites": sites, "storage": args.storage, "launch":
+                   "sites": sites, "storage": args.storage, "rounding": args.rounding,
+                   "batch_config": bcfg,
+                   "launch":
                    "one persistent cooperative launch of all steps (CUDA graph)",
                    "l2": f"working set {alg / 1e9:.1f} GB >> 129 MB L2, no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -441,6 +448,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--storage", default="f32", choices=list(BYTES_PER_LU) + ["mixed"])
     ap.add_argument("--workload", default="sweep2048", choices=["sweep2048", "batch", "serve"])
+    ap.add_argument("--rounding", default="nearest", choices=["nearest", "stochastic"],
+                    help="rounding of 16-bit stores")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-rows", type=int, default=0)
     ap.add_argument("--tune", action="store_true")

@@ -225,6 +225,10 @@ int lbm_batch_sync(lbm_batch_t b);
  * kernel; the autotuner picks them with lbm_batch_tune. */
 int lbm_batch_set_config(lbm_batch_t b, int rows, int blocks_per_sm);
 int lbm_batch_tune(lbm_batch_t b);
+/* Current tile height, resident blocks per SM, and whether the batch runs a
+ * kernel specialised for one storage kind (every grid the same storage,
+ * rounding and a vec of 4) rather than the general kernel. */
+int lbm_batch_get_config(lbm_batch_t b, int *rows, int *blocks_per_sm, int *specialised);
 
 /* Barrier wait limit of the batch kernel in microseconds (default 1e6). */
 int lbm_batch_set_timeout_us(lbm_batch_t b, long long us);

@@ -147,6 +147,63 @@ __global__ void __launch_bounds__(32 * kBatchWarps, 3)
     }
 }
 
+// Specialised persistent kernel for a batch whose grids all use one walk
+// (storage, vec, prefetch, rounding): the walk is inlined, so the kernel keeps
+// the single-grid kernel's register budget (128, 16 warps per SM) instead of
+// paying for calls.  Same time-step loop and bounded barrier as k_batch.
+template <int S, int V, bool PF, int RND>
+__global__ void __launch_bounds__(32 * kBatchWarps, 4)
+    k_batch_one(const GridDesc *__restrict__ grids, const Tile *__restrict__ tiles, int ntiles,
+                const long long *__restrict__ limit, const int *__restrict__ parity0,
+                const uint32_t *__restrict__ t0, long long nsteps, unsigned *bar, int *status,
+                unsigned long long timeout_ns) {
+    const int wpb = blockDim.x >> 5;
+    const int nwarps = gridDim.x * wpb;
+    const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+    for (long long k = 0; k < nsteps; ++k) {
+        for (int ti = gw; ti < ntiles; ti += nwarps) {
+            const Tile t = tiles[ti];
+            if (k >= limit[t.grid]) continue;
+            const GridDesc g = grids[t.grid];
+            const int par = (parity0[t.grid] + (int)(k & 1)) & 1;
+            Walker<S, V, LD_CG, RND> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P, t.x0);
+            if constexpr (RND) w.rstep = t0[t.grid] + (uint32_t)k;
+            if constexpr (PF)
+                w.run_prefetch(t.y0, t.y1, t.dir, g.c);
+            else
+                w.run(t.y0, t.y1, t.dir, g.c);
+        }
+        if (k + 1 < nsteps && !grid_barrier(bar, status, timeout_ns)) return;
+    }
+}
+
+using BatchKernel = void (*)(const GridDesc *, const Tile *, int, const long long *, const int *,
+                             const uint32_t *, long long, unsigned *, int *, unsigned long long);
+
+// The kernel for a set of kinds: a specialised one when every grid has the
+// same kind, else the general k_batch.
+BatchKernel kernel_for(const std::vector<int> &kinds) {
+    bool same = true;
+    for (int k : kinds) same = same && k == kinds[0];
+    if (!kinds.empty() && same) {
+        switch (kinds[0]) {
+            case ST_F32 * 16 + 4:
+                return k_batch_one<ST_F32, 4, false, 0>;
+            case ST_F16 * 16 + 4:
+                return k_batch_one<ST_F16, 4, true, 0>;
+            case ST_BF16 * 16 + 4:
+                return k_batch_one<ST_BF16, 4, true, 0>;
+            case ST_F16 * 16 + 8 + 4:
+                return k_batch_one<ST_F16, 4, true, 1>;
+            case ST_BF16 * 16 + 8 + 4:
+                return k_batch_one<ST_BF16, 4, true, 1>;
+            default:
+                break;
+        }
+    }
+    return k_batch;
+}
+
 }  // namespace
 
 struct lbm_batch {
@@ -156,6 +213,7 @@ struct lbm_batch {
     int rows = 16;
     int blocks_per_sm = 0;  // 0: the occupancy limit
     int max_blocks_per_sm = 1;
+    BatchKernel kernel = nullptr;  // k_batch or a specialised k_batch_one
     int sms = 1;
     unsigned long long timeout_ns = 1000000000ULL;
     // device
@@ -236,6 +294,13 @@ static int build_worklist(lbm_batch *b) {
     BCK(cudaMemcpy(b->d_grids, gd.data(), sizeof(GridDesc) * gd.size(), cudaMemcpyHostToDevice));
     BCK(cudaMemcpy(b->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice));
     b->ntiles = (int)tiles.size();
+    std::vector<int> kinds;
+    for (auto &d : gd) kinds.push_back(d.kind);
+    b->kernel = kernel_for(kinds);
+    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->max_blocks_per_sm,
+                                                      (const void *)b->kernel,
+                                                      32 * kBatchWarps, 0));
+    if (b->max_blocks_per_sm < 1) return bfail(LBM_ECUDA, "batch kernel cannot be resident");
     drop_graph(b);
     return LBM_OK;
 }
@@ -278,11 +343,7 @@ extern "C" int lbm_batch_create(const lbm_t *grids, int n, lbm_batch_t *out) {
     cudaError_t e = cudaSuccess;
     cudaDeviceProp prop;
     e = cudaGetDeviceProperties(&prop, b->device);
-    if (e == cudaSuccess) {
-        b->sms = prop.multiProcessorCount;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->max_blocks_per_sm, k_batch,
-                                                          32 * kBatchWarps, 0);
-    }
+    if (e == cudaSuccess) b->sms = prop.multiProcessorCount;
     if (e == cudaSuccess) e = cudaMalloc(&b->d_grids, sizeof(GridDesc) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_limit, sizeof(long long) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_parity, sizeof(int) * n);
@@ -299,10 +360,6 @@ extern "C" int lbm_batch_create(const lbm_t *grids, int n, lbm_batch_t *out) {
         int rc = bcuda(e, "lbm_batch_create");
         lbm_batch_destroy(b);
         return rc;
-    }
-    if (b->max_blocks_per_sm < 1) {
-        lbm_batch_destroy(b);
-        return bfail(LBM_ECUDA, "lbm_batch_create: batch kernel cannot be resident");
     }
     int rc = build_worklist(b);
     if (rc != LBM_OK) {
@@ -344,7 +401,7 @@ static cudaError_t enqueue(lbm_batch *b, long long n, cudaStream_t st) {
     void *args[] = {(void *)&grids, (void *)&tiles, (void *)&ntiles, (void *)&lim,
                     (void *)&par,   (void *)&t0,    (void *)&n,      (void *)&bar,
                     (void *)&status, (void *)&to};
-    return cudaLaunchCooperativeKernel((const void *)k_batch, dim3(grid_blocks(b)),
+    return cudaLaunchCooperativeKernel((const void *)b->kernel, dim3(grid_blocks(b)),
                                        dim3(32 * kBatchWarps), args, 0, st);
 }
 
@@ -435,36 +492,46 @@ extern "C" int lbm_batch_set_timeout_us(lbm_batch_t b, long long us) {
 }
 
 // Times one-step dry runs (the state is not advanced: every grid writes its
-// other buffer) for a few tile heights and occupancies; keeps the fastest.
+// other buffer) for several tile heights at full occupancy; keeps the fastest.
+// A one-step launch does the same per-step work as a step inside a longer
+// launch (the barriers between steps cost microseconds per millisecond step).
 extern "C" int lbm_batch_tune(lbm_batch_t b) {
     if (!b) return bfail(LBM_EINVAL, "lbm_batch_tune: NULL batch");
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0));
     BCK(cudaEventCreate(&e1));
-    int best_rows = b->rows, best_bps = b->blocks_per_sm;
+    int best_rows = b->rows;
     float best = 1e30f;
-    const int rowss[] = {8, 16, 32, 64};
+    const int rowss[] = {8, 12, 16, 24, 32};
     for (int r : rowss) {
-        for (int bps = 1; bps <= b->max_blocks_per_sm; bps *= 2) {
-            int rc = lbm_batch_set_config(b, r, bps);
-            if (rc != LBM_OK) return rc;
-            rc = run_batch(b, 1, nullptr, false);  // warm-up (and graph build)
-            if (rc != LBM_OK) return rc;
-            BCK(cudaEventRecord(e0, b->stream));
-            for (int k = 0; k < 3 && rc == LBM_OK; ++k) rc = run_batch(b, 1, nullptr, false);
-            if (rc != LBM_OK) return rc;
-            BCK(cudaEventRecord(e1, b->stream));
-            BCK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            BCK(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) {
-                best = ms;
-                best_rows = r;
-                best_bps = bps;
-            }
+        int rc = lbm_batch_set_config(b, r, 0);
+        if (rc != LBM_OK) return rc;
+        rc = run_batch(b, 1, nullptr, false);  // warm-up (and graph build)
+        if (rc != LBM_OK) return rc;
+        BCK(cudaEventRecord(e0, b->stream));
+        for (int k = 0; k < 4 && rc == LBM_OK; ++k) rc = run_batch(b, 1, nullptr, false);
+        if (rc != LBM_OK) return rc;
+        BCK(cudaEventRecord(e1, b->stream));
+        BCK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        BCK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            best_rows = r;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    return lbm_batch_set_config(b, best_rows, best_bps);
+    return lbm_batch_set_config(b, best_rows, 0);
+}
+
+extern "C" int lbm_batch_get_config(lbm_batch_t b, int *rows, int *blocks_per_sm,
+                                    int *specialised) {
+    if (!b) return bfail(LBM_EINVAL, "lbm_batch_get_config: NULL batch");
+    if (rows) *rows = b->rows;
+    if (blocks_per_sm)
+        *blocks_per_sm = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, b->max_blocks_per_sm)
+                                              : b->max_blocks_per_sm;
+    if (specialised) *specialised = b->kernel != (BatchKernel)k_batch ? 1 : 0;
+    return LBM_OK;
 }

@@ -280,19 +280,23 @@ __device__ __forceinline__ Dither site_dither(uint32_t site, uint32_t step) {
 }
 
 // FP32 -> 16-bit with round up probability equal to the discarded fraction:
-// add the dither below the kept bits of the magnitude, then truncate.  FP16
-// values below the smallest normal (2^-14) round to nearest instead (their
-// spacing is fixed, so a shift of the dither would not match it).
+// add the dither, (d + 1/2)/256 of a unit in the last kept place, below the
+// kept bits of the magnitude, then truncate.  The half step centres the 256
+// dither levels, so the rounding is unbiased on average (without it the
+// levels d/256 round up too often by 1/512 unit, which slows the decay of
+// slow modes).  FP16 values below the smallest normal (2^-14) round to
+// nearest instead (their spacing is fixed, so a shift of the dither would not
+// match it).
 template <int S>
 __device__ __forceinline__ uint32_t sr_round(float x, uint32_t d) {
     const uint32_t b = __float_as_uint(x);
     const uint32_t sgn = b & 0x80000000u;
     const uint32_t mag = b & 0x7fffffffu;
     if constexpr (S == ST_BF16) {
-        return (sgn | (mag + (d << 8))) >> 16;  // 16 discarded bits
+        return (sgn | (mag + ((d << 8) | 0x80u))) >> 16;  // 16 discarded bits
     } else {
         if (mag < 0x38800000u) return (uint32_t)__half_as_ushort(__float2half_rn(x));
-        const float y = __uint_as_float(sgn | (mag + (d << 5)));  // 13 discarded bits
+        const float y = __uint_as_float(sgn | (mag + ((d << 5) | 0x10u)));  // 13 discarded bits
         return (uint32_t)__half_as_ushort(__float2half_rz(y));
     }
 }

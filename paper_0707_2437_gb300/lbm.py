@@ -78,6 +78,8 @@ def load() -> ctypes.CDLL:
             "lbm_batch_sync": ([vp], i),
             "lbm_batch_set_config": ([vp, i, i], i),
             "lbm_batch_tune": ([vp], i),
+            "lbm_batch_get_config": ([vp, ctypes.POINTER(i), ctypes.POINTER(i),
+                                      ctypes.POINTER(i)], i),
             "lbm_batch_set_timeout_us": ([vp, ll], i),
             "lbm_sums_noalloc": ([vp, i, i, sz, i, d, vp, dp], i),
             "lbm_strerror": ([i], ctypes.c_char_p),
@@ -314,6 +316,13 @@ class Batch:
 
     def tune(self):
         _check(self.lib.lbm_batch_tune(self.b), "lbm_batch_tune")
+        return self.get_config()
+
+    def get_config(self):
+        r, b, sp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self.lib.lbm_batch_get_config(self.b, ctypes.byref(r), ctypes.byref(b),
+                                             ctypes.byref(sp)), "lbm_batch_get_config")
+        return {"rows": r.value, "blocks_per_sm": b.value, "specialised": bool(sp.value)}
 
     def set_timeout_us(self, us: int):
         _check(self.lib.lbm_batch_set_timeout_us(self.b, int(us)), "lbm_batch_set_timeout_us")
