@@ -3,8 +3,8 @@
 // barrier between time steps, replayed from a CUDA graph.
 //
 // Work-list: every grid is cut into tiles of (32*vec columns) x (rows rows),
-// one warp per tile per step; tile k is done by warp k mod W of the W resident
-// warps.  Within a time step tiles are independent (each reads its grid's
+// one warp per tile per step; within a step the resident warps take tiles in
+// list order from an atomic counter.  Within a time step tiles are independent (each reads its grid's
 // input buffer and writes the other one); between steps every block waits at
 // a barrier, because a tile's pull reaches two rows and one column into its
 // neighbours and its store overwrites what they read one step earlier.
@@ -83,6 +83,20 @@ __device__ bool grid_barrier(unsigned *bar, int *status, unsigned long long time
     return ok_sh != 0;
 }
 
+// Dynamic tile scheduling: within a time step, warps take the next tile
+// index from a counter (one per step parity; the counter of step k is reset
+// during step k+1, and the barrier at the end of k+1 orders that reset before
+// step k+2 uses it again).  Uneven tiles then balance across warps.
+__device__ __forceinline__ int next_tile(unsigned *ctr) {
+    unsigned v = 0;
+    if ((threadIdx.x & 31) == 0) v = atomicAdd(ctr, 1u);
+    return (int)__shfl_sync(FULL, v, 0);
+}
+
+__device__ __forceinline__ void reset_counter(unsigned *ctr, long long k) {
+    if (k >= 1 && blockIdx.x == 0 && threadIdx.x == 0) ctr[(k - 1) & 1] = 0u;
+}
+
 template <int S, int V, bool PF = false, int RND = 0>
 __device__ __noinline__ void do_tile(const GridDesc &g, int par, const Tile &t, uint32_t step) {
     Walker<S, V, LD_CG, RND> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P, t.x0);
@@ -98,11 +112,10 @@ __global__ void __launch_bounds__(32 * kBatchWarps, 3)
             const long long *__restrict__ limit, const int *__restrict__ parity0,
             const uint32_t *__restrict__ t0, long long nsteps, unsigned *bar, int *status,
             unsigned long long timeout_ns) {
-    const int wpb = blockDim.x >> 5;
-    const int nwarps = gridDim.x * wpb;
-    const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+    unsigned *ctr = bar + 2;  // two tile counters follow the barrier words
     for (long long k = 0; k < nsteps; ++k) {
-        for (int ti = gw; ti < ntiles; ti += nwarps) {
+        reset_counter(ctr, k);
+        for (int ti = next_tile(ctr + (k & 1)); ti < ntiles; ti = next_tile(ctr + (k & 1))) {
             const Tile t = tiles[ti];
             if (k >= limit[t.grid]) continue;
             const GridDesc &g = grids[t.grid];
@@ -157,11 +170,10 @@ __global__ void __launch_bounds__(32 * kBatchWarps, 4)
                 const long long *__restrict__ limit, const int *__restrict__ parity0,
                 const uint32_t *__restrict__ t0, long long nsteps, unsigned *bar, int *status,
                 unsigned long long timeout_ns) {
-    const int wpb = blockDim.x >> 5;
-    const int nwarps = gridDim.x * wpb;
-    const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+    unsigned *ctr = bar + 2;
     for (long long k = 0; k < nsteps; ++k) {
-        for (int ti = gw; ti < ntiles; ti += nwarps) {
+        reset_counter(ctr, k);
+        for (int ti = next_tile(ctr + (k & 1)); ti < ntiles; ti = next_tile(ctr + (k & 1))) {
             const Tile t = tiles[ti];
             if (k >= limit[t.grid]) continue;
             const GridDesc g = grids[t.grid];
@@ -348,7 +360,7 @@ extern "C" int lbm_batch_create(const lbm_t *grids, int n, lbm_batch_t *out) {
     if (e == cudaSuccess) e = cudaMalloc(&b->d_limit, sizeof(long long) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_parity, sizeof(int) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_t0, sizeof(uint32_t) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_bar, sizeof(unsigned) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_bar, sizeof(unsigned) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_limit, sizeof(long long) * n);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_parity, sizeof(int) * n);
@@ -386,7 +398,7 @@ static cudaError_t enqueue(lbm_batch *b, long long n, cudaStream_t st) {
                             st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_t0, b->h_t0, sizeof(uint32_t) * ng, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned) * 2, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned) * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     const GridDesc *grids = b->d_grids;
