@@ -36,7 +36,7 @@ METRIC = "MLUPS (million lattice updates per second), D2Q9 variable-speed-of-sou
 WORKLOAD = "2048x2048 periodic D2Q9, 9 runs c2=0.05..0.45, tau~U[0.55,1.5], acoustic+shear wave"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "step_f32_2048_traffic.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_0707_2437_gb300", "csrc", f)
-                  for f in ("lbm_device.cuh", "lbm_kernels.cu")]
+                  for f in ("lbm_device.cuh", "lbm_kernels.cu", "lbm_batch.cu")]
 
 
 def kernel_source_hash() -> str:
@@ -215,18 +215,23 @@ def run_native(args):
     cfg = grids[0].get_config()
     stages, pipelined = grids[0].get_pipeline()
     sites = sum(r.nx * r.ny for r in runs)
+    batch = lbm.Batch(grids) if args.path == "batch" else None
 
     def one_step():
-        for g in grids:
-            g.step(1)
+        if batch is not None:
+            batch.step(1)
+        else:
+            for g in grids:
+                g.step(1)
 
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
 
     # Timed region: events around every launch on the launching stream.
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps * len(grids))]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps * len(grids))]
+    per_step = 1 if batch is not None else len(grids)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps * per_step)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps * per_step)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
@@ -236,30 +241,66 @@ def run_native(args):
     t_start.record(stream)
     k = 0
     for _ in range(args.steps):
-        for g in grids:
+        if batch is not None:
             starts[k].record(stream)
-            g.step(1)
+            batch.step(1)
             ends[k].record(stream)
             k += 1
+        else:
+            for g in grids:
+                starts[k].record(stream)
+                g.step(1)
+                ends[k].record(stream)
+                k += 1
     t_end.record(stream)
     torch.cuda.synchronize()
     barrier(ws)
     clk = clocks.stop()
+    if batch is not None:
+        batch.sync()
     elapsed_ms = t_start.elapsed_time(t_end)
-    launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    launch_ms = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
     elapsed_ms = max_over_ranks(ws, elapsed_ms)
     value = ws * sites * args.steps / (elapsed_ms * 1e-3) / 1e6
 
-    # Roofline of the step kernel: algorithmic bytes per launch / mean launch time.
+    # Roofline of the dominant kernel: algorithmic bytes per launch / mean
+    # launch time (one launch = one step of all grids on the batch path, one
+    # step of one grid on the single-grid path).
     per_launch_s = statistics.mean(launch_ms) * 1e-3
-    alg_bytes = BYTES_PER_LU[storage] * runs[0].nx * runs[0].ny
+    alg_bytes = BYTES_PER_LU[storage] * (sites if batch is not None else runs[0].nx * runs[0].ny)
     achieved = alg_bytes / per_launch_s / 1e9
     peak, peak_kind = measured_peak()
     traffic = None
     if os.path.exists(PROFILE_TRAFFIC):
         tj = json.load(open(PROFILE_TRAFFIC))
-        if tj.get("source_hash") == kernel_source_hash() and tj.get("storage") == storage:
+        if (tj.get("source_hash") == kernel_source_hash() and tj.get("storage") == storage
+                and tj.get("path") == args.path):
             traffic = tj.get("dram_bytes_per_launch")
+
+    # The plain single-grid step kernel on the same grids (one launch per grid
+    # and step), for its own roofline fraction.
+    single = None
+    if batch is not None and not args.no_single:
+        n1 = max(20, args.steps // 10)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(n1 * len(grids))]
+        for g in grids:
+            g.step(1)
+        torch.cuda.synchronize()
+        k = 0
+        for _ in range(n1):
+            for g in grids:
+                ev[k][0].record(stream)
+                g.step(1)
+                ev[k][1].record(stream)
+                k += 1
+        torch.cuda.synchronize()
+        ms1 = statistics.mean(a.elapsed_time(b_) for a, b_ in ev)
+        b1 = BYTES_PER_LU[storage] * runs[0].nx * runs[0].ny
+        single = {"kernel": f"k_step<{storage},vec={cfg[0]}>", "launches": n1 * len(grids),
+                  "mean_launch_ms": ms1, "achieved": b1 / (ms1 * 1e-3) / 1e9,
+                  "frac": b1 / (ms1 * 1e-3) / 1e9 / measured_peak()[0],
+                  "mlups": runs[0].nx * runs[0].ny / (ms1 * 1e-3) / 1e6}
 
     # End to end through the C ABI with host buffers: one job = lbm_init from
     # pinned host fields, e2e_steps steps, lbm_moments back to pinned host
@@ -274,9 +315,13 @@ def run_native(args):
                 for r in e2e_runs]
 
     def job(steps):
-        for g, hin, hout in zip(grids, host_in, host_out):
+        for g, hin in zip(grids, host_in):
             g.init(*[t.numpy() for t in hin])
-            g.step(steps)
+        if batch is not None:
+            batch.step(steps)
+        else:
+            for g in grids:
+                g.step(steps)
         for g, hout in zip(grids, host_out):
             g.moments(out=[t.numpy() for t in hout])
 
@@ -310,26 +355,33 @@ def run_native(args):
                    "rows": cfg[1], "warps": cfg[2],
                    "pipeline_stages": stages if pipelined else 0},
                    "l2": "inputs larger than L2 (2 x 151 MB per grid, 129 MB L2), no flush",
+                   "path": ("one persistent launch per step over the 9 grids (batch API)"
+                            if batch is not None else "one step-kernel launch per grid and step"),
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
-                     "kernel": (f"k_step_tma<{storage},stages={stages}>" if pipelined
+                     "kernel": ("k_batch_one (persistent, 9 grids)" if batch is not None
+                                else f"k_step_tma<{storage},stages={stages}>" if pipelined
                                 else f"k_step<{storage},vec={cfg[0]}>"),
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "mean_launch_ms": per_launch_s * 1e3},
         "e2e": {"value": e2e_value, "unit": "MLUPS",
                 "h2d_bytes_per_step": len(runs) * 3 * n * 8,
                 "d2h_bytes_per_step": len(runs) * 3 * n * 8,
-                "step": f"one job: lbm_init from pinned host fields, {args.e2e_steps} steps, "
+                "step": f"one job: lbm_init from pinned host fields, {args.e2e_steps} steps "
+                        f"({'one batch launch' if batch is not None else 'lbm_step per grid'}), "
                         f"lbm_moments to host, for all {len(runs)} grids",
                 "jobs": args.e2e_jobs},
-        "gpu_launches": args.steps * len(grids),
+        "gpu_launches": args.steps * per_step,
         "clocks": clk,
+        "single_grid_kernel": single,
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if batch is not None:
+        batch.close()
     for g in grids:
         g.close()
     if rank == 0:
@@ -461,6 +513,11 @@ def main():
                     metavar=("VEC", "ROWS", "WARPS"))
     ap.add_argument("--stages", type=int, default=None,
                     help="row pipeline stages (0: register walk)")
+    ap.add_argument("--path", default="batch", choices=["batch", "single"],
+                    help="batch: one persistent launch per step over all grids; "
+                         "single: one step-kernel launch per grid and step")
+    ap.add_argument("--no-single", action="store_true",
+                    help="skip the extra single-grid kernel measurement")
     ap.add_argument("--grids", type=int, default=9, choices=range(1, 10),
                     help="use the first N of the nine 2048^2 runs (profiling)")
     ap.add_argument("--no-e2e", action="store_true")

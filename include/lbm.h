@@ -106,10 +106,19 @@ int lbm_init(lbm_t h, const double *rho, const double *ux, const double *uy,
              int on_device);
 
 /* Queues n >= 0 time steps of Eq. 5 (stream, moments, central grad(rho),
- * collide with force) on the handle's stream.  Steps are replayed from a CUDA
- * graph when n is large enough for launch overhead to matter.  Asynchronous:
- * errors of the kernels themselves surface at the next synchronising call. */
+ * collide with force) on the handle's stream.  From 64 steps on (while
+ * persistent mode is on, the default) the steps run as one persistent launch:
+ * the batched kernel (see lbm_batch_create) with this grid alone, warps taking
+ * tiles dynamically, a bounded grid barrier between steps.  Shorter calls
+ * launch the step kernel with the handle's tile configuration, replayed from
+ * CUDA graphs from 8 steps on.  All forms give bitwise the same result.
+ * Asynchronous: errors of the kernels surface at the next synchronising call
+ * (LBM_ETIMEOUT if a bounded wait ran out). */
 int lbm_step(lbm_t h, long long n);
+
+/* Persistent mode of lbm_step (on by default); off: every call uses the step
+ * kernel with the tile configuration. */
+int lbm_set_persistent(lbm_t h, int on);
 
 /* Writes rho, ux, uy (Eq. 3) of the current state, computed in FP64 from the
  * stored distributions.

@@ -101,8 +101,13 @@ static int *status_ptr(lbm_grid *h) { return reinterpret_cast<int *>(h->scratch 
 // Device step counter that seeds stochastic rounding inside graph replays.
 static uint32_t *step_ptr(lbm_grid *h) { return reinterpret_cast<uint32_t *>(h->scratch + 9); }
 
-// Reads and clears the status word (the stream must be idle).
+// Reads and clears the status word (the stream must be idle), and the status
+// of the grid's own persistent batch, if any.
 static int take_status(lbm_grid *h) {
+    if (h->self_batch) {
+        int rb = lbm_batch_sync(h->self_batch);
+        if (rb != LBM_OK) return rb;
+    }
     int st = 0;
     cudaError_t e = cudaMemcpy(&st, status_ptr(h), sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "status read");
@@ -111,6 +116,13 @@ static int take_status(lbm_grid *h) {
         return fail(st, "a bounded wait in the step kernel ran out");
     }
     return LBM_OK;
+}
+
+static void drop_self_batch(lbm_grid *h) {
+    if (h->self_batch) {
+        lbm_batch_destroy(h->self_batch);
+        h->self_batch = nullptr;
+    }
 }
 
 static void drop_graphs(lbm_grid *h) {
@@ -187,6 +199,7 @@ extern "C" int lbm_create(int nx, int ny, double tau, double c2, int storage, vo
 extern "C" int lbm_destroy(lbm_t h) {
     if (!h) return LBM_OK;
     if (h->stream || h->buf[0]) cudaStreamSynchronize(h->stream);
+    drop_self_batch(h);
     drop_graphs(h);
     for (int k = 0; k < 2; ++k) {
         if (h->buf[k]) cudaFree(h->buf[k]);
@@ -242,6 +255,7 @@ static cudaError_t launch_one(lbm_grid *h, int from) {
 }
 
 static const int kGraphPairs = 16;   // a graph holds 32 steps
+static const long long kPersistentMin = 64;  // persistent launch from this many steps
 static const long long kGraphMin = 8; // use graphs from this many steps on
 
 static int build_graphs(lbm_grid *h) {
@@ -294,6 +308,16 @@ extern "C" int lbm_step(lbm_t h, long long n) {
         h->kernel_launches = n;
         return LBM_OK;
     }
+    if (h->persistent && n >= kPersistentMin) {
+        // One persistent launch of all n steps (dynamic tile scheduling,
+        // barrier between steps), bitwise the same as n single launches.
+        if (!h->self_batch) {
+            lbm_t self = h;
+            int rc = lbm_batch_create(&self, 1, &h->self_batch);
+            if (rc != LBM_OK) return rc;
+        }
+        return lbm_batch_step(h->self_batch, n, nullptr);  // advances t and cur
+    }
     if (n >= kGraphMin) {
         if (!h->graph_pairs) {
             int rc = build_graphs(h);
@@ -313,6 +337,14 @@ extern "C" int lbm_step(lbm_t h, long long n) {
         h->cur ^= 1;
         h->t += 1;
     }
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_persistent(lbm_t h, int on) {
+    if (!h) return fail(LBM_EINVAL, "lbm_set_persistent: NULL handle");
+    CK(cudaStreamSynchronize(h->stream));
+    h->persistent = on != 0;
+    if (!h->persistent) drop_self_batch(h);
     return LBM_OK;
 }
 
@@ -448,6 +480,7 @@ extern "C" int lbm_set_config(lbm_t h, int vec, int rows, int warps) {
     if (h->cfg.vec != vec || h->cfg.rows != rows || h->cfg.warps != warps) {
         CK(cudaStreamSynchronize(h->stream));
         drop_graphs(h);
+        drop_self_batch(h);
     }
     h->cfg.vec = vec;
     h->cfg.rows = rows;
@@ -479,6 +512,7 @@ extern "C" int lbm_set_rounding(lbm_t h, int mode) {
         return fail(LBM_EINVAL, "lbm_set_rounding: stochastic rounding needs 16-bit storage");
     CK(cudaStreamSynchronize(h->stream));
     drop_graphs(h);
+    drop_self_batch(h);
     h->rounding = mode;
     if (mode == LBM_ROUND_STOCHASTIC) {
         // The stochastic-rounding walks are the register walks with vec <= 4.

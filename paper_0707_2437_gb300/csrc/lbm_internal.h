@@ -107,6 +107,10 @@ struct lbm_grid {
     // CUDA graphs of 2*graph_pairs steps starting from buffer 0 or buffer 1
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_pairs = 0;
+    // Long step calls run as one persistent launch through a batch holding
+    // only this grid (created on first use, dropped when the tiling changes).
+    bool persistent = true;
+    struct lbm_batch *self_batch = nullptr;
     // timing
     bool timing = false;
     double kernel_ms = 0;

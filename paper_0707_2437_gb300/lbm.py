@@ -71,6 +71,7 @@ def load() -> ctypes.CDLL:
             "lbm_get_rounding": ([vp, ctypes.POINTER(i)], i),
             "lbm_get_pipeline": ([vp, ctypes.POINTER(i), ctypes.POINTER(i)], i),
             "lbm_set_timing": ([vp, i], i),
+            "lbm_set_persistent": ([vp, i], i),
             "lbm_kernel_ms": ([vp, dp, ctypes.POINTER(ll)], i),
             "lbm_batch_create": ([ctypes.POINTER(vp), i, ctypes.POINTER(vp)], i),
             "lbm_batch_destroy": ([vp], i),
@@ -268,6 +269,9 @@ class Grid:
     def tune(self, cache_path: str | None = None):
         _check(self.lib.lbm_tune(self.h, cache_path.encode() if cache_path else None), "lbm_tune")
         return self.get_config() + (self.get_pipeline()[0],)
+
+    def set_persistent(self, on: bool):
+        _check(self.lib.lbm_set_persistent(self.h, 1 if on else 0), "lbm_set_persistent")
 
     def set_timing(self, on: bool):
         _check(self.lib.lbm_set_timing(self.h, 1 if on else 0), "lbm_set_timing")

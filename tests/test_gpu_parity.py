@@ -192,6 +192,28 @@ def test_rounding_mode_validation(lbm):
             g.set_pipeline(3)
 
 
+@pytest.mark.parametrize("storage,rounding", [("f32", "nearest"), ("f16d", "nearest"),
+                                              ("bf16d", "stochastic")])
+@pytest.mark.parametrize("nx,ny", [(256, 100), (37, 23), (520, 9)])
+def test_persistent_long_steps_equal_step_kernel(lbm, storage, rounding, nx, ny):
+    """lbm_step runs long calls as one persistent launch; the state equals the
+    step kernel's (persistent mode off) bit for bit."""
+    f = _fields(nx, ny, seed=nx + 7)
+    out = []
+    for persistent in (True, False):
+        with lbm.Grid(nx, ny, 0.75, 0.18, storage) as g:
+            if rounding != "nearest":
+                g.set_rounding(rounding)
+            g.set_persistent(persistent)
+            g.init(*f)
+            g.step(150)
+            g.step(3)
+            g.step(70)
+            assert g.t == 223
+            out.append(g.get_state()[0])
+    assert np.array_equal(out[0], out[1])
+
+
 def test_graph_replay_equals_single_launches(lbm):
     nx, ny = 96, 64
     f = _fields(nx, ny, seed=7)
