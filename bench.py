@@ -134,6 +134,25 @@ class ClockSampler:
                 "samples": len(sms), "reasons": sorted(reasons)}
 
 
+def serve_comparison(args, stream=None):
+    """A short serving trace (Poisson arrivals, mixed FP32 / FP16-delta
+    requests) through the continuous-batching server and through the plain
+    FIFO single-grid FP32 baseline: p50/p99 time-to-result and MLUPS."""
+    from paper_0707_2437_gb300 import serve
+    trace = serve.scaled_trace(args.serve_count, args.serve_rate,
+                               steps_hi=args.serve_steps_hi)
+    warm = serve.scaled_trace(8, 1000.0, seed=99, hi=256, steps_hi=2000)
+    serve.Server(quantum=args.serve_quantum).run(warm, realtime=False)
+    srv = serve.Server(quantum=args.serve_quantum).run(trace, realtime=True).summary()
+    fifo = serve.serve_fifo(trace, realtime=True).summary()
+    return {"trace": f"{args.serve_count} requests, Poisson {args.serve_rate}/s, sites "
+                     f"log-uniform 128^2..2048^2, steps U{{1000..{args.serve_steps_hi}}}, "
+                     "half f32 / half f16d",
+            "continuous_batching": srv, "fifo_f32": fifo,
+            "p99_speedup": fifo["p99_s"] / srv["p99_s"] if srv["p99_s"] else None,
+            "mlups_ratio": srv["mlups"] / fifo["mlups"] if fifo["mlups"] else None}
+
+
 def cpu_baseline(seconds: float = 12.0):
     """The FP64 oracle as it stands, on the host cores, on one 2048^2 grid of
     the sweep: runs whole steps until `seconds` have passed."""
@@ -380,6 +399,8 @@ def run_native(args):
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if not args.no_serve:
+        line["serve"] = serve_comparison(args, stream)
     if batch is not None:
         batch.close()
     for g in grids:
@@ -466,17 +487,12 @@ def run_serve_workload(args):
     aggregate MLUPS of both."""
     import torch
 
-    from paper_0707_2437_gb300 import serve
-
     ws, rank, local = dist_setup(args.gpus)
     torch.cuda.set_device(local)
-    trace = serve.scaled_trace(args.serve_count, args.serve_rate, steps_hi=args.serve_steps_hi)
-    warm = serve.scaled_trace(8, 1000.0, seed=99, hi=256, steps_hi=2000)
-    serve.Server(quantum=args.serve_quantum).run(warm, realtime=False)
     clocks = ClockSampler(local)
     clocks.start()
-    srv = serve.Server(quantum=args.serve_quantum).run(trace, realtime=True).summary()
-    fifo = serve.serve_fifo(trace, realtime=True).summary()
+    cmp_ = serve_comparison(args)
+    srv, fifo = cmp_["continuous_batching"], cmp_["fifo_f32"]
     clk = clocks.stop()
     line = {
         "metric": "served p50/p99 time-to-result and aggregate MLUPS vs plain FP32 FIFO",
@@ -505,9 +521,11 @@ def main():
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-rows", type=int, default=0)
     ap.add_argument("--tune", action="store_true")
-    ap.add_argument("--serve-count", type=int, default=200)
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the serving comparison in the default workload")
+    ap.add_argument("--serve-count", type=int, default=60)
     ap.add_argument("--serve-rate", type=float, default=200.0)
-    ap.add_argument("--serve-steps-hi", type=int, default=20000)
+    ap.add_argument("--serve-steps-hi", type=int, default=5000)
     ap.add_argument("--serve-quantum", type=int, default=256)
     ap.add_argument("--config", type=int, nargs=3, default=None,
                     metavar=("VEC", "ROWS", "WARPS"))
