@@ -142,6 +142,16 @@ int lbm_sums(lbm_t h, double *out3);
  * v = A sin(2 pi kx x / nx) gives out2 = {0, A}.  Waits for the stream. */
 int lbm_mode(lbm_t h, int field, int kx, int ky, double *out2);
 
+/* Spatially varying sound speed (the paper's Section 5 outlook: alpha set per
+ * site, for example for a temperature gradient or an acoustic lens).  c2 is a
+ * [ny][nx] array of c_e^2 > 0 (host if on_device == 0, else device; host
+ * values are checked); the force at site x uses alpha(x) = 1/3 - c2(x) in
+ * Eq. 5.  NULL returns to the grid's uniform c2.  The field costs one more
+ * 4-byte read per site and step.  While a field is set: lbm_step uses the
+ * step kernel (vec <= 4, no bulk-copy pipeline, nearest rounding), and the
+ * grid cannot join a batch (lbm_batch_create returns LBM_EINVAL). */
+int lbm_set_c2_field(lbm_t h, const double *c2, int on_device);
+
 /* Steps taken since lbm_init / lbm_set_state. */
 long long lbm_time(lbm_t h);
 

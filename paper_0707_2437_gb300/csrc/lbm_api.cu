@@ -206,6 +206,7 @@ extern "C" int lbm_destroy(lbm_t h) {
         if (h->ev[k]) cudaEventDestroy(h->ev[k]);
     }
     if (h->scratch) cudaFree(h->scratch);
+    if (h->a15f) cudaFree(h->a15f);
     if (h->host_out) cudaFreeHost(h->host_out);
     delete h;
     return LBM_OK;
@@ -251,7 +252,8 @@ extern "C" int lbm_init(lbm_t h, const double *rho, const double *ux, const doub
 // One step launch from buf[cur] to buf[cur ^ 1] (no bookkeeping).
 static cudaError_t launch_one(lbm_grid *h, int from) {
     return launch_step(h->storage, h->cfg, h->buf[from], h->buf[from ^ 1], h->nx, h->ny, h->P,
-                       h->coef, status_ptr(h), h->rounding, nullptr, (uint32_t)h->t, h->stream);
+                       h->coef, status_ptr(h), h->rounding, nullptr, (uint32_t)h->t, h->a15f,
+                       h->stream);
 }
 
 static const int kGraphPairs = 16;   // a graph holds 32 steps
@@ -269,7 +271,8 @@ static int build_graphs(lbm_grid *h) {
             for (int k = 0; k < 2 * kGraphPairs && e == cudaSuccess; ++k)
                 e = launch_step(h->storage, h->cfg, h->buf[(start + k) & 1],
                                 h->buf[(start + k + 1) & 1], h->nx, h->ny, h->P, h->coef,
-                                status_ptr(h), h->rounding, step_ptr(h), (uint32_t)k, cs);
+                                status_ptr(h), h->rounding, step_ptr(h), (uint32_t)k, h->a15f,
+                                cs);
             cudaError_t e2 = cudaStreamEndCapture(cs, &g);
             if (e == cudaSuccess) e = e2;
         }
@@ -308,7 +311,7 @@ extern "C" int lbm_step(lbm_t h, long long n) {
         h->kernel_launches = n;
         return LBM_OK;
     }
-    if (h->persistent && n >= kPersistentMin) {
+    if (h->persistent && !h->a15f && n >= kPersistentMin) {
         // One persistent launch of all n steps (dynamic tile scheduling,
         // barrier between steps), bitwise the same as n single launches.
         if (!h->self_batch) {
@@ -473,8 +476,8 @@ extern "C" int lbm_set_config(lbm_t h, int vec, int rows, int warps) {
     if (!valid_vec(h->storage, h->nx, vec))
         return fail(LBM_EINVAL, "lbm_set_config: vec must be 1, 2, 4 (or 8 for 16-bit) and divide nx");
     if (rows < 1 || rows > 4096) return fail(LBM_EINVAL, "lbm_set_config: rows in [1, 4096]");
-    if (h->rounding && vec == 8)
-        return fail(LBM_EINVAL, "lbm_set_config: stochastic rounding uses vec 1, 2 or 4");
+    if ((h->rounding || h->a15f) && vec == 8)
+        return fail(LBM_EINVAL, "lbm_set_config: stochastic rounding and c2 fields use vec <= 4");
     if (warps != 1 && warps != 2 && warps != 4 && warps != 8)
         return fail(LBM_EINVAL, "lbm_set_config: warps in {1, 2, 4, 8}");
     if (h->cfg.vec != vec || h->cfg.rows != rows || h->cfg.warps != warps) {
@@ -493,8 +496,8 @@ extern "C" int lbm_set_pipeline(lbm_t h, int stages) {
     if (!h) return fail(LBM_EINVAL, "lbm_set_pipeline: NULL handle");
     if (stages < 0 || stages > 4)
         return fail(LBM_EINVAL, "lbm_set_pipeline: stages must be 0..4");
-    if (h->rounding && stages >= 2)
-        return fail(LBM_EINVAL, "lbm_set_pipeline: stochastic rounding uses the register walk");
+    if ((h->rounding || h->a15f) && stages >= 2)
+        return fail(LBM_EINVAL, "lbm_set_pipeline: stochastic rounding and c2 fields use the register walk");
     if (h->cfg.stages != stages) {
         CK(cudaStreamSynchronize(h->stream));
         drop_graphs(h);
@@ -504,12 +507,47 @@ extern "C" int lbm_set_pipeline(lbm_t h, int stages) {
     return LBM_OK;
 }
 
+extern "C" int lbm_set_c2_field(lbm_t h, const double *c2, int on_device) {
+    if (!h) return fail(LBM_EINVAL, "lbm_set_c2_field: NULL handle");
+    CK(cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
+    drop_self_batch(h);
+    if (!c2) {
+        if (h->a15f) cudaFree(h->a15f);
+        h->a15f = nullptr;
+        return LBM_OK;
+    }
+    if (h->rounding) return fail(LBM_EINVAL, "lbm_set_c2_field: needs nearest rounding");
+    size_t n = (size_t)h->nx * h->ny;
+    if (!on_device) {
+        for (size_t s = 0; s < n; ++s)
+            if (!(c2[s] > 0.0) || !isfinite(c2[s]))
+                return fail(LBM_EINVAL, "lbm_set_c2_field: need c2 > 0 at every site");
+    }
+    if (h->cfg.vec == 8) h->cfg.vec = 4;   // the field walks use vec <= 4
+    if (h->cfg.stages >= 2) h->cfg.stages = 0;
+    if (!h->a15f) CK(cudaMalloc(&h->a15f, n * sizeof(float)));
+    std::vector<double *> owned;
+    double *d = nullptr;
+    int rc = stage_field(h, c2, on_device, &d, owned);
+    if (rc == LBM_OK) {
+        cudaError_t e = launch_a15_from_c2(d, h->a15f, (long long)n, h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "lbm_set_c2_field kernel");
+    }
+    for (double *p : owned) cudaFreeAsync(p, h->stream);
+    if (rc != LBM_OK) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
 extern "C" int lbm_set_rounding(lbm_t h, int mode) {
     if (!h) return fail(LBM_EINVAL, "lbm_set_rounding: NULL handle");
     if (mode != LBM_ROUND_NEAREST && mode != LBM_ROUND_STOCHASTIC)
         return fail(LBM_EINVAL, "lbm_set_rounding: unknown mode");
     if (mode == LBM_ROUND_STOCHASTIC && h->storage == ST_F32)
         return fail(LBM_EINVAL, "lbm_set_rounding: stochastic rounding needs 16-bit storage");
+    if (mode == LBM_ROUND_STOCHASTIC && h->a15f)
+        return fail(LBM_EINVAL, "lbm_set_rounding: not with a c2 field");
     CK(cudaStreamSynchronize(h->stream));
     drop_graphs(h);
     drop_self_batch(h);
@@ -636,7 +674,7 @@ extern "C" int lbm_tune(lbm_t h, const char *cache_path) {
     const int warpss[] = {2, 4, 8};
     for (int v : vecs) {
         if (!valid_vec(h->storage, h->nx, v)) continue;
-        if (h->rounding && v == 8) continue;
+        if ((h->rounding || h->a15f) && v == 8) continue;
         for (int r : rowss) {
             if (r > 2 * h->ny && r != 4) continue;
             for (int w : warpss) {
@@ -645,7 +683,7 @@ extern "C" int lbm_tune(lbm_t h, const char *cache_path) {
                     v == prefetch_vec(h->storage) || (h->storage != ST_F32 && v == 8);
                 for (int nst = 0; nst <= 4; ++nst) {
                     if (nst == 1 && !pf_ok) continue;
-                    if (nst >= 2 && (!tma_ok || h->rounding)) continue;
+                    if (nst >= 2 && (!tma_ok || h->rounding || h->a15f)) continue;
                     TileCfg c;
                     c.vec = v;
                     c.rows = r;

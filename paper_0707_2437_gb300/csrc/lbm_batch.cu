@@ -340,8 +340,11 @@ extern "C" int lbm_batch_destroy(lbm_batch_t b) {
 extern "C" int lbm_batch_create(const lbm_t *grids, int n, lbm_batch_t *out) {
     if (!out || !grids || n < 1) return bfail(LBM_EINVAL, "lbm_batch_create: bad argument");
     *out = nullptr;
-    for (int k = 0; k < n; ++k)
+    for (int k = 0; k < n; ++k) {
         if (!grids[k]) return bfail(LBM_EINVAL, "lbm_batch_create: NULL grid");
+        if (grids[k]->a15f)
+            return bfail(LBM_EINVAL, "lbm_batch_create: grids with a c2 field are not batched");
+    }
     lbm_batch *b = new (std::nothrow) lbm_batch();
     if (!b) return bfail(LBM_ENOMEM, "lbm_batch_create: host allocation failed");
     b->grids.assign(grids, grids + n);

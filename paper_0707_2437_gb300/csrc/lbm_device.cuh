@@ -381,7 +381,8 @@ struct SiteQ {
 // dr: drho at the site; dxm/dxp, dym/dyp: drho at x -/+ 1 and y -/+ 1.
 __device__ __forceinline__ SiteQ site_quantities(float h1, float h2, float h3, float h4, float h5,
                                                  float h6, float h7, float h8, float dr, float dxm,
-                                                 float dxp, float dym, float dyp, const Coef &c) {
+                                                 float dxp, float dym, float dyp, const Coef &c,
+                                                 float a15) {
     SiteQ q;
     float a = __fsub_rn(h5, h7);  // e_5 = (1, 1), e_7 = -e_5
     float b = __fsub_rn(h6, h8);  // e_6 = (-1, 1), e_8 = -e_6
@@ -393,8 +394,8 @@ __device__ __forceinline__ SiteQ site_quantities(float h1, float h2, float h3, f
     float ju = __fmaf_rn(q.jx, q.ux, __fmul_rn(q.jy, q.uy));
     q.wB = __fmul_rn(c.om, __fmaf_rn(-1.5f, ju, dr));
     // Central differences of Section 4: grad = (d(+1) - d(-1))/2; the 1/2 is in a15.
-    q.Ax = __fmaf_rn(c.w3, q.jx, __fmul_rn(c.a15, __fsub_rn(dxp, dxm)));
-    q.Ay = __fmaf_rn(c.w3, q.jy, __fmul_rn(c.a15, __fsub_rn(dyp, dym)));
+    q.Ax = __fmaf_rn(c.w3, q.jx, __fmul_rn(a15, __fsub_rn(dxp, dxm)));
+    q.Ay = __fmaf_rn(c.w3, q.jy, __fmul_rn(a15, __fsub_rn(dyp, dym)));
     return q;
 }
 
@@ -423,12 +424,14 @@ __device__ __forceinline__ void pair_out(float hi, float hopp, float ej, float e
 //                  (the left neighbour value lane 0 needs for its pull)
 //   lanes 16..24 : pulled f_i at the column after the strip, i = lane - 16
 //   lanes 25..27 : f_i at that column for the directions with e_x = -1
-template <int S, int V, int LD = LD_NC, int RND = 0>
+template <int S, int V, int LD = LD_NC, int RND = 0, int VA = 0>
 struct Walker {
     static constexpr int NW = Pack<S, V>::NW;
     using T = typename StoreT<S>::T;
     static_assert(RND == 0 || S != ST_F32, "stochastic rounding applies to 16-bit storage");
     uint32_t rstep = 0;  // step number that seeds stochastic rounding
+    // Spatially varying sound speed (VA = 1): 1.5 alpha per site, [ny][nx].
+    const float *__restrict__ a15f = nullptr;
 
     const T *__restrict__ fin;
     T *__restrict__ fout;
@@ -630,6 +633,23 @@ struct Walker {
         float rgt = __shfl_down_sync(FULL, d[0], 1);
         if (lane == 0) lft = dl;
         if (lane == nact - 1) rgt = dr;
+        // 1.5 alpha of the lane's sites: the grid's constant, or the field.
+        float a15v[V];
+        if constexpr (VA) {
+            const size_t aidx = (size_t)r * nx + (act ? xs : x0);
+            uint32_t aw[V];
+            if (VSS_IN_BOUNDS(aidx, V, (size_t)nx * ny)) {
+                load_words<ST_F32, V, LD>(a15f + aidx, aw);
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) aw[v] = 0u;
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) a15v[v] = __uint_as_float(aw[v]);
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) a15v[v] = c.a15;
+        }
         constexpr int SP = SitesPerWord<S, V>::value;
 #pragma unroll
         for (int v0 = 0; v0 < V; v0 += SP) {
@@ -642,7 +662,8 @@ struct Walker {
                 const float dxp = (v == V - 1) ? rgt : d[v + 1];
                 float *hs = h[s];
                 const SiteQ q = site_quantities(hs[1], hs[2], hs[3], hs[4], hs[5], hs[6], hs[7],
-                                                hs[8], d[v], dxm, dxp, dym[v], dyp[v], c);
+                                                hs[8], d[v], dxm, dxp, dym[v], dyp[v], c,
+                                                a15v[v]);
                 float o[9];
                 o[0] = __fmaf_rn(c.om1, hs[0], q.wB);                           // rest
                 pair_out(hs[1], hs[3], q.jx, q.ux, q.Ax, q.wB, c, o[1], o[3]);  // e = (1, 0)

@@ -64,9 +64,11 @@ Coef make_coef(double tau, double c2, double rho0);
 // `status` (device int) receives STATUS_TIMEOUT if a pipeline wait runs out.
 // rnd = 1: stochastic rounding of 16-bit stores, seeded by the step number
 // (*tdev if tdev is not NULL, plus toff).
+// a15f: NULL for a uniform alpha, else 1.5 alpha per site ([ny][nx] floats).
 Err launch_step(int storage, const TileCfg &cfg, const void *fin, void *fout, int nx, int ny,
                 size_t P, const Coef &c, int *status, int rnd, const uint32_t *tdev, uint32_t toff,
-                cudaStream_t st);
+                const float *a15f, cudaStream_t st);
+Err launch_a15_from_c2(const double *c2, float *a15, long long n, cudaStream_t st);
 Err launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t st);
 // Sets the kernel attributes a configuration needs (dynamic shared memory);
 // call before the first launch or capture of that configuration.
@@ -102,6 +104,7 @@ struct lbm_grid {
     vss::Coef coef{};
     vss::TileCfg cfg{};
     int rounding = 0;             // 1: stochastic rounding of 16-bit stores
+    float *a15f = nullptr;        // spatially varying alpha: 1.5 alpha per site
     double *scratch = nullptr;    // reduction partials + results
     double *host_out = nullptr;   // pinned, 8 doubles
     // CUDA graphs of 2*graph_pairs steps starting from buffer 0 or buffer 1

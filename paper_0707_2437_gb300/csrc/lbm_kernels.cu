@@ -28,11 +28,11 @@ bool valid_vec(int storage, int nx, int vec) {
 // ---------------------------------------------------------------------------
 // Fused step: one warp per (strip, row segment) tile.
 
-template <int S, int V, bool PF, int RND = 0>
+template <int S, int V, bool PF, int RND = 0, int VA = 0>
 __global__ void __launch_bounds__(256, 2)
     k_step(const void *__restrict__ fin, void *__restrict__ fout, int nx, int ny, size_t P,
            int nstrips, long long ntiles, int rows, Coef c, const uint32_t *tdev,
-           uint32_t toff) {
+           uint32_t toff, const float *__restrict__ a15f) {
     long long tile = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (tile >= ntiles) return;  // whole warps leave together
     int strip = (int)(tile % nstrips);
@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(256, 2)
     int x0 = strip * 32 * V;
     int y0 = seg * rows;
     int y1 = min(ny, y0 + rows);
-    Walker<S, V, LD_NC, RND> w(fin, fout, nx, ny, P, x0);
+    Walker<S, V, LD_NC, RND, VA> w(fin, fout, nx, ny, P, x0);
+    if constexpr (VA) w.a15f = a15f;
     // Stochastic rounding is seeded by the step being computed: a device
     // counter (set before each graph replay) plus this launch's offset.
     if constexpr (RND) w.rstep = (tdev ? *tdev : 0u) + toff;
@@ -97,24 +98,47 @@ __global__ void __launch_bounds__(256, 2)
 
 template <int S, int V, int RND>
 static Err launch_step_t(const TileCfg &cfg, const void *fin, void *fout, int nx, int ny, size_t P,
-                         const Coef &c, const uint32_t *tdev, uint32_t toff, cudaStream_t st) {
+                         const Coef &c, const uint32_t *tdev, uint32_t toff, const float *a15f,
+                         cudaStream_t st) {
     StepGeom g = step_geom(nx, ny, cfg);
     long long blocks = (g.ntiles + cfg.warps - 1) / cfg.warps;
+    const unsigned nb = (unsigned)blocks, nt = 32u * cfg.warps;
+    if (a15f) {
+        // Spatially varying alpha: the register walks (prefetching at 64-bit
+        // vectors for 16-bit storage), nearest rounding.
+        if constexpr (RND == 0 && V <= 4) {
+            if (uses_prefetch(S, cfg)) {
+                if constexpr (Pack<S, V>::BYTES == 8)
+                    k_step<S, V, true, 0, 1><<<nb, nt, 0, st>>>(fin, fout, nx, ny, P, g.nstrips,
+                                                              g.ntiles, cfg.rows, c, tdev, toff,
+                                                              a15f);
+                else
+                    return cudaErrorInvalidValue;
+            } else {
+                k_step<S, V, false, 0, 1><<<nb, nt, 0, st>>>(fin, fout, nx, ny, P, g.nstrips,
+                                                           g.ntiles, cfg.rows, c, tdev, toff,
+                                                           a15f);
+            }
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
     if (uses_prefetch(S, cfg) && V == 8) {
         if constexpr (S != ST_F32 && V == 8 && RND == 0)
-            k_step_wide<S><<<(unsigned)blocks, 32 * cfg.warps, 0, st>>>(
-                fin, fout, nx, ny, P, g.nstrips, g.ntiles, cfg.rows, c);
+            k_step_wide<S><<<nb, nt, 0, st>>>(fin, fout, nx, ny, P, g.nstrips, g.ntiles, cfg.rows,
+                                              c);
         else
             return cudaErrorInvalidValue;
     } else if (uses_prefetch(S, cfg)) {
         if constexpr (Pack<S, V>::BYTES == 8)
-            k_step<S, V, true, RND><<<(unsigned)blocks, 32 * cfg.warps, 0, st>>>(
-                fin, fout, nx, ny, P, g.nstrips, g.ntiles, cfg.rows, c, tdev, toff);
+            k_step<S, V, true, RND><<<nb, nt, 0, st>>>(fin, fout, nx, ny, P, g.nstrips, g.ntiles,
+                                                      cfg.rows, c, tdev, toff, nullptr);
         else
             return cudaErrorInvalidValue;
     } else {
-        k_step<S, V, false, RND><<<(unsigned)blocks, 32 * cfg.warps, 0, st>>>(
-            fin, fout, nx, ny, P, g.nstrips, g.ntiles, cfg.rows, c, tdev, toff);
+        k_step<S, V, false, RND><<<nb, nt, 0, st>>>(fin, fout, nx, ny, P, g.nstrips, g.ntiles,
+                                                   cfg.rows, c, tdev, toff, nullptr);
     }
     return cudaGetLastError();
 }
@@ -169,7 +193,8 @@ Err prepare_step(int storage, const TileCfg &cfg) {
 template <int S>
 static Err launch_step_s(const TileCfg &cfg, const void *fin, void *fout, int nx, int ny, size_t P,
                          const Coef &c, int *status, int rnd, const uint32_t *tdev,
-                         uint32_t toff, cudaStream_t st) {
+                         uint32_t toff, const float *a15f, cudaStream_t st) {
+    if (a15f && (rnd || cfg.vec == 8)) return cudaErrorInvalidValue;
     if (rnd) {
         // Stochastic rounding: register walks with vec 1, 2 or 4.
         if constexpr (S == ST_F32) {
@@ -177,17 +202,17 @@ static Err launch_step_s(const TileCfg &cfg, const void *fin, void *fout, int nx
         } else {
             switch (cfg.vec) {
                 case 1:
-                    return launch_step_t<S, 1, 1>(cfg, fin, fout, nx, ny, P, c, tdev, toff, st);
+                    return launch_step_t<S, 1, 1>(cfg, fin, fout, nx, ny, P, c, tdev, toff, nullptr, st);
                 case 2:
-                    return launch_step_t<S, 2, 1>(cfg, fin, fout, nx, ny, P, c, tdev, toff, st);
+                    return launch_step_t<S, 2, 1>(cfg, fin, fout, nx, ny, P, c, tdev, toff, nullptr, st);
                 case 4:
-                    return launch_step_t<S, 4, 1>(cfg, fin, fout, nx, ny, P, c, tdev, toff, st);
+                    return launch_step_t<S, 4, 1>(cfg, fin, fout, nx, ny, P, c, tdev, toff, nullptr, st);
                 default:
                     return cudaErrorInvalidValue;
             }
         }
     }
-    if (uses_tma(S, cfg)) {
+    if (uses_tma(S, cfg) && !a15f) {
         switch (cfg.stages) {
             case 2:
                 return launch_tma_t<S, 2>(cfg, fin, fout, nx, ny, P, c, status, st);
@@ -201,14 +226,14 @@ static Err launch_step_s(const TileCfg &cfg, const void *fin, void *fout, int nx
     }
     switch (cfg.vec) {
         case 1:
-            return launch_step_t<S, 1, 0>(cfg, fin, fout, nx, ny, P, c, tdev, toff, st);
+            return launch_step_t<S, 1, 0>(cfg, fin, fout, nx, ny, P, c, tdev, toff, a15f, st);
         case 2:
-            return launch_step_t<S, 2, 0>(cfg, fin, fout, nx, ny, P, c, tdev, toff, st);
+            return launch_step_t<S, 2, 0>(cfg, fin, fout, nx, ny, P, c, tdev, toff, a15f, st);
         case 4:
-            return launch_step_t<S, 4, 0>(cfg, fin, fout, nx, ny, P, c, tdev, toff, st);
+            return launch_step_t<S, 4, 0>(cfg, fin, fout, nx, ny, P, c, tdev, toff, a15f, st);
         case 8:
             if constexpr (S != ST_F32)
-                return launch_step_t<S, 8, 0>(cfg, fin, fout, nx, ny, P, c, tdev, toff, st);
+                return launch_step_t<S, 8, 0>(cfg, fin, fout, nx, ny, P, c, tdev, toff, a15f, st);
             return cudaErrorInvalidValue;
         default:
             return cudaErrorInvalidValue;
@@ -217,21 +242,36 @@ static Err launch_step_s(const TileCfg &cfg, const void *fin, void *fout, int nx
 
 Err launch_step(int storage, const TileCfg &cfg, const void *fin, void *fout, int nx, int ny,
                 size_t P, const Coef &c, int *status, int rnd, const uint32_t *tdev, uint32_t toff,
-                cudaStream_t st) {
+                const float *a15f, cudaStream_t st) {
     switch (storage) {
         case ST_F32:
-            return launch_step_s<ST_F32>(cfg, fin, fout, nx, ny, P, c, status, rnd, tdev, toff, st);
+            return launch_step_s<ST_F32>(cfg, fin, fout, nx, ny, P, c, status, rnd, tdev, toff,
+                                         a15f, st);
         case ST_F16:
-            return launch_step_s<ST_F16>(cfg, fin, fout, nx, ny, P, c, status, rnd, tdev, toff, st);
+            return launch_step_s<ST_F16>(cfg, fin, fout, nx, ny, P, c, status, rnd, tdev, toff,
+                                         a15f, st);
         case ST_BF16:
             return launch_step_s<ST_BF16>(cfg, fin, fout, nx, ny, P, c, status, rnd, tdev, toff,
-                                          st);
+                                          a15f, st);
         default:
             return cudaErrorInvalidValue;
     }
 }
 
 __global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
+
+// 1.5 alpha per site from c^2 per site (alpha = 1/3 - c^2, Section 3, Eq. 8).
+__global__ void k_a15_from_c2(const double *c2, float *a15, long long n) {
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (long long)gridDim.x * blockDim.x)
+        a15[s] = (float)(1.5 * (1.0 / 3.0 - c2[s]));
+}
+
+Err launch_a15_from_c2(const double *c2, float *a15, long long n, cudaStream_t st) {
+    long long b = (n + 255) / 256;
+    k_a15_from_c2<<<(unsigned)(b < 4096 ? b : 4096), 256, 0, st>>>(c2, a15, n);
+    return cudaGetLastError();
+}
 
 Err launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t st) {
     k_set_u32<<<1, 1, 0, st>>>(p, v);

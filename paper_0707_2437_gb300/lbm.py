@@ -68,6 +68,7 @@ def load() -> ctypes.CDLL:
             "lbm_tune": ([vp, ctypes.c_char_p], i),
             "lbm_set_pipeline": ([vp, i], i),
             "lbm_set_rounding": ([vp, i], i),
+            "lbm_set_c2_field": ([vp, vp, i], i),
             "lbm_get_rounding": ([vp, ctypes.POINTER(i)], i),
             "lbm_get_pipeline": ([vp, ctypes.POINTER(i), ctypes.POINTER(i)], i),
             "lbm_set_timing": ([vp, i], i),
@@ -246,6 +247,17 @@ class Grid:
         _check(self.lib.lbm_get_config(self.h, ctypes.byref(v), ctypes.byref(r), ctypes.byref(w)),
                "lbm_get_config")
         return v.value, r.value, w.value
+
+    def set_c2_field(self, c2):
+        """Per-site c_e^2 ([ny, nx] float64, host or CUDA), or None for the
+        grid's uniform c^2."""
+        if c2 is None:
+            _check(self.lib.lbm_set_c2_field(self.h, None, 0), "lbm_set_c2_field")
+            return
+        p, dev, keep = _ptr(c2)
+        if tuple(keep.shape) != (self.ny, self.nx):
+            raise ValueError("c2 field shape mismatch")
+        _check(self.lib.lbm_set_c2_field(self.h, p, dev), "lbm_set_c2_field")
 
     def set_rounding(self, mode: str):
         """'nearest' or 'stochastic' (16-bit storage only)."""
