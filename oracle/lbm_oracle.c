@@ -155,6 +155,80 @@ void oracle_step_field(int nx, int ny, double tau, const double *alpha,
     }
 }
 
+/* One step of the driven channel of Section 4 (the runs of Fig. 1).  The
+ * paper prescribes rho(t) and u = 0 at x = 0 and rho = 1, u = 0 at the far end
+ * without giving a boundary scheme; the reading taken here is equilibrium
+ * columns: after the collision, the post-collision distributions of column
+ * x = 0 are replaced by fbar(rho_left, u = 0) and those of the last two
+ * columns by fbar(rho_right, u = 0), then everything streams as usual.  The
+ * far-end condition spans two columns so that the periodic wrap in x, which
+ * brings column 0's values into column nx-1, reaches no interior gradient:
+ * the density of column nx-1 enters only the gradients of columns nx-2 and 0,
+ * both of which are overwritten.  Periodic in y.  Needs nx >= 4. */
+void oracle_step_driven(int nx, int ny, double tau, const double *alpha, double rho_left,
+                        double rho_right, double *f, double *work, double *rho, double *ux,
+                        double *uy) {
+    long n = (long)nx * ny;
+    oracle_moments(nx, ny, f, rho, ux, uy);
+    for (long s = 0; s < n; s++) {
+        int x = (int)(s % nx), y = (int)(s / nx);
+        double gx = 0.5 * (rho[(long)y * nx + wrap(x + 1, nx)] -
+                           rho[(long)y * nx + wrap(x - 1, nx)]);
+        double gy = 0.5 * (rho[(long)wrap(y + 1, ny) * nx + x] -
+                           rho[(long)wrap(y - 1, ny) * nx + x]);
+        double feq[9];
+        oracle_equilibrium(rho[s], ux[s], uy[s], feq);
+        for (int i = 0; i < 9; i++) {
+            double fi = f[i * n + s];
+            double force = 3.0 * W[i] * alpha[s] * (gx * EX[i] + gy * EY[i]);
+            work[i * n + s] = fi - (fi - feq[i]) / tau + force;
+        }
+    }
+    for (int y = 0; y < ny; y++) {
+        double fl[9], fr[9];
+        oracle_equilibrium(rho_left, 0.0, 0.0, fl);
+        oracle_equilibrium(rho_right, 0.0, 0.0, fr);
+        for (int i = 0; i < 9; i++) {
+            work[i * n + (long)y * nx] = fl[i];
+            work[i * n + (long)y * nx + nx - 2] = fr[i];
+            work[i * n + (long)y * nx + nx - 1] = fr[i];
+        }
+    }
+    for (long s = 0; s < n; s++) {
+        int x = (int)(s % nx), y = (int)(s / nx);
+        for (int i = 0; i < 9; i++) {
+            long d = (long)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
+            f[i * n + d] = work[i * n + s];
+        }
+    }
+}
+
+/* Runs `steps` driven-channel steps, the step from time t to t+1 using
+ * rho_left(t) = 1 + amp sin(2 pi t / period) (Section 4: a sinusoidal density
+ * with a period of 500 steps in the paper), rho_right = 1, for
+ * t = t0 .. t0+steps-1; one alpha for the grid. */
+int oracle_run_driven(int nx, int ny, double tau, double alpha, long t0, long steps, double amp,
+                      double period, double *f) {
+    long n = (long)nx * ny;
+    if (nx < 4) return -2;
+    double *work = (double *)malloc(sizeof(double) * 9 * n);
+    double *buf = (double *)malloc(sizeof(double) * 4 * n);
+    if (!work || !buf) {
+        free(work);
+        free(buf);
+        return -1;
+    }
+    double *al = buf, *rho = buf + n, *ux = buf + 2 * n, *uy = buf + 3 * n;
+    for (long s = 0; s < n; s++) al[s] = alpha;
+    const double two_pi = 6.283185307179586476925287;
+    for (long t = t0; t < t0 + steps; t++)
+        oracle_step_driven(nx, ny, tau, al, 1.0 + amp * sin(two_pi * (double)t / period), 1.0, f,
+                           work, rho, ux, uy);
+    free(work);
+    free(buf);
+    return 0;
+}
+
 /* Runs `steps` steps with one alpha for the whole grid. */
 int oracle_run(int nx, int ny, double tau, double alpha, int grad_mode,
                long steps, double *f) {

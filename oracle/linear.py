@@ -97,3 +97,40 @@ def max_growth(n: int, tau: float, alpha: float, grad: str = "central") -> float
     ks = 2 * np.pi * np.arange(n) / n
     return max(spectral_radius(kx, ky, tau, alpha, grad)
                for kx in ks for ky in ks)
+
+
+def driven_wave(omega: float, tau: float, alpha: float, grad: str = "central"):
+    """The wave a boundary driven at angular frequency ``omega`` (per step)
+    sends along +x, as in the sound-speed runs of Section 4: the complex
+    wavenumber k at which M(k, 0) has the eigenvalue exp(-i omega), so that
+    a_i exp(i (k x - omega t)) is a mode (Im k > 0: spatial decay).
+
+    Returns a dict with ``k``, ``c_phase`` = omega / Re k (the speed a
+    time-of-flight measurement sees), ``impedance`` = U / R (complex: the
+    x-velocity over the density amplitude of the eigenvector, U = sum a_i
+    e_ix, R = sum a_i; the plane-wave relation of Section 4 gives
+    U / R = c_e at rho0 = 1) and ``decay`` = Im k per lattice unit.
+    Solved by the secant method on k from omega / sqrt(1/3 - alpha)."""
+    target = np.exp(-1j * omega)
+
+    def g(k):
+        lam = np.linalg.eigvals(update_matrix(k, 0.0, tau, alpha, grad))
+        return lam[np.argmin(np.abs(lam - target))] - target
+
+    k0 = omega / np.sqrt(1.0 / 3.0 - alpha) + 0j
+    k1 = k0 * (1 + 1e-3)
+    g0, g1 = g(k0), g(k1)
+    for _ in range(100):
+        if g1 == g0:
+            break
+        k2 = k1 - g1 * (k1 - k0) / (g1 - g0)
+        k0, g0, k1 = k1, g1, k2
+        g1 = g(k1)
+        if abs(g1) < 1e-14:
+            break
+    lam, vec = np.linalg.eig(update_matrix(k1, 0.0, tau, alpha, grad))
+    v = vec[:, np.argmin(np.abs(lam - target))]
+    R, U = v.sum(), (v * EX).sum()
+    return {"k": complex(k1), "c_phase": float(omega / k1.real),
+            "impedance": complex(U / R), "decay": float(k1.imag),
+            "residual": float(abs(g1))}

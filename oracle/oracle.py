@@ -78,6 +78,10 @@ def _load():
                                          ctypes.c_long, dp]
         lib.oracle_run_field.restype = ctypes.c_int
         lib.oracle_sums.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
+        lib.oracle_run_driven.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_long, ctypes.c_long,
+                                          ctypes.c_double, ctypes.c_double, dp]
+        lib.oracle_run_driven.restype = ctypes.c_int
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_set_threads.restype = ctypes.c_int
         _lib = lib
@@ -143,6 +147,25 @@ def run(f: np.ndarray, tau: float, alpha, steps: int,
                                   int(steps), _ptr(f))
     if rc != 0:
         raise MemoryError("oracle_run: allocation failed")
+    return f
+
+
+def run_driven(f: np.ndarray, tau: float, alpha: float, t0: int, steps: int, amp: float,
+               period: float) -> np.ndarray:
+    """Driven channel of Section 4 (the runs of Fig. 1), in place.  After each
+    collision the post-collision distributions of column 0 become the
+    equilibrium at rho = 1 + amp sin(2 pi t / period), u = 0, and those of
+    columns nx-2 and nx-1 the equilibrium at rho = 1, u = 0 (the reading taken
+    where the paper names the boundary values but no scheme); periodic in y.
+    Steps t = t0 .. t0+steps-1; needs nx >= 4."""
+    assert f.dtype == np.float64 and f.flags["C_CONTIGUOUS"]
+    _, ny, nx = f.shape
+    rc = _load().oracle_run_driven(nx, ny, float(tau), float(alpha), int(t0), int(steps),
+                                   float(amp), float(period), _ptr(f))
+    if rc == -2:
+        raise ValueError("oracle_run_driven: needs nx >= 4")
+    if rc != 0:
+        raise MemoryError("oracle_run_driven: allocation failed")
     return f
 
 

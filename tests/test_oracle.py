@@ -14,7 +14,8 @@ import pytest
 
 from oracle import exact, linear, oracle
 from paper_0707_2437_gb300 import workloads
-from tests.helpers import fit_damped_cos, fit_decay, harmonic_amplitudes, mode_sin_cos
+from tests.helpers import (driven_estimates, driven_plan, fit_damped_cos, fit_decay,
+                           harmonic_amplitudes, mode_sin_cos)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")
 
@@ -331,3 +332,86 @@ def test_nonlinearity_grows_as_sound_speed_falls():
     for ce in (0.2, 0.5):
         r = h2[(ce, 4e-3)] / h2[(ce, 2e-3)]
         assert 1.7 < r < 2.3, (ce, r)
+
+
+# ---------------------------------------------------------------------------
+# Driven channel (Section 4, the sound-speed runs of Fig. 1).
+
+def test_driven_boundary_emits_boundary_equilibrium():
+    """The values streamed out of column 0 after a driven step are
+    fbar_i(rho_b(t), u = 0) = w_i rho_b(t) (Eq. 2 at u = 0) with rho_b the
+    sinusoid of the last step, and those out of the far columns w_i * 1."""
+    nx, ny, tau, alpha, amp, per = 64, 5, 0.7, 0.1, 3e-2, 37.0
+    rho, ux, uy = workloads.fourier_modes(nx, ny, amp=1e-2, seed=9)
+    f = oracle.init(rho, ux, uy)
+    t0, steps = 11, 23
+    oracle.run_driven(f, tau, alpha, t0, steps, amp, per)
+    tl = t0 + steps - 1
+    rb = 1.0 + amp * np.sin(2 * np.pi * tl / per)
+    for i in range(9):
+        # Pre-collision value at x holds the post-collision value of x - e_i.
+        for xs, r in ((0, rb), (nx - 2, 1.0), (nx - 1, 1.0)):
+            xd = (xs + oracle.EX[i]) % nx
+            # Row y receives from row y - e_iy; the boundary rows are all equal.
+            np.testing.assert_allclose(f[i][:, xd], oracle.W[i] * r, rtol=0, atol=1e-15)
+
+
+def test_driven_boundary_is_local():
+    """Away from the boundary columns the driven step is the periodic step of
+    Eq. 5: a central-difference step reaches 2 sites, so after n steps the
+    sites farther than 2n + 2 columns from columns 0 and nx-2 equal the
+    periodic run."""
+    nx, ny, tau, alpha, n = 96, 4, 0.8, -0.2, 6
+    rho, ux, uy = workloads.fourier_modes(nx, ny, amp=1e-2, seed=2)
+    fa = oracle.init(rho, ux, uy)
+    fb = fa.copy()
+    oracle.run_driven(fa, tau, alpha, 0, n, 5e-2, 20.0)
+    oracle.run(fb, tau, alpha, n)
+    lo, hi = 2 * n + 3, nx - 2 - (2 * n + 3)
+    np.testing.assert_allclose(fa[:, :, lo:hi], fb[:, :, lo:hi], rtol=0, atol=1e-15)
+    assert np.abs(fa[:, :, :2] - fb[:, :, :2]).max() > 1e-4
+
+
+def test_driven_boundary_rejects_short_channel():
+    f = oracle.init(np.ones((2, 3)), np.zeros((2, 3)), np.zeros((2, 3)))
+    with pytest.raises(ValueError):
+        oracle.run_driven(f, 0.7, 0.0, 0, 1, 1e-3, 10.0)
+
+
+def _driven_oracle_speeds(ce, tau=0.53, amp=1e-4, period=500.0):
+    alpha = 1 / 3 - ce * ce
+    x1, D, t0, t1, every = driven_plan(ce, period)
+    nx = 64 * int(np.ceil((1.3 * ce * t1 + 16) / 64))
+    f = oracle.init(np.ones((4, nx)), np.zeros((4, nx)), np.zeros((4, nx)))
+    oracle.run_driven(f, tau, alpha, 0, t0, amp, period)
+    ts, r1, r2, u1 = [], [], [], []
+    for t in range(t0, t1, every):
+        r, u, _ = oracle.moments(f)
+        ts.append(t)
+        r1.append(r[:, x1].mean())
+        r2.append(r[:, x1 + D].mean())
+        u1.append(u[:, x1].mean())
+        oracle.run_driven(f, tau, alpha, t, every, amp, period)
+    return driven_estimates(ts, r1, r2, u1, D, 2 * np.pi / period)
+
+
+@pytest.mark.parametrize("ce,tol", [(0.1, 1e-3), (0.3651, 1e-6), (1.125, 1e-6)])
+def test_driven_channel_sound_speed_matches_driven_wave_theory(ce, tol):
+    """Section 4, Fig. 1: the wave launched by a density boundary oscillating
+    with a period of 500 steps, measured both ways the paper uses (time of
+    flight between two probes, and u / c_e = (rho - rho0) / rho0 at the near
+    probe), equals the speed and impedance of the driven-wave solution of the
+    linearised Eq. 5 (a separate eigenvalue computation), also above c_e = 1.
+    Far from alpha = 1/3 both equal Eq. 8, c_e = sqrt(1/3 - alpha), to 5e-4;
+    at c_e = 0.1 the central-difference gradient raises the speed by 5 %
+    at this wavelength (50 sites), as the discrete theory predicts."""
+    tau, period = 0.53, 500.0
+    alpha = 1 / 3 - ce * ce
+    c_tof, c_imp = _driven_oracle_speeds(ce, tau, period=period)
+    lin = linear.driven_wave(2 * np.pi / period, tau, alpha)
+    assert abs(c_tof / lin["c_phase"] - 1) < tol, (c_tof, lin["c_phase"])
+    assert abs(c_imp / abs(lin["impedance"]) - 1) < tol, (c_imp, lin["impedance"])
+    if ce > 0.3:
+        assert abs(c_tof / ce - 1) < 5e-4 and abs(c_imp / ce - 1) < 5e-4
+    else:
+        assert 0.03 < c_tof / ce - 1 < 0.08
