@@ -142,6 +142,27 @@ int lbm_sums(lbm_t h, double *out3);
  * v = A sin(2 pi kx x / nx) gives out2 = {0, A}.  Waits for the stream. */
 int lbm_mode(lbm_t h, int field, int kx, int ky, double *out2);
 
+/* Driven channel in x, the setup of the sound-speed runs of Section 4
+ * (Fig. 1): a plane wave launched from x = 0, where the density varies
+ * sinusoidally at zero velocity, into fluid held at rho = 1, u = 0 at the far
+ * end.  The paper gives the boundary values but no scheme; this library
+ * uses equilibrium columns.  After every step, the post-collision values
+ * of column 0 become fbar_i(rho_b(t), u = 0) = w_i rho_b(t) with
+ *   rho_b(t) = 1 + amplitude sin(2 pi t / period),
+ * t the step number (the step from t to t+1, mod 2^32), and those of columns
+ * nx-2 and nx-1 become w_i * 1.  The far end spans two columns, so the
+ * periodic wrap in x, which links column nx-1 to column 0, carries nothing
+ * into the interior.  y stays periodic.
+ *   on         1 to drive, 0 to return to a fully periodic grid
+ *   amplitude  |amplitude| < 1 (the paper's runs are small-amplitude)
+ *   period     steps per cycle, finite and > 0 (500 in the paper)
+ * Needs nx >= 4.  Each step then runs one extra small kernel (27 ny
+ * stores), and long step calls use CUDA graphs instead of the persistent
+ * launch.  A driven grid cannot join a batch: lbm_batch_create and
+ * lbm_batch_step return LBM_EINVAL.  Waits for the grid's stream; returns
+ * LBM_EINVAL for a bad argument. */
+int lbm_set_drive(lbm_t h, int on, double amplitude, double period);
+
 /* Spatially varying sound speed (the paper's Section 5 outlook: alpha set per
  * site, for example for a temperature gradient or an acoustic lens).  c2 is a
  * [ny][nx] array of c_e^2 > 0 (host if on_device == 0, else device; host
@@ -149,7 +170,8 @@ int lbm_mode(lbm_t h, int field, int kx, int ky, double *out2);
  * Eq. 5.  NULL returns to the grid's uniform c2.  The field costs one more
  * 4-byte read per site and step.  While a field is set: lbm_step uses the
  * step kernel (vec <= 4, no bulk-copy pipeline, nearest rounding), and the
- * grid cannot join a batch (lbm_batch_create returns LBM_EINVAL). */
+ * grid cannot join a batch (lbm_batch_create and lbm_batch_step return
+ * LBM_EINVAL). */
 int lbm_set_c2_field(lbm_t h, const double *c2, int on_device);
 
 /* Steps taken since lbm_init / lbm_set_state. */

@@ -249,11 +249,23 @@ extern "C" int lbm_init(lbm_t h, const double *rho, const double *ux, const doub
     return LBM_OK;
 }
 
-// One step launch from buf[cur] to buf[cur ^ 1] (no bookkeeping).
+// The driven-channel boundary columns for the step numbered *tdev + toff,
+// written into the buffer that step produced.
+static cudaError_t launch_drive(lbm_grid *h, void *out, const uint32_t *tdev, uint32_t toff,
+                                cudaStream_t st) {
+    return launch_drive_x(h->storage, out, h->nx, h->ny, h->P, h->rho0, h->drive_amp,
+                          h->drive_period, tdev, toff, st);
+}
+
+// One step launch from buf[cur] to buf[cur ^ 1] (no bookkeeping), followed
+// by the boundary columns when the channel is driven.
 static cudaError_t launch_one(lbm_grid *h, int from) {
-    return launch_step(h->storage, h->cfg, h->buf[from], h->buf[from ^ 1], h->nx, h->ny, h->P,
-                       h->coef, status_ptr(h), h->rounding, nullptr, (uint32_t)h->t, h->a15f,
-                       h->stream);
+    cudaError_t e = launch_step(h->storage, h->cfg, h->buf[from], h->buf[from ^ 1], h->nx, h->ny,
+                                h->P, h->coef, status_ptr(h), h->rounding, nullptr,
+                                (uint32_t)h->t, h->a15f, h->stream);
+    if (e == cudaSuccess && h->drive)
+        e = launch_drive(h, h->buf[from ^ 1], nullptr, (uint32_t)h->t, h->stream);
+    return e;
 }
 
 static const int kGraphPairs = 16;   // a graph holds 32 steps
@@ -268,11 +280,14 @@ static int build_graphs(lbm_grid *h) {
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            for (int k = 0; k < 2 * kGraphPairs && e == cudaSuccess; ++k)
+            for (int k = 0; k < 2 * kGraphPairs && e == cudaSuccess; ++k) {
                 e = launch_step(h->storage, h->cfg, h->buf[(start + k) & 1],
                                 h->buf[(start + k + 1) & 1], h->nx, h->ny, h->P, h->coef,
                                 status_ptr(h), h->rounding, step_ptr(h), (uint32_t)k, h->a15f,
                                 cs);
+                if (e == cudaSuccess && h->drive)
+                    e = launch_drive(h, h->buf[(start + k + 1) & 1], step_ptr(h), (uint32_t)k, cs);
+            }
             cudaError_t e2 = cudaStreamEndCapture(cs, &g);
             if (e == cudaSuccess) e = e2;
         }
@@ -311,7 +326,7 @@ extern "C" int lbm_step(lbm_t h, long long n) {
         h->kernel_launches = n;
         return LBM_OK;
     }
-    if (h->persistent && !h->a15f && n >= kPersistentMin) {
+    if (h->persistent && !h->a15f && !h->drive && n >= kPersistentMin) {
         // One persistent launch of all n steps (dynamic tile scheduling,
         // barrier between steps), bitwise the same as n single launches.
         if (!h->self_batch) {
@@ -328,7 +343,8 @@ extern "C" int lbm_step(lbm_t h, long long n) {
         }
         long long per = 2LL * h->graph_pairs;
         while (n >= per) {
-            if (h->rounding) CK(launch_set_u32(step_ptr(h), (uint32_t)h->t, h->stream));
+            if (h->rounding || h->drive)
+                CK(launch_set_u32(step_ptr(h), (uint32_t)h->t, h->stream));
             CK(cudaGraphLaunch(h->graph[h->cur], h->stream));
             n -= per;
             h->t += per;  // an even number of steps leaves cur unchanged
@@ -537,6 +553,24 @@ extern "C" int lbm_set_c2_field(lbm_t h, const double *c2, int on_device) {
     for (double *p : owned) cudaFreeAsync(p, h->stream);
     if (rc != LBM_OK) return rc;
     CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_drive(lbm_t h, int on, double amplitude, double period) {
+    if (!h) return fail(LBM_EINVAL, "lbm_set_drive: NULL handle");
+    if (on) {
+        if (h->nx < 4) return fail(LBM_EINVAL, "lbm_set_drive: needs nx >= 4");
+        if (!(period > 0.0) || !isfinite(period))
+            return fail(LBM_EINVAL, "lbm_set_drive: period must be finite and > 0");
+        if (!isfinite(amplitude) || !(fabs(amplitude) < 1.0))
+            return fail(LBM_EINVAL, "lbm_set_drive: need |amplitude| < 1");
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
+    drop_self_batch(h);
+    h->drive = on != 0;
+    h->drive_amp = on ? amplitude : 0.0;
+    h->drive_period = on ? period : 0.0;
     return LBM_OK;
 }
 

@@ -344,6 +344,8 @@ extern "C" int lbm_batch_create(const lbm_t *grids, int n, lbm_batch_t *out) {
         if (!grids[k]) return bfail(LBM_EINVAL, "lbm_batch_create: NULL grid");
         if (grids[k]->a15f)
             return bfail(LBM_EINVAL, "lbm_batch_create: grids with a c2 field are not batched");
+        if (grids[k]->drive)
+            return bfail(LBM_EINVAL, "lbm_batch_create: driven grids are not batched");
     }
     lbm_batch *b = new (std::nothrow) lbm_batch();
     if (!b) return bfail(LBM_ENOMEM, "lbm_batch_create: host allocation failed");
@@ -473,6 +475,9 @@ static int run_batch(lbm_batch *b, long long n, const long long *limits, bool ad
 extern "C" int lbm_batch_step(lbm_batch_t b, long long n, const long long *limits) {
     if (!b || n < 0) return bfail(LBM_EINVAL, "lbm_batch_step: bad argument");
     if (n == 0) return LBM_OK;
+    for (lbm_grid *g : b->grids)
+        if (g->a15f || g->drive)
+            return bfail(LBM_EINVAL, "lbm_batch_step: a grid gained a c2 field or a drive");
     return run_batch(b, n, limits, true);
 }
 

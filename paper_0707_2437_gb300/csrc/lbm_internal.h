@@ -75,6 +75,10 @@ Err launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t st);
 Err prepare_step(int storage, const TileCfg &cfg);
 Err launch_init(int storage, void *f, int nx, int ny, size_t P, double rho0, const double *rho,
                 const double *ux, const double *uy, cudaStream_t st);
+// Driven-channel boundary columns (Section 4, Fig. 1 runs) on the buffer a
+// step just wrote; step number *tdev + toff (tdev may be NULL).
+Err launch_drive_x(int storage, void *f, int nx, int ny, size_t P, double rho0, double amp,
+                   double period, const uint32_t *tdev, uint32_t toff, cudaStream_t st);
 Err launch_moments(int storage, const void *f, int nx, int ny, size_t P, double rho0, double *rho,
                    double *ux, double *uy, cudaStream_t st);
 // FP64 reductions: `partials` holds at least reduce_partials_needed() doubles
@@ -105,6 +109,9 @@ struct lbm_grid {
     vss::TileCfg cfg{};
     int rounding = 0;             // 1: stochastic rounding of 16-bit stores
     float *a15f = nullptr;        // spatially varying alpha: 1.5 alpha per site
+    // Driven channel in x (lbm_set_drive): boundary columns after every step.
+    bool drive = false;
+    double drive_amp = 0, drive_period = 0;
     double *scratch = nullptr;    // reduction partials + results
     double *host_out = nullptr;   // pinned, 8 doubles
     // CUDA graphs of 2*graph_pairs steps starting from buffer 0 or buffer 1

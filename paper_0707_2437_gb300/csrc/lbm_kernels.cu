@@ -332,6 +332,30 @@ __global__ void k_init(void *f, int nx, int ny, size_t P, double rho0, const dou
     }
 }
 
+// Driven channel of Section 4 (the runs of Fig. 1), applied after a step to
+// the buffer the step wrote (post-collision values stored at their source
+// site): column 0 becomes the equilibrium at rho = 1 + amp sin(2 pi t /
+// period), u = 0, and columns nx-2 and nx-1 the equilibrium at rho = 1,
+// u = 0.  At u = 0 the equilibrium of Eq. 2 is w_i rho, so the stored
+// deviation is h_i = rho - rho0 in every direction.  The step number is
+// t = *tdev + toff (tdev may be NULL), taken mod 2^32.
+template <int S>
+__global__ void k_drive_x(void *f, int nx, int ny, size_t P, double rho0, double amp,
+                          double period, const uint32_t *tdev, uint32_t toff) {
+    const uint32_t t = (tdev ? *tdev : 0u) + toff;
+    const double hb = (1.0 + amp * sin(6.283185307179586476925287 * (double)t / period)) - rho0;
+    const double hr = 1.0 - rho0;
+    const long long n = 27LL * ny;  // 9 planes x 3 columns x ny rows
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int col = (int)(k % 3);
+        const long long r = k / 3;
+        const int y = (int)(r % ny), i = (int)(r / ny);
+        const int x = col == 0 ? 0 : nx - 3 + col;  // 0, nx-2, nx-1
+        st_elem_d<S>(f, (size_t)i * P + (size_t)y * nx + x, col == 0 ? hb : hr);
+    }
+}
+
 // Moments (Section 2, Eq. 3) of the current state in FP64.
 template <int S>
 __device__ __forceinline__ void site_moments_d(const void *f, int nx, int ny, size_t P, int x,
@@ -488,6 +512,15 @@ Err launch_init(int storage, void *f, int nx, int ny, size_t P, double rho0, con
                 const double *ux, const double *uy, cudaStream_t st) {
     DISPATCH_S(storage, (k_init<S_><<<side_blocks(nx, ny), 256, 0, st>>>(f, nx, ny, P, rho0, rho,
                                                                          ux, uy)));
+    return cudaGetLastError();
+}
+
+Err launch_drive_x(int storage, void *f, int nx, int ny, size_t P, double rho0, double amp,
+                   double period, const uint32_t *tdev, uint32_t toff, cudaStream_t st) {
+    long long b = (27LL * ny + 255) / 256;
+    unsigned nb = (unsigned)(b < 1024 ? b : 1024);
+    DISPATCH_S(storage, (k_drive_x<S_><<<nb, 256, 0, st>>>(f, nx, ny, P, rho0, amp, period, tdev,
+                                                            toff)));
     return cudaGetLastError();
 }
 

@@ -69,6 +69,7 @@ def load() -> ctypes.CDLL:
             "lbm_set_pipeline": ([vp, i], i),
             "lbm_set_rounding": ([vp, i], i),
             "lbm_set_c2_field": ([vp, vp, i], i),
+            "lbm_set_drive": ([vp, i, ctypes.c_double, ctypes.c_double], i),
             "lbm_get_rounding": ([vp, ctypes.POINTER(i)], i),
             "lbm_get_pipeline": ([vp, ctypes.POINTER(i), ctypes.POINTER(i)], i),
             "lbm_set_timing": ([vp, i], i),
@@ -258,6 +259,17 @@ class Grid:
         if tuple(keep.shape) != (self.ny, self.nx):
             raise ValueError("c2 field shape mismatch")
         _check(self.lib.lbm_set_c2_field(self.h, p, dev), "lbm_set_c2_field")
+
+    def set_drive(self, amplitude: float | None, period: float = 500.0):
+        """Driven channel in x (Section 4, the Fig. 1 runs): after each step
+        column 0 holds the equilibrium at rho = 1 + amplitude sin(2 pi t /
+        period), u = 0, and columns nx-2, nx-1 the equilibrium at rho = 1,
+        u = 0.  None returns to a periodic grid."""
+        if amplitude is None:
+            _check(self.lib.lbm_set_drive(self.h, 0, 0.0, 0.0), "lbm_set_drive")
+        else:
+            _check(self.lib.lbm_set_drive(self.h, 1, float(amplitude), float(period)),
+                   "lbm_set_drive")
 
     def set_rounding(self, mode: str):
         """'nearest' or 'stochastic' (16-bit storage only)."""

@@ -1,0 +1,151 @@
+"""Driven channel (Section 4, the sound-speed runs of Fig. 1) on the GPU path:
+parity with the oracle's driven channel, the graph path against single
+launches, and c_e against alpha measured both ways the paper uses, from
+c_e = 0.1 up to the largest stable value the paper reports (1.125)."""
+import numpy as np
+import pytest
+
+from oracle import linear, oracle
+from paper_0707_2437_gb300 import workloads
+from tests.helpers import driven_estimates, driven_plan
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-6), ("f16d", 2e-5), ("bf16d", 2e-4)])
+@pytest.mark.parametrize("nx,ny,steps", [(512, 4, 300), (130, 9, 201), (37, 23, 77)])
+def test_driven_channel_matches_oracle(lbm, storage, tol, nx, ny, steps):
+    """Driven grid (amplitude 1e-3, period 50, on top of seeded Fourier modes)
+    against the oracle's driven channel; step calls of 5 and of the rest mix
+    single launches with the graph path."""
+    rho, ux, uy = workloads.fourier_modes(nx, ny, amp=1e-3, seed=nx + ny)
+    tau, c2, amp, per = 0.6, 0.3, 1e-3, 50.0
+    with lbm.Grid(nx, ny, tau, c2, storage) as g:
+        g.set_drive(amp, per)
+        g.init(rho, ux, uy)
+        g.step(5)
+        g.step(steps - 5)
+        got = g.moments()
+    f = oracle.init(rho, ux, uy)
+    oracle.run_driven(f, tau, 1 / 3 - c2, 0, steps, amp, per)
+    ref = oracle.moments(f)
+    err = max(np.abs(a - b).max() for a, b in zip(got, ref))
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("kind", ["f32", "f16d-sr"])
+def test_driven_graph_path_equals_single_launches(lbm, kind):
+    """One call of 96 steps (CUDA graphs, step number from the device
+    counter) leaves the same state bit for bit as 96 calls of one step."""
+    nx, ny = 256, 8
+    f = workloads.fourier_modes(nx, ny, amp=1e-3, seed=5)
+    out = []
+    for split in (False, True):
+        with lbm.Grid(nx, ny, 0.7, 0.25, kind.replace("-sr", "")) as g:
+            if kind.endswith("-sr"):
+                g.set_rounding("stochastic")
+            g.set_drive(2e-3, 40.0)
+            g.init(*f)
+            if split:
+                for _ in range(96):
+                    g.step(1)
+            else:
+                g.step(96)
+            assert g.t == 96
+            out.append(g.get_state()[0])
+    assert np.array_equal(out[0], out[1])
+
+
+def test_drive_off_restores_periodic_step(lbm):
+    """After set_drive(None) the grid steps exactly as a never-driven grid."""
+    nx, ny = 192, 6
+    f = workloads.fourier_modes(nx, ny, amp=1e-3, seed=8)
+    with lbm.Grid(nx, ny, 0.8, 0.2) as g:
+        g.init(*f)
+        g.set_drive(1e-3, 30.0)
+        g.step(50)
+        state, t = g.get_state()
+        g.set_drive(None)
+        g.step(100)
+        a = g.get_state()[0]
+    with lbm.Grid(nx, ny, 0.8, 0.2) as h:
+        h.set_state(state, t)
+        h.step(100)
+        b = h.get_state()[0]
+    assert np.array_equal(a, b)
+
+
+def test_drive_argument_checks(lbm):
+    with lbm.Grid(3, 4, 0.8, 0.2) as g:
+        with pytest.raises(lbm.LbmError):
+            g.set_drive(1e-3, 500.0)
+    with lbm.Grid(64, 4, 0.8, 0.2) as g:
+        for amp, per in ((1e-3, 0.0), (1e-3, -5.0), (1.0, 500.0), (float("nan"), 500.0),
+                         (1e-3, float("inf"))):
+            with pytest.raises(lbm.LbmError):
+                g.set_drive(amp, per)
+        g.set_drive(1e-3, 500.0)
+        with pytest.raises(lbm.LbmError):
+            lbm.Batch([g])
+
+
+def test_batch_step_rejects_grid_driven_after_batching(lbm):
+    g = lbm.Grid(64, 8, 0.8, 0.2)
+    g.init(*workloads.fourier_modes(64, 8, amp=1e-3, seed=1))
+    b = lbm.Batch([g])
+    b.step(2)
+    g.set_drive(1e-3, 50.0)
+    with pytest.raises(lbm.LbmError):
+        b.step(2)
+    g.set_drive(None)
+    b.step(2)
+    b.sync()
+    b.close()
+    g.close()
+
+
+# Fig. 1 sweep: alpha from near 1/3 (c_e = 0.1) through c_e = 1 to 1.125.
+CES = [0.1, 0.2, 0.3651, 0.5774, 0.7958, 0.9, 1.0, 1.0878, 1.125]
+
+
+def test_sound_speed_against_alpha_fig1(lbm):
+    """Section 4, Fig. 1: density driven at x = 0 with a 500-step period,
+    amplitude 1e-4, tau = 0.53, 8192 x 4 channel.  Both estimates (time of
+    flight between two probes; u / c_e = (rho - rho0) / rho0 at the near probe)
+    equal the driven-wave solution of the linearised Eq. 5 to 2e-4 (1e-3 at
+    c_e = 0.1), and Eq. 8 to 5e-4 wherever the central-difference offset of
+    the discrete scheme is below that (c_e >= 0.36); above c_e = 1 the waves
+    propagate stably at the predicted speed."""
+    tau, amp, period, nx = 0.53, 1e-4, 500.0, 8192
+    om = 2 * np.pi / period
+    rows = []
+    for ce in CES:
+        alpha = 1 / 3 - ce * ce
+        x1, D, t0, t1, every = driven_plan(ce, period)
+        assert 1.3 * ce * t1 + 16 < nx
+        with lbm.Grid(nx, 4, tau, ce * ce) as g:
+            g.set_drive(amp, period)
+            g.init(np.ones((4, nx)), np.zeros((4, nx)), np.zeros((4, nx)))
+            g.step(t0)
+            ts, r1, r2, u1 = [], [], [], []
+            while g.t < t1:
+                r, u, _ = g.moments()
+                ts.append(g.t)
+                r1.append(r[:, x1].mean())
+                r2.append(r[:, x1 + D].mean())
+                u1.append(u[:, x1].mean())
+                g.step(every)
+            r, _, _ = g.moments()
+            assert np.all(np.isfinite(r)) and np.abs(r - 1).max() < 10 * amp
+        c_tof, c_imp = driven_estimates(ts, r1, r2, u1, D, om)
+        lin = linear.driven_wave(om, tau, alpha)
+        rows.append((alpha, ce, c_tof, c_imp, lin["c_phase"], abs(lin["impedance"])))
+    print("\nalpha     Eq.8 c_e  c_tof     c_imp     theory(tof)  theory(imp)")
+    for a, ce, ct, ci, lt, li in rows:
+        print(f"{a:+.5f}  {ce:.4f}   {ct:.5f}   {ci:.5f}   {lt:.5f}      {li:.5f}")
+    for a, ce, ct, ci, lt, li in rows:
+        tol = 1e-3 if ce < 0.15 else 2e-4
+        assert abs(ct / lt - 1) < tol, (ce, ct, lt)
+        assert abs(ci / li - 1) < tol, (ce, ci, li)
+        if ce > 0.3:
+            assert abs(ct / ce - 1) < 5e-4 and abs(ci / ce - 1) < 5e-4, (ce, ct, ci)
