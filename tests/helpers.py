@@ -74,3 +74,60 @@ def driven_estimates(t, rho1, rho2, u1, D: int, omega: float):
     c_tof = D * omega / lag
     c_imp = abs(zu) / abs(z1)
     return float(c_tof), float(c_imp)
+
+
+def oracle_cone_window(fields, tau: float, alpha: float, steps: int, y0: int, x0: int, h: int,
+                       w: int, crop_every: int = 100):
+    """Exact oracle moments after ``steps`` steps on the window [y0, y0+h) x
+    [x0, x0+w) of a large periodic grid, computed from the window's dependency
+    cone only.  The central-difference step of Eq. 5 reaches 2 sites per step
+    (streaming 1, the gradient 1 more), so a periodic oracle run on the window
+    grown by 2 (steps - t) + 2 on each side is exact on the target window at
+    step ``steps``; the state is re-cropped every ``crop_every`` steps as the
+    cone narrows.  ``fields`` = (rho, ux, uy) of the whole grid, [ny, nx]."""
+    from oracle import oracle
+
+    ny, nx = fields[0].shape
+    m = 2 * steps + 2
+    ys = np.arange(y0 - m, y0 + h + m) % ny
+    xs = np.arange(x0 - m, x0 + w + m) % nx
+    f = oracle.init(*(np.ascontiguousarray(a[np.ix_(ys, xs)]) for a in fields))
+    t = 0
+    while t < steps:
+        n = min(crop_every, steps - t)
+        oracle.run(f, tau, alpha, n)
+        t += n
+        cut = m - (2 * (steps - t) + 2)
+        if cut > 0:
+            f = np.ascontiguousarray(f[:, cut:f.shape[1] - cut, cut:f.shape[2] - cut])
+            m -= cut
+    r, u, v = oracle.moments(f)
+    sl = (slice(m, m + h), slice(m, m + w))
+    return r[sl], u[sl], v[sl]
+
+
+def linear_mode_prediction(z0: complex, kx: float, ky: float, tau: float, alpha: float,
+                           steps: int, zux: complex = 0j, zuy: complex = 0j):
+    """Complex amplitudes (rho, u_x, u_y) after ``steps`` steps of a mode that
+    starts as the equilibrium at rho = 1 + Re(z0 exp(i k.x)),
+    u = Re((zux, zuy) exp(i k.x)), by the linearised update M(k) (wavevector
+    in radians per site; first order in the amplitudes, rho0 = 1).  With
+    zux = zuy = 0 returns the density amplitude alone."""
+    from oracle import linear
+
+    M = linear.update_matrix(kx, ky, tau, alpha)
+    a0 = linear.W * (z0 + 3.0 * (linear.EX * zux + linear.EY * zuy))
+    a = np.linalg.matrix_power(M, steps) @ a0
+    if zux == 0 and zuy == 0:
+        return complex(a.sum())
+    return complex(a.sum()), complex(a @ linear.EX), complex(a @ linear.EY)
+
+
+def low_modes(field: np.ndarray, kmax: int = 4):
+    """(2/N) sum field exp(-i k.x) for integer wave numbers |kx|, |ky| <= kmax,
+    as a [2 kmax + 1, 2 kmax + 1] array indexed [ky + kmax, kx + kmax]."""
+    ny, nx = field.shape
+    ks = np.arange(-kmax, kmax + 1)
+    ex = np.exp(-2j * np.pi * np.outer(ks, np.arange(nx)) / nx)
+    ey = np.exp(-2j * np.pi * np.outer(ks, np.arange(ny)) / ny)
+    return 2.0 * (ey @ (field @ ex.T)) / (nx * ny)

@@ -15,7 +15,8 @@ import pytest
 from oracle import exact, linear, oracle
 from paper_0707_2437_gb300 import workloads
 from tests.helpers import (driven_estimates, driven_plan, fit_damped_cos, fit_decay,
-                           harmonic_amplitudes, mode_sin_cos)
+                           harmonic_amplitudes, linear_mode_prediction, mode_sin_cos,
+                           oracle_cone_window)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")
 
@@ -415,3 +416,33 @@ def test_driven_channel_sound_speed_matches_driven_wave_theory(ce, tol):
         assert abs(c_tof / ce - 1) < 5e-4 and abs(c_imp / ce - 1) < 5e-4
     else:
         assert 0.03 < c_tof / ce - 1 < 0.08
+
+
+def test_cone_window_equals_full_grid_run():
+    """The windowed oracle used for sampled full-size parity equals the
+    whole-grid run on the window, bit for bit."""
+    nx, ny, tau, alpha, steps = 150, 130, 0.7, 0.1, 23
+    fields = workloads.fourier_modes(nx, ny, amp=1e-2, seed=4)
+    full = oracle.simulate(*fields, tau, 1 / 3 - alpha, steps)
+    y0, x0, h, w = 120, 7, 9, 13   # wraps in y
+    got = oracle_cone_window(fields, tau, alpha, steps, y0, x0, h, w, crop_every=5)
+    ys = np.arange(y0, y0 + h) % ny
+    for a, b in zip(got, full):
+        assert np.array_equal(a, b[np.ix_(ys, np.arange(x0, x0 + w))])
+
+
+def test_linear_mode_prediction_matches_small_amplitude_run():
+    """The linearised mode evolution used for the long full-size checks agrees
+    with an oracle run of one small-amplitude oblique mode."""
+    nx, ny, tau, alpha, steps = 64, 48, 0.6, 0.2, 300
+    kx, ky = 2 * np.pi * 3 / nx, 2 * np.pi * (-2) / ny
+    x = np.arange(nx)[None, :]
+    y = np.arange(ny)[:, None]
+    z0 = 1e-6 * np.exp(0.7j)
+    rho = 1 + np.real(z0 * np.exp(1j * (kx * x + ky * y)))
+    f = oracle.init(rho, np.zeros_like(rho), np.zeros_like(rho))
+    oracle.run(f, tau, alpha, steps)
+    r, _, _ = oracle.moments(f)
+    z = 2 * np.mean((r - 1) * np.exp(-1j * (kx * x + ky * y)))
+    pred = linear_mode_prediction(z0, kx, ky, tau, alpha, steps)
+    assert abs(z - pred) < 1e-6 * abs(z0)
