@@ -235,22 +235,39 @@ def run_native(args):
     stages, pipelined = grids[0].get_pipeline()
     sites = sum(r.nx * r.ny for r in runs)
     batch = lbm.Batch(grids) if args.path == "batch" else None
+    if batch is not None and args.batch_prefetch:
+        batch.set_prefetch(args.batch_prefetch)
 
-    def one_step():
+    # Launch plan: on the batch path every launch is one persistent
+    # cooperative kernel running `spl` steps of all grids (grid barrier between
+    # steps), as lbm_batch_step runs a long call; the single-grid path launches
+    # one step kernel per grid and step.
+    spl = max(1, args.steps_per_launch) if batch is not None else 1
+
+    def chunks(n):
+        out = []
+        while n > 0:
+            out.append(min(spl, n))
+            n -= out[-1]
+        return out
+
+    def advance(n):
         if batch is not None:
-            batch.step(1)
+            batch.step(n)
         else:
             for g in grids:
-                g.step(1)
+                g.step(n)
 
-    for _ in range(args.warmup):
-        one_step()
+    for c in chunks(args.warmup):
+        advance(c)
     torch.cuda.synchronize()
 
     # Timed region: events around every launch on the launching stream.
+    plan = chunks(args.steps)
     per_step = 1 if batch is not None else len(grids)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps * per_step)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps * per_step)]
+    n_launch = len(plan) if batch is not None else args.steps * per_step
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(n_launch)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(n_launch)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
@@ -259,13 +276,14 @@ def run_native(args):
     torch.cuda.synchronize()
     t_start.record(stream)
     k = 0
-    for _ in range(args.steps):
-        if batch is not None:
+    if batch is not None:
+        for c in plan:
             starts[k].record(stream)
-            batch.step(1)
+            batch.step(c)
             ends[k].record(stream)
             k += 1
-        else:
+    else:
+        for _ in range(args.steps):
             for g in grids:
                 starts[k].record(stream)
                 g.step(1)
@@ -282,19 +300,44 @@ def run_native(args):
     elapsed_ms = max_over_ranks(ws, elapsed_ms)
     value = ws * sites * args.steps / (elapsed_ms * 1e-3) / 1e6
 
-    # Roofline of the dominant kernel: algorithmic bytes per launch / mean
-    # launch time (one launch = one step of all grids on the batch path, one
-    # step of one grid on the single-grid path).
+    # Roofline of the dominant kernel: algorithmic bytes of a launch / its
+    # time, averaged over the launches (a launch = `spl` steps of all grids on
+    # the batch path, one step of one grid on the single-grid path).
+    per_step_bytes = BYTES_PER_LU[storage] * (sites if batch is not None
+                                              else runs[0].nx * runs[0].ny)
+    steps_launched = plan if batch is not None else [1] * n_launch
+    achieved = per_step_bytes * sum(steps_launched) / (sum(launch_ms) * 1e-3) / 1e9
     per_launch_s = statistics.mean(launch_ms) * 1e-3
-    alg_bytes = BYTES_PER_LU[storage] * (sites if batch is not None else runs[0].nx * runs[0].ny)
-    achieved = alg_bytes / per_launch_s / 1e9
+    alg_bytes = per_step_bytes * (spl if batch is not None else 1)
     peak, peak_kind = measured_peak()
     traffic = None
     if os.path.exists(PROFILE_TRAFFIC):
         tj = json.load(open(PROFILE_TRAFFIC))
         if (tj.get("source_hash") == kernel_source_hash() and tj.get("storage") == storage
-                and tj.get("path") == args.path):
-            traffic = tj.get("dram_bytes_per_launch")
+                and tj.get("path") == args.path and batch is not None):
+            # Captured on one-step launches of the same kernel; a launch of
+            # `spl` steps moves `spl` times the bytes of one step.
+            per = tj.get("dram_bytes_per_step")
+            traffic = per * spl if per is not None else None
+
+    # The same batch with one step per launch, for the launch overhead.
+    one_step = None
+    if batch is not None and spl > 1:
+        n1 = max(20, args.steps // 20)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(n1)]
+        batch.step(1)
+        torch.cuda.synchronize()
+        for a, b_ in ev:
+            a.record(stream)
+            batch.step(1)
+            b_.record(stream)
+        torch.cuda.synchronize()
+        ms1 = statistics.mean(a.elapsed_time(b_) for a, b_ in ev)
+        one_step = {"launches": n1, "mean_launch_ms": ms1,
+                    "achieved": per_step_bytes / (ms1 * 1e-3) / 1e9,
+                    "frac": per_step_bytes / (ms1 * 1e-3) / 1e9 / peak,
+                    "mlups": sites / (ms1 * 1e-3) / 1e6}
 
     # The plain single-grid step kernel on the same grids (one launch per grid
     # and step), for its own roofline fraction.
@@ -374,14 +417,17 @@ def run_native(args):
                    "rows": cfg[1], "warps": cfg[2],
                    "pipeline_stages": stages if pipelined else 0},
                    "l2": "inputs larger than L2 (2 x 151 MB per grid, 129 MB L2), no flush",
-                   "path": ("one persistent launch per step over the 9 grids (batch API)"
+                   "path": (f"persistent launches of {spl} steps over the 9 grids (batch API, "
+                            "grid barrier between steps)"
                             if batch is not None else "one step-kernel launch per grid and step"),
+                   "steps_per_launch": spl,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
-                     "kernel": ("k_batch_one (persistent, 9 grids)" if batch is not None
+                     "kernel": (f"k_batch_one (persistent, 9 grids, {spl} steps per launch)"
+                                if batch is not None
                                 else f"k_step_tma<{storage},stages={stages}>" if pipelined
                                 else f"k_step<{storage},vec={cfg[0]}>"),
                      "algorithmic_bytes_per_launch": alg_bytes,
@@ -393,9 +439,10 @@ def run_native(args):
                         f"({'one batch launch' if batch is not None else 'lbm_step per grid'}), "
                         f"lbm_moments to host, for all {len(runs)} grids",
                 "jobs": args.e2e_jobs},
-        "gpu_launches": args.steps * per_step,
+        "gpu_launches": n_launch,
         "clocks": clk,
         "single_grid_kernel": single,
+        "batch_one_step_per_launch": one_step,
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
@@ -433,6 +480,8 @@ def run_batch_workload(args):
     b = lbm.Batch(grids)
     if args.batch_rows:
         b.set_config(args.batch_rows, 0)
+    if args.batch_prefetch:
+        b.set_prefetch(args.batch_prefetch)
     if args.tune:
         b.tune()
     bcfg = b.get_config()
@@ -520,6 +569,10 @@ def main():
                     help="rounding of 16-bit stores")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-rows", type=int, default=0)
+    ap.add_argument("--batch-prefetch", type=int, default=0, choices=[0, 1, 2],
+                    help="rows of loads in flight per warp in 16-bit batch kernels (0: default)")
+    ap.add_argument("--steps-per-launch", type=int, default=20,
+                    help="steps of all grids per persistent launch on the batch path")
     ap.add_argument("--tune", action="store_true")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the serving comparison in the default workload")

@@ -44,35 +44,48 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
+// Barrier and scheduling words, each on its own 128-byte line: the arrival
+// count, the generation the waiting blocks poll, and the two tile counters
+// (the counters' atomics must not queue behind the polling).
+constexpr int kBarGen = 32;     // generation (word offset)
+constexpr int kCtr = 64;        // tile counter of even steps; odd steps at kCtr + 32
+constexpr int kBarWords = 128;  // words allocated
+
 // Grid-wide barrier over all blocks of a cooperative launch.  bar[0] counts
-// arrivals, bar[1] is the generation.  Returns false if the wait ran out or
-// another block reported an error.
+// arrivals, bar[kBarGen] is the generation.  Waiting blocks poll with a
+// sleep that doubles from 64 ns to 1 us, and look at the status word and the
+// clock every 16 polls.  Returns false if the wait ran out or another block
+// reported an error.
 __device__ bool grid_barrier(unsigned *bar, int *status, unsigned long long timeout_ns) {
     __shared__ int ok_sh;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned *vgen = bar + 1;
+        volatile unsigned *vgen = bar + kBarGen;
         unsigned gen = *vgen;
         __threadfence();
         unsigned prev = atomicAdd(bar, 1u);
         if (prev == gridDim.x - 1) {
             atomicExch(bar, 0u);
             __threadfence();
-            atomicAdd(bar + 1, 1u);
+            atomicAdd(bar + kBarGen, 1u);
         } else {
             unsigned long long t0 = global_ns();
-            while (*vgen == gen) {
-                if (*(volatile int *)status != 0) {
-                    ok = 0;
-                    break;
+            unsigned ns = 64;
+            for (unsigned it = 0; *vgen == gen; ++it) {
+                if ((it & 15u) == 15u) {
+                    if (*(volatile int *)status != 0) {
+                        ok = 0;
+                        break;
+                    }
+                    if (global_ns() - t0 > timeout_ns) {
+                        atomicCAS(status, 0, LBM_ETIMEOUT);
+                        ok = 0;
+                        break;
+                    }
                 }
-                if (global_ns() - t0 > timeout_ns) {
-                    atomicCAS(status, 0, LBM_ETIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(128);
+                __nanosleep(ns);
+                if (ns < 1024u) ns *= 2u;
             }
         }
         __threadfence();
@@ -87,14 +100,18 @@ __device__ bool grid_barrier(unsigned *bar, int *status, unsigned long long time
 // index from a counter (one per step parity; the counter of step k is reset
 // during step k+1, and the barrier at the end of k+1 orders that reset before
 // step k+2 uses it again).  Uneven tiles then balance across warps.
+__device__ __forceinline__ unsigned *step_counter(unsigned *bar, long long k) {
+    return bar + kCtr + 32 * (int)(k & 1);
+}
+
 __device__ __forceinline__ int next_tile(unsigned *ctr) {
     unsigned v = 0;
     if ((threadIdx.x & 31) == 0) v = atomicAdd(ctr, 1u);
     return (int)__shfl_sync(FULL, v, 0);
 }
 
-__device__ __forceinline__ void reset_counter(unsigned *ctr, long long k) {
-    if (k >= 1 && blockIdx.x == 0 && threadIdx.x == 0) ctr[(k - 1) & 1] = 0u;
+__device__ __forceinline__ void reset_counter(unsigned *bar, long long k) {
+    if (k >= 1 && blockIdx.x == 0 && threadIdx.x == 0) *step_counter(bar, k - 1) = 0u;
 }
 
 template <int S, int V, bool PF = false, int RND = 0>
@@ -112,10 +129,10 @@ __global__ void __launch_bounds__(32 * kBatchWarps, 3)
             const long long *__restrict__ limit, const int *__restrict__ parity0,
             const uint32_t *__restrict__ t0, long long nsteps, unsigned *bar, int *status,
             unsigned long long timeout_ns) {
-    unsigned *ctr = bar + 2;  // two tile counters follow the barrier words
     for (long long k = 0; k < nsteps; ++k) {
-        reset_counter(ctr, k);
-        for (int ti = next_tile(ctr + (k & 1)); ti < ntiles; ti = next_tile(ctr + (k & 1))) {
+        reset_counter(bar, k);
+        unsigned *ctr = step_counter(bar, k);
+        for (int ti = next_tile(ctr); ti < ntiles; ti = next_tile(ctr)) {
             const Tile t = tiles[ti];
             if (k >= limit[t.grid]) continue;
             const GridDesc &g = grids[t.grid];
@@ -125,17 +142,17 @@ __global__ void __launch_bounds__(32 * kBatchWarps, 3)
                 case ST_F32 * 16 + 4:
                     do_tile<ST_F32, 4>(g, par, t, step);
                     break;
-                case ST_F32 * 16 + 1:
-                    do_tile<ST_F32, 1>(g, par, t, step);
-                    break;
                 case ST_F16 * 16 + 4:
                     do_tile<ST_F16, 4, true>(g, par, t, step);
                     break;
-                case ST_F16 * 16 + 1:
-                    do_tile<ST_F16, 1>(g, par, t, step);
-                    break;
                 case ST_BF16 * 16 + 4:
                     do_tile<ST_BF16, 4, true>(g, par, t, step);
+                    break;
+                case ST_F32 * 16 + 1:
+                    do_tile<ST_F32, 1>(g, par, t, step);
+                    break;
+                case ST_F16 * 16 + 1:
+                    do_tile<ST_F16, 1>(g, par, t, step);
                     break;
                 case ST_BF16 * 16 + 1:
                     do_tile<ST_BF16, 1>(g, par, t, step);
@@ -161,29 +178,35 @@ __global__ void __launch_bounds__(32 * kBatchWarps, 3)
 }
 
 // Specialised persistent kernel for a batch whose grids all use one walk
-// (storage, vec, prefetch, rounding): the walk is inlined, so the kernel keeps
-// the single-grid kernel's register budget (128, 16 warps per SM) instead of
-// paying for calls.  Same time-step loop and bounded barrier as k_batch.
-template <int S, int V, bool PF, int RND>
-__global__ void __launch_bounds__(32 * kBatchWarps, 4)
+// (storage, vec, rounding, rows of loads in flight PD = 0, 1 or 2): the walk is
+// inlined, so the kernel keeps the single-grid kernel's register budget (128,
+// 16 warps per SM; 170 and 12 warps per SM for the two-row prefetch) instead
+// of paying for calls.  Same time-step loop and bounded barrier as k_batch.
+template <int S, int V, int PD, int RND>
+__global__ void __launch_bounds__(32 * kBatchWarps, PD == 2 ? 3 : 4)
     k_batch_one(const GridDesc *__restrict__ grids, const Tile *__restrict__ tiles, int ntiles,
                 const long long *__restrict__ limit, const int *__restrict__ parity0,
                 const uint32_t *__restrict__ t0, long long nsteps, unsigned *bar, int *status,
                 unsigned long long timeout_ns) {
-    unsigned *ctr = bar + 2;
     for (long long k = 0; k < nsteps; ++k) {
-        reset_counter(ctr, k);
-        for (int ti = next_tile(ctr + (k & 1)); ti < ntiles; ti = next_tile(ctr + (k & 1))) {
+        reset_counter(bar, k);
+        unsigned *ctr = step_counter(bar, k);
+        for (int ti = next_tile(ctr); ti < ntiles; ti = next_tile(ctr)) {
             const Tile t = tiles[ti];
             if (k >= limit[t.grid]) continue;
-            const GridDesc g = grids[t.grid];
+            // Fields are read through a reference: a local copy indexed by the
+            // run-time parity would live in local memory.
+            const GridDesc &g = grids[t.grid];
             const int par = (parity0[t.grid] + (int)(k & 1)) & 1;
+            const Coef c = g.c;
             Walker<S, V, LD_CG, RND> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P, t.x0);
             if constexpr (RND) w.rstep = t0[t.grid] + (uint32_t)k;
-            if constexpr (PF)
-                w.run_prefetch(t.y0, t.y1, t.dir, g.c);
+            if constexpr (PD == 2)
+                w.run_prefetch2(t.y0, t.y1, t.dir, c);
+            else if constexpr (PD == 1)
+                w.run_prefetch(t.y0, t.y1, t.dir, c);
             else
-                w.run(t.y0, t.y1, t.dir, g.c);
+                w.run(t.y0, t.y1, t.dir, c);
         }
         if (k + 1 < nsteps && !grid_barrier(bar, status, timeout_ns)) return;
     }
@@ -193,22 +216,24 @@ using BatchKernel = void (*)(const GridDesc *, const Tile *, int, const long lon
                              const uint32_t *, long long, unsigned *, int *, unsigned long long);
 
 // The kernel for a set of kinds: a specialised one when every grid has the
-// same kind, else the general k_batch.
-BatchKernel kernel_for(const std::vector<int> &kinds) {
+// same kind, else the general k_batch.  `prefetch` (1 or 2) picks the rows of
+// loads in flight of the 16-bit specialised kernels.
+BatchKernel kernel_for(const std::vector<int> &kinds, int prefetch) {
     bool same = true;
     for (int k : kinds) same = same && k == kinds[0];
     if (!kinds.empty() && same) {
+        const bool two = prefetch == 2;
         switch (kinds[0]) {
             case ST_F32 * 16 + 4:
-                return k_batch_one<ST_F32, 4, false, 0>;
+                return k_batch_one<ST_F32, 4, 0, 0>;
             case ST_F16 * 16 + 4:
-                return k_batch_one<ST_F16, 4, true, 0>;
+                return two ? k_batch_one<ST_F16, 4, 2, 0> : k_batch_one<ST_F16, 4, 1, 0>;
             case ST_BF16 * 16 + 4:
-                return k_batch_one<ST_BF16, 4, true, 0>;
+                return two ? k_batch_one<ST_BF16, 4, 2, 0> : k_batch_one<ST_BF16, 4, 1, 0>;
             case ST_F16 * 16 + 8 + 4:
-                return k_batch_one<ST_F16, 4, true, 1>;
+                return two ? k_batch_one<ST_F16, 4, 2, 1> : k_batch_one<ST_F16, 4, 1, 1>;
             case ST_BF16 * 16 + 8 + 4:
-                return k_batch_one<ST_BF16, 4, true, 1>;
+                return two ? k_batch_one<ST_BF16, 4, 2, 1> : k_batch_one<ST_BF16, 4, 1, 1>;
             default:
                 break;
         }
@@ -224,8 +249,16 @@ struct lbm_batch {
     int device = 0;
     int rows = 16;
     int blocks_per_sm = 0;  // 0: the occupancy limit
-    int max_blocks_per_sm = 1;
-    BatchKernel kernel = nullptr;  // k_batch or a specialised k_batch_one
+    // Kind groups: consecutive ranges of the tile list, each run by its own
+    // persistent launch (a specialised k_batch_one, or k_batch for the rest),
+    // one after the other on the batch's stream.
+    struct Group {
+        int begin = 0, count = 0;
+        BatchKernel kernel = nullptr;
+        int max_blocks_per_sm = 1;
+    };
+    std::vector<Group> groups;
+    int prefetch = 1;              // rows of loads in flight (16-bit specialised kernels)
     int sms = 1;
     unsigned long long timeout_ns = 1000000000ULL;
     // device
@@ -300,19 +333,64 @@ static int build_worklist(lbm_batch *b) {
                 tiles.push_back(Tile{(int)k, x0, y0, std::min(g->ny, y0 + b->rows),
                                      (seg & 1) ? -1 : 1});
     }
+    // Kind groups.  A kind with a specialised kernel runs in its own launch
+    // when its tiles fill at least half the resident warps of that kernel (the
+    // launch then stays bandwidth-bound); all other tiles share one launch of
+    // the general kernel, where small grids of any kind overlap.  A batch of
+    // one kind is one group.
+    std::vector<int> count(256, 0);
+    for (const Tile &t : tiles) count[gd[t.grid].kind & 255]++;
+    int kinds_present = 0;
+    for (int kd = 0; kd < 256; ++kd) kinds_present += count[kd] > 0;
+    std::vector<int> own, rest;
+    for (int kd = 0; kd < 256; ++kd) {
+        if (!count[kd]) continue;
+        BatchKernel kk = kernel_for({kd}, b->prefetch);
+        int bps = 0;
+        if (kk != (BatchKernel)k_batch)
+            BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void *)kk,
+                                                              32 * kBatchWarps, 0));
+        if (kk != (BatchKernel)k_batch &&
+            (kinds_present == 1 || 2LL * count[kd] >= (long long)bps * b->sms * kBatchWarps))
+            own.push_back(kd);
+        else
+            rest.push_back(kd);
+    }
+    std::vector<Tile> ordered;
+    ordered.reserve(tiles.size());
+    b->groups.clear();
+    auto add_group = [&](const std::vector<int> &kinds_in) -> int {
+        lbm_batch::Group gr;
+        gr.begin = (int)ordered.size();
+        for (const Tile &t : tiles) {
+            int kd = gd[t.grid].kind & 255;
+            if (std::find(kinds_in.begin(), kinds_in.end(), kd) != kinds_in.end())
+                ordered.push_back(t);
+        }
+        gr.count = (int)ordered.size() - gr.begin;
+        gr.kernel = kernel_for(kinds_in, b->prefetch);
+        BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gr.max_blocks_per_sm,
+                                                          (const void *)gr.kernel,
+                                                          32 * kBatchWarps, 0));
+        if (gr.max_blocks_per_sm < 1) return bfail(LBM_ECUDA, "batch kernel cannot be resident");
+        b->groups.push_back(gr);
+        return LBM_OK;
+    };
+    for (int kd : own) {
+        int rc = add_group({kd});
+        if (rc != LBM_OK) return rc;
+    }
+    if (!rest.empty()) {
+        int rc = add_group(rest);
+        if (rc != LBM_OK) return rc;
+    }
     if (b->d_tiles) cudaFree(b->d_tiles);
     b->d_tiles = nullptr;
-    BCK(cudaMalloc(&b->d_tiles, sizeof(Tile) * std::max<size_t>(1, tiles.size())));
+    BCK(cudaMalloc(&b->d_tiles, sizeof(Tile) * std::max<size_t>(1, ordered.size())));
     BCK(cudaMemcpy(b->d_grids, gd.data(), sizeof(GridDesc) * gd.size(), cudaMemcpyHostToDevice));
-    BCK(cudaMemcpy(b->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice));
-    b->ntiles = (int)tiles.size();
-    std::vector<int> kinds;
-    for (auto &d : gd) kinds.push_back(d.kind);
-    b->kernel = kernel_for(kinds);
-    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->max_blocks_per_sm,
-                                                      (const void *)b->kernel,
-                                                      32 * kBatchWarps, 0));
-    if (b->max_blocks_per_sm < 1) return bfail(LBM_ECUDA, "batch kernel cannot be resident");
+    BCK(cudaMemcpy(b->d_tiles, ordered.data(), sizeof(Tile) * ordered.size(),
+                   cudaMemcpyHostToDevice));
+    b->ntiles = (int)ordered.size();
     drop_graph(b);
     return LBM_OK;
 }
@@ -365,7 +443,7 @@ extern "C" int lbm_batch_create(const lbm_t *grids, int n, lbm_batch_t *out) {
     if (e == cudaSuccess) e = cudaMalloc(&b->d_limit, sizeof(long long) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_parity, sizeof(int) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_t0, sizeof(uint32_t) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_bar, sizeof(unsigned) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_bar, sizeof(unsigned) * kBarWords);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_limit, sizeof(long long) * n);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_parity, sizeof(int) * n);
@@ -387,9 +465,9 @@ extern "C" int lbm_batch_create(const lbm_t *grids, int n, lbm_batch_t *out) {
     return LBM_OK;
 }
 
-static int grid_blocks(const lbm_batch *b) {
-    int per = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, b->max_blocks_per_sm)
-                                   : b->max_blocks_per_sm;
+static int grid_blocks(const lbm_batch *b, const lbm_batch::Group &g) {
+    int per = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, g.max_blocks_per_sm)
+                                   : g.max_blocks_per_sm;
     return per * b->sms;
 }
 
@@ -403,23 +481,30 @@ static cudaError_t enqueue(lbm_batch *b, long long n, cudaStream_t st) {
                             st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_t0, b->h_t0, sizeof(uint32_t) * ng, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned) * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     const GridDesc *grids = b->d_grids;
-    const Tile *tiles = b->d_tiles;
-    int ntiles = b->ntiles;
     const long long *lim = b->d_limit;
     const int *par = b->d_parity;
     const uint32_t *t0 = b->d_t0;
     unsigned *bar = b->d_bar;
     int *status = b->d_status;
     unsigned long long to = b->timeout_ns;
-    void *args[] = {(void *)&grids, (void *)&tiles, (void *)&ntiles, (void *)&lim,
-                    (void *)&par,   (void *)&t0,    (void *)&n,      (void *)&bar,
-                    (void *)&status, (void *)&to};
-    return cudaLaunchCooperativeKernel((const void *)b->kernel, dim3(grid_blocks(b)),
-                                       dim3(32 * kBatchWarps), args, 0, st);
+    // The groups hold disjoint grids: each launch advances its grids by all n
+    // steps.  Barrier words and tile counters start at zero for every launch.
+    for (const lbm_batch::Group &gr : b->groups) {
+        e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned) * kBarWords, st);
+        if (e != cudaSuccess) return e;
+        const Tile *tiles = b->d_tiles + gr.begin;
+        int ntiles = gr.count;
+        void *args[] = {(void *)&grids, (void *)&tiles, (void *)&ntiles, (void *)&lim,
+                        (void *)&par,   (void *)&t0,    (void *)&n,      (void *)&bar,
+                        (void *)&status, (void *)&to};
+        e = cudaLaunchCooperativeKernel((const void *)gr.kernel, dim3(grid_blocks(b, gr)),
+                                        dim3(32 * kBatchWarps), args, 0, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 static int run_batch(lbm_batch *b, long long n, const long long *limits, bool advance) {
@@ -504,6 +589,27 @@ extern "C" int lbm_batch_set_config(lbm_batch_t b, int rows, int blocks_per_sm) 
     return LBM_OK;
 }
 
+extern "C" int lbm_batch_set_prefetch(lbm_batch_t b, int rows_ahead) {
+    if (!b || rows_ahead < 1 || rows_ahead > 2)
+        return bfail(LBM_EINVAL, "lbm_batch_set_prefetch: rows_ahead must be 1 or 2");
+    BCK(cudaStreamSynchronize(b->stream));
+    if (rows_ahead == b->prefetch) return LBM_OK;
+    b->prefetch = rows_ahead;
+    return build_worklist(b);
+}
+
+extern "C" int lbm_batch_get_groups(lbm_batch_t b, int *groups) {
+    if (!b || !groups) return bfail(LBM_EINVAL, "lbm_batch_get_groups: bad argument");
+    *groups = (int)b->groups.size();
+    return LBM_OK;
+}
+
+extern "C" int lbm_batch_get_prefetch(lbm_batch_t b, int *rows_ahead) {
+    if (!b || !rows_ahead) return bfail(LBM_EINVAL, "lbm_batch_get_prefetch: bad argument");
+    *rows_ahead = b->prefetch;
+    return LBM_OK;
+}
+
 extern "C" int lbm_batch_set_timeout_us(lbm_batch_t b, long long us) {
     if (!b || us < 1) return bfail(LBM_EINVAL, "lbm_batch_set_timeout_us: bad argument");
     b->timeout_ns = (unsigned long long)us * 1000ULL;
@@ -512,7 +618,8 @@ extern "C" int lbm_batch_set_timeout_us(lbm_batch_t b, long long us) {
 }
 
 // Times one-step dry runs (the state is not advanced: every grid writes its
-// other buffer) for several tile heights at full occupancy; keeps the fastest.
+// other buffer) for several tile heights, and for the 16-bit specialised
+// kernels both prefetch depths, each at its full occupancy; keeps the fastest.
 // A one-step launch does the same per-step work as a step inside a longer
 // launch (the barriers between steps cost microseconds per millisecond step).
 extern "C" int lbm_batch_tune(lbm_batch_t b) {
@@ -520,28 +627,40 @@ extern "C" int lbm_batch_tune(lbm_batch_t b) {
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0));
     BCK(cudaEventCreate(&e1));
-    int best_rows = b->rows;
+    int best_rows = b->rows, best_pf = b->prefetch;
     float best = 1e30f;
     const int rowss[] = {8, 12, 16, 24, 32};
-    for (int r : rowss) {
-        int rc = lbm_batch_set_config(b, r, 0);
+    std::vector<BatchKernel> k1;
+    for (int pf = 1; pf <= 2; ++pf) {
+        int rc = lbm_batch_set_prefetch(b, pf);
         if (rc != LBM_OK) return rc;
-        rc = run_batch(b, 1, nullptr, false);  // warm-up (and graph build)
-        if (rc != LBM_OK) return rc;
-        BCK(cudaEventRecord(e0, b->stream));
-        for (int k = 0; k < 4 && rc == LBM_OK; ++k) rc = run_batch(b, 1, nullptr, false);
-        if (rc != LBM_OK) return rc;
-        BCK(cudaEventRecord(e1, b->stream));
-        BCK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        BCK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-            best = ms;
-            best_rows = r;
+        std::vector<BatchKernel> ks;
+        for (const auto &gr : b->groups) ks.push_back(gr.kernel);
+        if (pf == 1) k1 = ks;
+        if (pf == 2 && ks == k1) break;  // the depth applies to none of these kernels
+        for (int r : rowss) {
+            rc = lbm_batch_set_config(b, r, 0);
+            if (rc != LBM_OK) return rc;
+            rc = run_batch(b, 1, nullptr, false);  // warm-up (and graph build)
+            if (rc != LBM_OK) return rc;
+            BCK(cudaEventRecord(e0, b->stream));
+            for (int k = 0; k < 4 && rc == LBM_OK; ++k) rc = run_batch(b, 1, nullptr, false);
+            if (rc != LBM_OK) return rc;
+            BCK(cudaEventRecord(e1, b->stream));
+            BCK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            BCK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                best_rows = r;
+                best_pf = pf;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    int rc = lbm_batch_set_prefetch(b, best_pf);
+    if (rc != LBM_OK) return rc;
     return lbm_batch_set_config(b, best_rows, 0);
 }
 
@@ -550,8 +669,11 @@ extern "C" int lbm_batch_get_config(lbm_batch_t b, int *rows, int *blocks_per_sm
     if (!b) return bfail(LBM_EINVAL, "lbm_batch_get_config: NULL batch");
     if (rows) *rows = b->rows;
     if (blocks_per_sm)
-        *blocks_per_sm = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, b->max_blocks_per_sm)
-                                              : b->max_blocks_per_sm;
-    if (specialised) *specialised = b->kernel != (BatchKernel)k_batch ? 1 : 0;
+        *blocks_per_sm = b->groups.empty() ? 0 : grid_blocks(b, b->groups[0]) / b->sms;
+    if (specialised) {
+        *specialised = 1;
+        for (const auto &gr : b->groups)
+            if (gr.kernel == (BatchKernel)k_batch) *specialised = 0;
+    }
     return LBM_OK;
 }

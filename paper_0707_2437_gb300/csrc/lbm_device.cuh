@@ -279,26 +279,39 @@ __device__ __forceinline__ Dither site_dither(uint32_t site, uint32_t step) {
     return d;
 }
 
-// FP32 -> 16-bit with round up probability equal to the discarded fraction:
-// add the dither, (d + 1/2)/256 of a unit in the last kept place, below the
-// kept bits of the magnitude, then truncate.  The half step centres the 256
-// dither levels, so the rounding is unbiased on average (without it the
-// levels d/256 round up too often by 1/512 unit, which slows the decay of
-// slow modes).  FP16 values below the smallest normal (2^-14) round to
-// nearest instead (their spacing is fixed, so a shift of the dither would not
-// match it).
+// FP32 -> 16-bit with round up probability equal to the discarded fraction,
+// on the stochastic-rounding conversions of sm_100-class GPUs (PTX cvt with
+// .rs rounding): the conversion adds the caller's random bits to the bits
+// the 16-bit format drops and truncates (FP16 drops 13 bits and takes the low
+// 13 random bits of its half of rbits, BF16 drops 16 and takes all 16; the
+// low half of rbits rounds the low element).  The random bits here are an
+// 8-bit dither d per element placed as (d + 1/2)/256 of a unit in the last
+// kept place; the half step centres the 256 levels, so the rounding is
+// unbiased on average (without it the levels d/256 round up too often by
+// 1/512 unit, which slows the decay of slow modes).  One instruction
+// converts a pair of elements.
+template <int S>
+__device__ __forceinline__ uint32_t sr_bits(uint32_t d_lo, uint32_t d_hi) {
+    if constexpr (S == ST_F16)
+        return ((d_lo << 5) | 0x10u) | (((d_hi << 5) | 0x10u) << 16);
+    else
+        return ((d_lo << 8) | 0x80u) | (((d_hi << 8) | 0x80u) << 16);
+}
+
+template <int S>
+__device__ __forceinline__ uint32_t sr_pack2(float lo, float hi, uint32_t rbits) {
+    uint32_t out;
+    if constexpr (S == ST_F16)
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(out) : "f"(hi), "f"(lo), "r"(rbits));
+    else
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(out) : "f"(hi), "f"(lo), "r"(rbits));
+    return out;
+}
+
+// One element (in the low half of the result).
 template <int S>
 __device__ __forceinline__ uint32_t sr_round(float x, uint32_t d) {
-    const uint32_t b = __float_as_uint(x);
-    const uint32_t sgn = b & 0x80000000u;
-    const uint32_t mag = b & 0x7fffffffu;
-    if constexpr (S == ST_BF16) {
-        return (sgn | (mag + ((d << 8) | 0x80u))) >> 16;  // 16 discarded bits
-    } else {
-        if (mag < 0x38800000u) return (uint32_t)__half_as_ushort(__float2half_rn(x));
-        const float y = __uint_as_float(sgn | (mag + ((d << 5) | 0x10u)));  // 13 discarded bits
-        return (uint32_t)__half_as_ushort(__float2half_rz(y));
-    }
+    return sr_pack2<S>(x, 0.0f, sr_bits<S>(d, 0u)) & 0xffffu;
 }
 
 // Sites per packed word: the 16-bit kinds convert two sites at a time.
@@ -542,8 +555,8 @@ struct Walker {
                 const Dither db = site_dither(site + 1u, rstep);
 #pragma unroll
                 for (int i = 0; i < 9; ++i)
-                    w[i][v0 >> 1] = sr_round<S>(h[0][i], da.get(i)) |
-                                    (sr_round<S>(h[1][i], db.get(i)) << 16);
+                    w[i][v0 >> 1] =
+                        sr_pack2<S>(h[0][i], h[1][i], sr_bits<S>(da.get(i), db.get(i)));
             } else {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
@@ -770,6 +783,59 @@ struct Walker {
                     wn[i][kk] = wf[i][kk];
                 }
             gn = gf;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                d2[v] = d1[v];
+                d1[v] = d0[v];
+            }
+            l1 = l0;
+            r1 = r0;
+        }
+    }
+
+    // The same walk with two rows of loads in flight ahead of the row being
+    // pulled (one more row of raw words in registers): for kernels run at
+    // lower occupancy, where one row per warp leaves too few bytes in flight.
+    __device__ __forceinline__ void run_prefetch2(int y0, int y1, int dir, const Coef &c) const {
+        int q0 = dir > 0 ? ((y0 == 0) ? ny - 1 : y0 - 1) : (y1 == ny ? 0 : y1);
+        int qm = (q0 == 0) ? ny - 1 : q0 - 1;
+        int qp = (q0 + 1 == ny) ? 0 : q0 + 1;
+
+        uint32_t wc[9][NW], wn[9][NW], wf[9][NW], wg[9][NW];
+        uint32_t gn, gf, gg;
+        float d2[V], d1[V], d0[V];
+        float l1 = 0.f, r1 = 0.f, l0, r0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            d2[v] = 0.f;
+            d1[v] = 0.f;
+        }
+        const int n = y1 - y0;
+        const int K = n + 2;  // K >= 3: every tile has at least one row
+        load_row(qm, q0, qp, wn, gn);
+        advance(qm, q0, qp, dir);
+        load_row(qm, q0, qp, wf, gf);
+        for (int k = 0; k < K; ++k) {
+            advance(qm, q0, qp, dir);
+            if (k + 2 < K) load_row(qm, q0, qp, wg, gg);
+            finish_pull(wn, gn, d0, l0, r0);
+            if (k >= 2) {
+                const int r = dir > 0 ? y0 + (k - 2) : y1 - 1 - (k - 2);
+                if (dir > 0)
+                    collide_store(r, wc, d1, d2, d0, l1, r1, c);
+                else
+                    collide_store(r, wc, d1, d0, d2, l1, r1, c);
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+#pragma unroll
+                for (int kk = 0; kk < NW; ++kk) {
+                    wc[i][kk] = wn[i][kk];
+                    wn[i][kk] = wf[i][kk];
+                    wf[i][kk] = wg[i][kk];
+                }
+            gn = gf;
+            gf = gg;
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 d2[v] = d1[v];

@@ -81,6 +81,9 @@ def load() -> ctypes.CDLL:
             "lbm_batch_sync": ([vp], i),
             "lbm_batch_set_config": ([vp, i, i], i),
             "lbm_batch_tune": ([vp], i),
+            "lbm_batch_set_prefetch": ([vp, i], i),
+            "lbm_batch_get_prefetch": ([vp, ctypes.POINTER(i)], i),
+            "lbm_batch_get_groups": ([vp, ctypes.POINTER(i)], i),
             "lbm_batch_get_config": ([vp, ctypes.POINTER(i), ctypes.POINTER(i),
                                       ctypes.POINTER(i)], i),
             "lbm_batch_set_timeout_us": ([vp, ll], i),
@@ -350,7 +353,16 @@ class Batch:
         r, b, sp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(self.lib.lbm_batch_get_config(self.b, ctypes.byref(r), ctypes.byref(b),
                                              ctypes.byref(sp)), "lbm_batch_get_config")
-        return {"rows": r.value, "blocks_per_sm": b.value, "specialised": bool(sp.value)}
+        pf = ctypes.c_int()
+        _check(self.lib.lbm_batch_get_prefetch(self.b, ctypes.byref(pf)), "lbm_batch_get_prefetch")
+        ng = ctypes.c_int()
+        _check(self.lib.lbm_batch_get_groups(self.b, ctypes.byref(ng)), "lbm_batch_get_groups")
+        return {"rows": r.value, "blocks_per_sm": b.value, "specialised": bool(sp.value),
+                "prefetch": pf.value, "groups": ng.value}
+
+    def set_prefetch(self, rows_ahead: int):
+        """Rows of loads in flight per warp (1 or 2) for 16-bit batches."""
+        _check(self.lib.lbm_batch_set_prefetch(self.b, int(rows_ahead)), "lbm_batch_set_prefetch")
 
     def set_timeout_us(self, us: int):
         _check(self.lib.lbm_batch_set_timeout_us(self.b, int(us)), "lbm_batch_set_timeout_us")

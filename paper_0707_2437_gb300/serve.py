@@ -150,7 +150,8 @@ class Server:
                 fields = g.moments() if self.keep_fields else None
                 if not self.keep_fields:
                     g.sync()
-                stats.results.append(Result(req.rid, req.arrival_s, adm, now(), req.steps,
+                arrival = req.arrival_s if realtime else 0.0
+                stats.results.append(Result(req.rid, arrival, adm, now(), req.steps,
                                             req.nx * req.ny, req.storage, fields))
                 g.close()
             if len(keep) != len(active):
@@ -167,7 +168,8 @@ class Server:
 def serve_fifo(requests, realtime: bool = True, storage: str = "f32",
                keep_fields: bool = False, stream=None) -> ServeStats:
     """Plain baseline: each request alone, in arrival order, single-grid
-    kernel, stored as `storage` (FP32 by default) whatever it asked for."""
+    kernel, stored as `storage` (FP32 by default) whatever it asked for.
+    With realtime=False every request is present at time 0."""
     lbm.load()
     stats = ServeStats()
     t0 = time.perf_counter()
@@ -183,7 +185,8 @@ def serve_fifo(requests, realtime: bool = True, storage: str = "f32",
             fields = g.moments() if keep_fields else None
             if not keep_fields:
                 g.sync()
-        stats.results.append(Result(req.rid, req.arrival_s, start, time.perf_counter() - t0,
+        arrival = req.arrival_s if realtime else 0.0
+        stats.results.append(Result(req.rid, arrival, start, time.perf_counter() - t0,
                                     req.steps, req.nx * req.ny, storage, fields))
         stats.lattice_updates += req.steps * req.nx * req.ny
         stats.max_active = 1

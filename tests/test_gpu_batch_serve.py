@@ -49,3 +49,76 @@ def test_fifo_baseline_runs(lbm):
     stats = serve.serve_fifo(reqs, realtime=False)
     assert [r.rid for r in stats.results] == [0, 1, 2]
     assert stats.summary()["mlups"] > 0
+
+
+@pytest.mark.parametrize("kind", ["f16d", "bf16d", "f16d-sr", "bf16d-sr"])
+@pytest.mark.parametrize("rows", [1, 5, 16])
+def test_batch_prefetch_depths_bitwise_equal(lbm, kind, rows):
+    """The 16-bit specialised batch kernels with one or two rows of loads in
+    flight per warp leave the same state bit for bit, for tile heights down to
+    a single row."""
+    sizes = [(256, 40), (128, 33), (64, 7)]
+    out = {}
+    for pf in (1, 2):
+        grids = []
+        for nx, ny in sizes:
+            g = lbm.Grid(nx, ny, 0.7, 0.2, kind.replace("-sr", ""))
+            if kind.endswith("-sr"):
+                g.set_rounding("stochastic")
+            g.init(*workloads.fourier_modes(nx, ny, amp=1e-3, seed=nx + ny))
+            grids.append(g)
+        b = lbm.Batch(grids)
+        b.set_config(rows, 0)
+        b.set_prefetch(pf)
+        cfg = b.get_config()
+        assert cfg["specialised"] and cfg["prefetch"] == pf
+        b.step(37)
+        assert b.sync() == 0
+        out[pf] = [g.get_state()[0] for g in grids]
+        b.close()
+        for g in grids:
+            g.close()
+    for a, c in zip(out[1], out[2]):
+        assert np.array_equal(a, c)
+
+
+def test_batch_prefetch_argument_checks(lbm):
+    g = lbm.Grid(64, 8, 0.8, 0.2, "f16d")
+    b = lbm.Batch([g])
+    for bad in (0, 3, -1):
+        with pytest.raises(lbm.LbmError):
+            b.set_prefetch(bad)
+    b.close()
+    g.close()
+
+
+def test_kind_groups_equal_solo_runs(lbm):
+    """A batch whose FP32 and FP16-D grids each fill the GPU runs them in
+    separate specialised launches (with the small odd-width grid in a launch of
+    the general kernel): 3 kind groups, and every grid reaches bitwise the
+    state it reaches alone, including per-grid step limits."""
+    specs = [(2048, 2048, 0.8, 0.2, "f32"), (2048, 2048, 0.6, 0.1, "f16d"),
+             (37, 29, 0.7, 0.3, "f32"), (256, 64, 0.9, 0.25, "bf16d")]
+    limits = [12, 9, 12, 5]
+    solo = []
+    for (nx, ny, tau, c2, st), lim in zip(specs, limits):
+        with lbm.Grid(nx, ny, tau, c2, st) as g:
+            g.init(*workloads.fourier_modes(nx, ny, amp=1e-3, seed=nx + ny))
+            g.step(lim)
+            solo.append(g.get_state()[0])
+    grids = []
+    for nx, ny, tau, c2, st in specs:
+        g = lbm.Grid(nx, ny, tau, c2, st)
+        g.init(*workloads.fourier_modes(nx, ny, amp=1e-3, seed=nx + ny))
+        grids.append(g)
+    b = lbm.Batch(grids)
+    assert b.get_config()["groups"] == 3
+    b.step(7, limits)
+    b.step(5, [max(0, x - 7) for x in limits])
+    assert b.sync() == 0
+    for g, s, lim in zip(grids, solo, limits):
+        assert g.t == lim
+        assert np.array_equal(g.get_state()[0], s)
+    b.close()
+    for g in grids:
+        g.close()

@@ -60,7 +60,9 @@ def test_sweep_2048_full_run_matches_linear_theory(lbm):
         # here, so rounding alone moves the mass by at most 2^-25 * 3A per
         # step and unit mass (a lost term of the update moves it by O(A)).
         assert dm < steps * 2.0 ** -25 * 3 * r.amp
-        assert e_uy < 1e-3
+        # u = j / rho in a wave with drho ~ A mixes third-order terms of
+        # relative size O(A^2) into the shear mode.
+        assert e_uy < 1e-3 + 3 * r.amp ** 2
         if r.amp <= 3e-3:
             assert e_rho < 1e-3
 
