@@ -249,8 +249,8 @@ def run_native(args):
     stages, pipelined = grids[0].get_pipeline()
     sites = sum(r.nx * r.ny for r in runs)
     batch = lbm.Batch(grids) if args.path == "batch" else None
-    if batch is not None and args.batch_prefetch:
-        batch.set_prefetch(args.batch_prefetch)
+    if batch is not None and args.walk16:
+        batch.set_walk16(args.walk16)
 
     # Launch plan: on the batch path every launch is one persistent
     # cooperative kernel running `spl` steps of all grids (grid barrier between
@@ -494,8 +494,8 @@ def run_batch_workload(args):
     b = lbm.Batch(grids)
     if args.batch_rows:
         b.set_config(args.batch_rows, 0)
-    if args.batch_prefetch:
-        b.set_prefetch(args.batch_prefetch)
+    if args.walk16:
+        b.set_walk16(args.walk16)
     if args.tune:
         b.tune()
     bcfg = b.get_config()
@@ -584,8 +584,8 @@ def main():
                     help="rounding of 16-bit stores")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-rows", type=int, default=0)
-    ap.add_argument("--batch-prefetch", type=int, default=0, choices=[0, 1, 2],
-                    help="rows of loads in flight per warp in 16-bit batch kernels (0: default)")
+    ap.add_argument("--walk16", default=None, choices=["auto", "v8", "v4", "v4pf2"],
+                    help="walk of 16-bit grids in batch kernels (default: the library's)")
     ap.add_argument("--steps-per-launch", type=int, default=20,
                     help="steps of all grids per persistent launch on the batch path")
     ap.add_argument("--tune", action="store_true")

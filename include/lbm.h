@@ -271,22 +271,32 @@ int lbm_batch_tune(lbm_batch_t b);
  * rounding and a vec of 4) rather than the general kernel. */
 int lbm_batch_get_config(lbm_batch_t b, int *rows, int *blocks_per_sm, int *specialised);
 
-/* Number of persistent launches one lbm_batch_step makes (kind groups).  A
- * storage kind whose grids (nx a multiple of 4) fill at least half the GPU's
- * resident warps runs in a launch of its own specialised kernel; the other
- * grids share one launch of the general kernel.  The groups hold disjoint
+/* Number of persistent launches one lbm_batch_step makes (kind groups).  The
+ * grids of one walk (storage kind, sites per lane, rounding; nx a multiple of
+ * 4) that together move at least 64 MiB per step run in a launch of their own
+ * specialised kernel; the other grids share one launch of the general kernel.  The groups hold disjoint
  * grids and run one after the other on the batch's stream, each advancing
  * its grids by all the steps of the call. */
 int lbm_batch_get_groups(lbm_batch_t b, int *groups);
 
-/* Rows of loads each warp keeps in flight ahead of the row it pulls, for a
- * batch whose grids all use 16-bit storage with nx a multiple of 4 (the
- * specialised kernels): 1 (default; 128 registers, 16 warps per SM) or 2
- * (one more row of raw words in registers; 12 warps per SM).  Results are
- * bitwise the same either way.  Other batches ignore it.  lbm_batch_tune
- * tries both.  Waits for the batch's stream; LBM_EINVAL for other values. */
-int lbm_batch_set_prefetch(lbm_batch_t b, int rows_ahead);
-int lbm_batch_get_prefetch(lbm_batch_t b, int *rows_ahead);
+/* The walk of 16-bit grids in a batch (results are bitwise the same for all):
+ *   LBM_WALK16_AUTO    LBM_WALK16_V8 for grids with round-to-nearest stores,
+ *                      LBM_WALK16_V4 for stochastic rounding (the faster of
+ *                      the two for each on GB300); the default
+ *   LBM_WALK16_V8      8 sites per lane, 128-bit loads, when nx is a multiple
+ *                      of 8 (else as LBM_WALK16_V4)
+ *   LBM_WALK16_V4      4 sites per lane, 64-bit loads, one row of loads in
+ *                      flight ahead of the row being pulled
+ *   LBM_WALK16_V4_PF2  as LBM_WALK16_V4 with two rows in flight (more
+ *                      registers, 12 warps per SM instead of 16)
+ * lbm_batch_tune tries them all.  Waits for the batch's stream; LBM_EINVAL
+ * for other values. */
+#define LBM_WALK16_AUTO 0
+#define LBM_WALK16_V8 1
+#define LBM_WALK16_V4 2
+#define LBM_WALK16_V4_PF2 3
+int lbm_batch_set_walk16(lbm_batch_t b, int walk);
+int lbm_batch_get_walk16(lbm_batch_t b, int *walk);
 
 /* Barrier wait limit of the batch kernel in microseconds (default 1e6). */
 int lbm_batch_set_timeout_us(lbm_batch_t b, long long us);

@@ -26,8 +26,7 @@ struct GridDesc {
     void *buf[2];
     size_t P;
     int nx, ny;
-    int kind;  // storage * 16 + vec, + 8 for stochastic rounding (16-bit vec 4
-               // uses the prefetching walk)
+    int kind;  // kind_code(storage, vec, stochastic rounding)
     int pad;
     Coef c;
 };
@@ -35,6 +34,11 @@ struct GridDesc {
 struct Tile {
     int grid, x0, y0, y1, dir;
 };
+
+// A grid's walk in the batch kernels: storage kind, sites per lane (1, 4 or
+// 8) and stochastic rounding.
+constexpr int kind_code(int storage, int vec, int sr) { return storage * 32 + vec + 16 * sr; }
+constexpr int kKindCodes = 3 * 32;
 
 constexpr int kBatchWarps = 4;  // warps per block of the persistent kernel
 
@@ -139,34 +143,46 @@ __global__ void __launch_bounds__(32 * kBatchWarps, 3)
             const int par = (parity0[t.grid] + (int)(k & 1)) & 1;
             const uint32_t step = t0[t.grid] + (uint32_t)k;
             switch (g.kind) {
-                case ST_F32 * 16 + 4:
+                case kind_code(ST_F32, 4, 0):
                     do_tile<ST_F32, 4>(g, par, t, step);
                     break;
-                case ST_F16 * 16 + 4:
-                    do_tile<ST_F16, 4, true>(g, par, t, step);
-                    break;
-                case ST_BF16 * 16 + 4:
-                    do_tile<ST_BF16, 4, true>(g, par, t, step);
-                    break;
-                case ST_F32 * 16 + 1:
+                case kind_code(ST_F32, 1, 0):
                     do_tile<ST_F32, 1>(g, par, t, step);
                     break;
-                case ST_F16 * 16 + 1:
+                case kind_code(ST_F16, 8, 0):
+                    do_tile<ST_F16, 8>(g, par, t, step);
+                    break;
+                case kind_code(ST_F16, 4, 0):
+                    do_tile<ST_F16, 4, true>(g, par, t, step);
+                    break;
+                case kind_code(ST_F16, 1, 0):
                     do_tile<ST_F16, 1>(g, par, t, step);
                     break;
-                case ST_BF16 * 16 + 1:
+                case kind_code(ST_BF16, 8, 0):
+                    do_tile<ST_BF16, 8>(g, par, t, step);
+                    break;
+                case kind_code(ST_BF16, 4, 0):
+                    do_tile<ST_BF16, 4, true>(g, par, t, step);
+                    break;
+                case kind_code(ST_BF16, 1, 0):
                     do_tile<ST_BF16, 1>(g, par, t, step);
                     break;
-                case ST_F16 * 16 + 8 + 4:
+                case kind_code(ST_F16, 8, 1):
+                    do_tile<ST_F16, 8, false, 1>(g, par, t, step);
+                    break;
+                case kind_code(ST_F16, 4, 1):
                     do_tile<ST_F16, 4, true, 1>(g, par, t, step);
                     break;
-                case ST_F16 * 16 + 8 + 1:
+                case kind_code(ST_F16, 1, 1):
                     do_tile<ST_F16, 1, false, 1>(g, par, t, step);
                     break;
-                case ST_BF16 * 16 + 8 + 4:
+                case kind_code(ST_BF16, 8, 1):
+                    do_tile<ST_BF16, 8, false, 1>(g, par, t, step);
+                    break;
+                case kind_code(ST_BF16, 4, 1):
                     do_tile<ST_BF16, 4, true, 1>(g, par, t, step);
                     break;
-                case ST_BF16 * 16 + 8 + 1:
+                case kind_code(ST_BF16, 1, 1):
                     do_tile<ST_BF16, 1, false, 1>(g, par, t, step);
                     break;
                 default:
@@ -216,23 +232,31 @@ using BatchKernel = void (*)(const GridDesc *, const Tile *, int, const long lon
                              const uint32_t *, long long, unsigned *, int *, unsigned long long);
 
 // The kernel for a set of kinds: a specialised one when every grid has the
-// same kind, else the general k_batch.  `prefetch` (1 or 2) picks the rows of
-// loads in flight of the 16-bit specialised kernels.
-BatchKernel kernel_for(const std::vector<int> &kinds, int prefetch) {
+// same kind, else the general k_batch.  `walk16` picks the prefetch depth of
+// the 16-bit vec 4 walks (LBM_WALK16_V4: one row, LBM_WALK16_V4_PF2: two).
+BatchKernel kernel_for(const std::vector<int> &kinds, int walk16) {
     bool same = true;
     for (int k : kinds) same = same && k == kinds[0];
     if (!kinds.empty() && same) {
-        const bool two = prefetch == 2;
+        const bool two = walk16 == LBM_WALK16_V4_PF2;
         switch (kinds[0]) {
-            case ST_F32 * 16 + 4:
+            case kind_code(ST_F32, 4, 0):
                 return k_batch_one<ST_F32, 4, 0, 0>;
-            case ST_F16 * 16 + 4:
+            case kind_code(ST_F16, 8, 0):
+                return k_batch_one<ST_F16, 8, 0, 0>;
+            case kind_code(ST_BF16, 8, 0):
+                return k_batch_one<ST_BF16, 8, 0, 0>;
+            case kind_code(ST_F16, 8, 1):
+                return k_batch_one<ST_F16, 8, 0, 1>;
+            case kind_code(ST_BF16, 8, 1):
+                return k_batch_one<ST_BF16, 8, 0, 1>;
+            case kind_code(ST_F16, 4, 0):
                 return two ? k_batch_one<ST_F16, 4, 2, 0> : k_batch_one<ST_F16, 4, 1, 0>;
-            case ST_BF16 * 16 + 4:
+            case kind_code(ST_BF16, 4, 0):
                 return two ? k_batch_one<ST_BF16, 4, 2, 0> : k_batch_one<ST_BF16, 4, 1, 0>;
-            case ST_F16 * 16 + 8 + 4:
+            case kind_code(ST_F16, 4, 1):
                 return two ? k_batch_one<ST_F16, 4, 2, 1> : k_batch_one<ST_F16, 4, 1, 1>;
-            case ST_BF16 * 16 + 8 + 4:
+            case kind_code(ST_BF16, 4, 1):
                 return two ? k_batch_one<ST_BF16, 4, 2, 1> : k_batch_one<ST_BF16, 4, 1, 1>;
             default:
                 break;
@@ -258,7 +282,7 @@ struct lbm_batch {
         int max_blocks_per_sm = 1;
     };
     std::vector<Group> groups;
-    int prefetch = 1;              // rows of loads in flight (16-bit specialised kernels)
+    int walk16 = LBM_WALK16_AUTO;  // walk of 16-bit grids (lbm_batch_set_walk16)
     int sms = 1;
     unsigned long long timeout_ns = 1000000000ULL;
     // device
@@ -304,10 +328,18 @@ static void drop_graph(lbm_batch *b) {
     b->graph_n = -1;
 }
 
-// The batch kernel carries two walks per storage: 4 sites per lane (128-bit
-// loads for FP32; 64-bit loads with one row prefetched for 16-bit), used when
-// nx is a multiple of 4, and 1 site per lane for any other nx.
-static int batch_vec(const lbm_grid *g) { return g->nx % 4 == 0 ? 4 : 1; }
+// Sites per lane of a grid's walk.  FP32: 4 (128-bit loads) when nx is a
+// multiple of 4.  16-bit: 8 (128-bit loads) when nx is a multiple of 8 and
+// the walk is LBM_WALK16_V8, or LBM_WALK16_AUTO with round-to-nearest stores;
+// else 4 (64-bit loads, rows prefetched) when nx is a multiple of 4.  Any
+// other nx: 1.  (Measured on GB300: with nearest rounding 8 sites per lane
+// run 13 % faster than 4; with stochastic rounding the 8-site kernel spills
+// and runs 25 % slower.)
+static int batch_vec(const lbm_batch *b, const lbm_grid *g) {
+    const bool eight = b->walk16 == LBM_WALK16_V8 || (b->walk16 == LBM_WALK16_AUTO && !g->rounding);
+    if (g->storage != ST_F32 && eight && g->nx % 8 == 0) return 8;
+    return g->nx % 4 == 0 ? 4 : 1;
+}
 
 // (Re)builds the device grid table and the tile work-list.
 static int build_worklist(lbm_batch *b) {
@@ -321,8 +353,8 @@ static int build_worklist(lbm_batch *b) {
         d.P = g->P;
         d.nx = g->nx;
         d.ny = g->ny;
-        int v = batch_vec(g);
-        d.kind = g->storage * 16 + v + (g->rounding ? 8 : 0);
+        int v = batch_vec(b, g);
+        d.kind = kind_code(g->storage, v, g->rounding ? 1 : 0);
         d.pad = 0;
         d.c = g->coef;
         int w = 32 * v;
@@ -334,24 +366,25 @@ static int build_worklist(lbm_batch *b) {
                                      (seg & 1) ? -1 : 1});
     }
     // Kind groups.  A kind with a specialised kernel runs in its own launch
-    // when its tiles fill at least half the resident warps of that kernel (the
-    // launch then stays bandwidth-bound); all other tiles share one launch of
-    // the general kernel, where small grids of any kind overlap.  A batch of
-    // one kind is one group.
-    std::vector<int> count(256, 0);
-    for (const Tile &t : tiles) count[gd[t.grid].kind & 255]++;
+    // when its grids move at least kOwnLaunchBytes per step (about 10 us of
+    // HBM time, so the launch's fixed costs and its barrier stay small); all
+    // other tiles share one launch of the general kernel, where small grids of
+    // any kind overlap.  A batch of one kind is one group.
+    constexpr double kOwnLaunchBytes = 64.0 * 1024 * 1024;
+    std::vector<double> bytes(kKindCodes, 0.0);
+    std::vector<int> count(kKindCodes, 0);
+    for (size_t k = 0; k < b->grids.size(); ++k) {
+        const lbm_grid *g = b->grids[k];
+        bytes[gd[k].kind] += (double)g->nx * g->ny * (g->storage == ST_F32 ? 72.0 : 36.0);
+    }
+    for (const Tile &t : tiles) count[gd[t.grid].kind]++;
     int kinds_present = 0;
-    for (int kd = 0; kd < 256; ++kd) kinds_present += count[kd] > 0;
+    for (int kd = 0; kd < kKindCodes; ++kd) kinds_present += count[kd] > 0;
     std::vector<int> own, rest;
-    for (int kd = 0; kd < 256; ++kd) {
+    for (int kd = 0; kd < kKindCodes; ++kd) {
         if (!count[kd]) continue;
-        BatchKernel kk = kernel_for({kd}, b->prefetch);
-        int bps = 0;
-        if (kk != (BatchKernel)k_batch)
-            BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void *)kk,
-                                                              32 * kBatchWarps, 0));
-        if (kk != (BatchKernel)k_batch &&
-            (kinds_present == 1 || 2LL * count[kd] >= (long long)bps * b->sms * kBatchWarps))
+        BatchKernel kk = kernel_for({kd}, b->walk16);
+        if (kk != (BatchKernel)k_batch && (kinds_present == 1 || bytes[kd] >= kOwnLaunchBytes))
             own.push_back(kd);
         else
             rest.push_back(kd);
@@ -363,12 +396,12 @@ static int build_worklist(lbm_batch *b) {
         lbm_batch::Group gr;
         gr.begin = (int)ordered.size();
         for (const Tile &t : tiles) {
-            int kd = gd[t.grid].kind & 255;
+            int kd = gd[t.grid].kind;
             if (std::find(kinds_in.begin(), kinds_in.end(), kd) != kinds_in.end())
                 ordered.push_back(t);
         }
         gr.count = (int)ordered.size() - gr.begin;
-        gr.kernel = kernel_for(kinds_in, b->prefetch);
+        gr.kernel = kernel_for(kinds_in, b->walk16);
         BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gr.max_blocks_per_sm,
                                                           (const void *)gr.kernel,
                                                           32 * kBatchWarps, 0));
@@ -589,24 +622,24 @@ extern "C" int lbm_batch_set_config(lbm_batch_t b, int rows, int blocks_per_sm) 
     return LBM_OK;
 }
 
-extern "C" int lbm_batch_set_prefetch(lbm_batch_t b, int rows_ahead) {
-    if (!b || rows_ahead < 1 || rows_ahead > 2)
-        return bfail(LBM_EINVAL, "lbm_batch_set_prefetch: rows_ahead must be 1 or 2");
+extern "C" int lbm_batch_set_walk16(lbm_batch_t b, int walk) {
+    if (!b || walk < LBM_WALK16_AUTO || walk > LBM_WALK16_V4_PF2)
+        return bfail(LBM_EINVAL, "lbm_batch_set_walk16: unknown walk");
     BCK(cudaStreamSynchronize(b->stream));
-    if (rows_ahead == b->prefetch) return LBM_OK;
-    b->prefetch = rows_ahead;
+    if (walk == b->walk16) return LBM_OK;
+    b->walk16 = walk;
     return build_worklist(b);
+}
+
+extern "C" int lbm_batch_get_walk16(lbm_batch_t b, int *walk) {
+    if (!b || !walk) return bfail(LBM_EINVAL, "lbm_batch_get_walk16: bad argument");
+    *walk = b->walk16;
+    return LBM_OK;
 }
 
 extern "C" int lbm_batch_get_groups(lbm_batch_t b, int *groups) {
     if (!b || !groups) return bfail(LBM_EINVAL, "lbm_batch_get_groups: bad argument");
     *groups = (int)b->groups.size();
-    return LBM_OK;
-}
-
-extern "C" int lbm_batch_get_prefetch(lbm_batch_t b, int *rows_ahead) {
-    if (!b || !rows_ahead) return bfail(LBM_EINVAL, "lbm_batch_get_prefetch: bad argument");
-    *rows_ahead = b->prefetch;
     return LBM_OK;
 }
 
@@ -618,8 +651,8 @@ extern "C" int lbm_batch_set_timeout_us(lbm_batch_t b, long long us) {
 }
 
 // Times one-step dry runs (the state is not advanced: every grid writes its
-// other buffer) for several tile heights, and for the 16-bit specialised
-// kernels both prefetch depths, each at its full occupancy; keeps the fastest.
+// other buffer) for several tile heights and, when the batch holds 16-bit
+// grids, the 16-bit walks, each at its full occupancy; keeps the fastest.
 // A one-step launch does the same per-step work as a step inside a longer
 // launch (the barriers between steps cost microseconds per millisecond step).
 extern "C" int lbm_batch_tune(lbm_batch_t b) {
@@ -627,17 +660,17 @@ extern "C" int lbm_batch_tune(lbm_batch_t b) {
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0));
     BCK(cudaEventCreate(&e1));
-    int best_rows = b->rows, best_pf = b->prefetch;
+    int best_rows = b->rows, best_walk = b->walk16;
     float best = 1e30f;
     const int rowss[] = {8, 12, 16, 24, 32};
-    std::vector<BatchKernel> k1;
-    for (int pf = 1; pf <= 2; ++pf) {
-        int rc = lbm_batch_set_prefetch(b, pf);
+    std::vector<std::vector<BatchKernel>> seen;
+    for (int walk = LBM_WALK16_AUTO; walk <= LBM_WALK16_V4_PF2; ++walk) {
+        int rc = lbm_batch_set_walk16(b, walk);
         if (rc != LBM_OK) return rc;
         std::vector<BatchKernel> ks;
         for (const auto &gr : b->groups) ks.push_back(gr.kernel);
-        if (pf == 1) k1 = ks;
-        if (pf == 2 && ks == k1) break;  // the depth applies to none of these kernels
+        if (std::find(seen.begin(), seen.end(), ks) != seen.end()) continue;  // same kernels
+        seen.push_back(ks);
         for (int r : rowss) {
             rc = lbm_batch_set_config(b, r, 0);
             if (rc != LBM_OK) return rc;
@@ -653,13 +686,13 @@ extern "C" int lbm_batch_tune(lbm_batch_t b) {
             if (ms < best) {
                 best = ms;
                 best_rows = r;
-                best_pf = pf;
+                best_walk = walk;
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    int rc = lbm_batch_set_prefetch(b, best_pf);
+    int rc = lbm_batch_set_walk16(b, best_walk);
     if (rc != LBM_OK) return rc;
     return lbm_batch_set_config(b, best_rows, 0);
 }

@@ -232,13 +232,11 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
 }
 template <int S>
 __device__ __forceinline__ uint32_t pack1(float v) {
-    if constexpr (S == ST_F32) {
+    // The paired conversion (same rounding) with the value in the low half.
+    if constexpr (S == ST_F32)
         return __float_as_uint(v);
-    } else if constexpr (S == ST_F16) {
-        return (uint32_t)__half_as_ushort(__float2half_rn(v));
-    } else {
-        return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v));
-    }
+    else
+        return pack2<S>(v, 0.0f) & 0xffffu;
 }
 
 // ---------------------------------------------------------------------------

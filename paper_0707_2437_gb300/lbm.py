@@ -21,7 +21,7 @@ STORAGE = {"f32": 0, "f16d": 1, "bf16d": 2}
 BYTES_PER_LU = {"f32": 72, "f16d": 36, "bf16d": 36}  # algorithmic bytes per lattice update
 FIELD = {"rho": 0, "ux": 1, "uy": 2}
 LBM_OK, LBM_WUNSTABLE = 0, 1
-LBM_ETIMEOUT = -5
+LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT = -1, -2, -3, -4, -5
 
 _lib = None
 _lock = threading.Lock()
@@ -81,8 +81,8 @@ def load() -> ctypes.CDLL:
             "lbm_batch_sync": ([vp], i),
             "lbm_batch_set_config": ([vp, i, i], i),
             "lbm_batch_tune": ([vp], i),
-            "lbm_batch_set_prefetch": ([vp, i], i),
-            "lbm_batch_get_prefetch": ([vp, ctypes.POINTER(i)], i),
+            "lbm_batch_set_walk16": ([vp, i], i),
+            "lbm_batch_get_walk16": ([vp, ctypes.POINTER(i)], i),
             "lbm_batch_get_groups": ([vp, ctypes.POINTER(i)], i),
             "lbm_batch_get_config": ([vp, ctypes.POINTER(i), ctypes.POINTER(i),
                                       ctypes.POINTER(i)], i),
@@ -309,6 +309,10 @@ class Grid:
         return ms.value, n.value
 
 
+WALK16 = {"auto": 0, "v8": 1, "v4": 2, "v4pf2": 3}
+WALK16_NAMES = {v: k for k, v in WALK16.items()}
+
+
 class Batch:
     """Many grids advanced together by one persistent launch (lbm_batch_*)."""
 
@@ -353,16 +357,18 @@ class Batch:
         r, b, sp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(self.lib.lbm_batch_get_config(self.b, ctypes.byref(r), ctypes.byref(b),
                                              ctypes.byref(sp)), "lbm_batch_get_config")
-        pf = ctypes.c_int()
-        _check(self.lib.lbm_batch_get_prefetch(self.b, ctypes.byref(pf)), "lbm_batch_get_prefetch")
+        wk = ctypes.c_int()
+        _check(self.lib.lbm_batch_get_walk16(self.b, ctypes.byref(wk)), "lbm_batch_get_walk16")
         ng = ctypes.c_int()
         _check(self.lib.lbm_batch_get_groups(self.b, ctypes.byref(ng)), "lbm_batch_get_groups")
         return {"rows": r.value, "blocks_per_sm": b.value, "specialised": bool(sp.value),
-                "prefetch": pf.value, "groups": ng.value}
+                "walk16": WALK16_NAMES[wk.value], "groups": ng.value}
 
-    def set_prefetch(self, rows_ahead: int):
-        """Rows of loads in flight per warp (1 or 2) for 16-bit batches."""
-        _check(self.lib.lbm_batch_set_prefetch(self.b, int(rows_ahead)), "lbm_batch_set_prefetch")
+    def set_walk16(self, walk: str):
+        """Walk of the batch's 16-bit grids: 'auto' (the default: 'v8' with
+        nearest rounding, 'v4' with stochastic rounding), 'v8' (8 sites per
+        lane), 'v4' (4 per lane, one row prefetched) or 'v4pf2' (two rows)."""
+        _check(self.lib.lbm_batch_set_walk16(self.b, WALK16[walk]), "lbm_batch_set_walk16")
 
     def set_timeout_us(self, us: int):
         _check(self.lib.lbm_batch_set_timeout_us(self.b, int(us)), "lbm_batch_set_timeout_us")

@@ -53,13 +53,14 @@ def test_fifo_baseline_runs(lbm):
 
 @pytest.mark.parametrize("kind", ["f16d", "bf16d", "f16d-sr", "bf16d-sr"])
 @pytest.mark.parametrize("rows", [1, 5, 16])
-def test_batch_prefetch_depths_bitwise_equal(lbm, kind, rows):
-    """The 16-bit specialised batch kernels with one or two rows of loads in
-    flight per warp leave the same state bit for bit, for tile heights down to
-    a single row."""
-    sizes = [(256, 40), (128, 33), (64, 7)]
+def test_batch_walk16_variants_bitwise_equal(lbm, kind, rows):
+    """The walks of 16-bit grids (8 sites per lane; 4 per lane with one or two
+    rows of loads in flight; the automatic choice) leave the same state bit
+    for bit, for tile heights down to a single row; a grid with nx a multiple
+    of 4 but not 8 takes the 4-site walk within the 8-site setting."""
+    sizes = [(256, 40), (128, 33), (64, 7), (36, 12)]
     out = {}
-    for pf in (1, 2):
+    for walk in ("auto", "v8", "v4", "v4pf2"):
         grids = []
         for nx, ny in sizes:
             g = lbm.Grid(nx, ny, 0.7, 0.2, kind.replace("-sr", ""))
@@ -69,25 +70,44 @@ def test_batch_prefetch_depths_bitwise_equal(lbm, kind, rows):
             grids.append(g)
         b = lbm.Batch(grids)
         b.set_config(rows, 0)
-        b.set_prefetch(pf)
-        cfg = b.get_config()
-        assert cfg["specialised"] and cfg["prefetch"] == pf
+        b.set_walk16(walk)
+        assert b.get_config()["walk16"] == walk
         b.step(37)
         assert b.sync() == 0
-        out[pf] = [g.get_state()[0] for g in grids]
+        out[walk] = [g.get_state()[0] for g in grids]
         b.close()
         for g in grids:
             g.close()
-    for a, c in zip(out[1], out[2]):
-        assert np.array_equal(a, c)
+    for w in ("auto", "v4", "v4pf2"):
+        for a, c in zip(out["v8"], out[w]):
+            assert np.array_equal(a, c)
 
 
-def test_batch_prefetch_argument_checks(lbm):
+@pytest.mark.parametrize("kind", ["f16d", "bf16d-sr"])
+def test_batch_walk16_single_kind_specialised(lbm, kind):
+    """A batch of one 16-bit kind runs one specialised launch in every walk."""
+    for walk in ("auto", "v8", "v4", "v4pf2"):
+        g = lbm.Grid(512, 64, 0.8, 0.2, kind.replace("-sr", ""))
+        if kind.endswith("-sr"):
+            g.set_rounding("stochastic")
+        g.init(*workloads.fourier_modes(512, 64, amp=1e-3, seed=2))
+        b = lbm.Batch([g])
+        b.set_walk16(walk)
+        cfg = b.get_config()
+        assert cfg["specialised"] and cfg["groups"] == 1
+        b.step(3)
+        assert b.sync() == 0
+        b.close()
+        g.close()
+
+
+def test_batch_walk16_argument_checks(lbm):
     g = lbm.Grid(64, 8, 0.8, 0.2, "f16d")
     b = lbm.Batch([g])
-    for bad in (0, 3, -1):
-        with pytest.raises(lbm.LbmError):
-            b.set_prefetch(bad)
+    for bad in (4, -1):
+        assert b.lib.lbm_batch_set_walk16(b.b, bad) == lbm.LBM_EINVAL
+    with pytest.raises(KeyError):
+        b.set_walk16("v16")
     b.close()
     g.close()
 
