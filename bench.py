@@ -34,7 +34,7 @@ from paper_0707_2437_gb300 import workloads  # noqa: E402
 BYTES_PER_LU = {"f32": 72, "f16d": 36, "bf16d": 36}
 METRIC = "MLUPS (million lattice updates per second), D2Q9 variable-speed-of-sound step"
 WORKLOAD = "2048x2048 periodic D2Q9, 9 runs c2=0.05..0.45, tau~U[0.55,1.5], acoustic+shear wave"
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "step_f32_2048_traffic.json")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "batch_sweep2048_traffic.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_0707_2437_gb300", "csrc", f)
                   for f in ("lbm_device.cuh", "lbm_kernels.cu", "lbm_batch.cu")]
 
@@ -325,14 +325,14 @@ def run_native(args):
     alg_bytes = per_step_bytes * (spl if batch is not None else 1)
     peak, peak_kind = measured_peak()
     traffic = None
-    if os.path.exists(PROFILE_TRAFFIC):
+    if os.path.exists(PROFILE_TRAFFIC) and batch is not None:
         tj = json.load(open(PROFILE_TRAFFIC))
-        if (tj.get("source_hash") == kernel_source_hash() and tj.get("storage") == storage
-                and tj.get("path") == args.path and batch is not None):
+        entry = tj.get("storage", {}).get(storage)
+        if (entry and tj.get("source_hash") == kernel_source_hash()
+                and tj.get("path") == args.path and args.rounding == "nearest"):
             # Captured on one-step launches of the same kernel; a launch of
             # `spl` steps moves `spl` times the bytes of one step.
-            per = tj.get("dram_bytes_per_step")
-            traffic = per * spl if per is not None else None
+            traffic = entry["dram_bytes_per_step"] * spl
 
     # The same batch with one step per launch, for the launch overhead.
     one_step = None

@@ -204,6 +204,10 @@ __global__ void __launch_bounds__(32 * kBatchWarps, PD == 2 ? 3 : 4)
                 const long long *__restrict__ limit, const int *__restrict__ parity0,
                 const uint32_t *__restrict__ t0, long long nsteps, unsigned *bar, int *status,
                 unsigned long long timeout_ns) {
+    // Row buffers of the 8-site 16-bit walks: per warp a landing slot and a
+    // stash of 9 x 32 16-byte vectors each (36 KiB per block).
+    __shared__ uint4 rowbuf[(S != ST_F32 && V == 8) ? kBatchWarps : 1][2 * 9 * 32];
+    (void)rowbuf;
     for (long long k = 0; k < nsteps; ++k) {
         reset_counter(bar, k);
         unsigned *ctr = step_counter(bar, k);
@@ -217,7 +221,9 @@ __global__ void __launch_bounds__(32 * kBatchWarps, PD == 2 ? 3 : 4)
             const Coef c = g.c;
             Walker<S, V, LD_CG, RND> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P, t.x0);
             if constexpr (RND) w.rstep = t0[t.grid] + (uint32_t)k;
-            if constexpr (PD == 2)
+            if constexpr (S != ST_F32 && V == 8)
+                w.run_async(t.y0, t.y1, t.dir, c, &rowbuf[threadIdx.x >> 5][0]);
+            else if constexpr (PD == 2)
                 w.run_prefetch2(t.y0, t.y1, t.dir, c);
             else if constexpr (PD == 1)
                 w.run_prefetch(t.y0, t.y1, t.dir, c);

@@ -741,6 +741,106 @@ struct Walker {
         }
     }
 
+    // Asynchronous copy (cp.async, through L2 only) of this lane's nine
+    // 16-byte vectors of pulled row q0 into `slot` ([9][32] vectors), as one
+    // commit group.  Same sources as load_row.
+    __device__ __forceinline__ void issue_row_async(int qm, int q0, int qp, uint4 *slot) const {
+        const int xl = act ? xs : x0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int sr = (EYi(i) > 0) ? qm : ((EYi(i) < 0) ? qp : q0);
+            const size_t idx = (size_t)i * P + (size_t)sr * nx + xl;
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(slot + i * 32 + lane);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(fin + idx)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    // The helper lane's value of pulled row q0 (see load_row).
+    __device__ __forceinline__ uint32_t load_helper(int qm, int q0, int qp) const {
+        const int gsr = (gey > 0) ? qm : ((gey < 0) ? qp : q0);
+        const size_t gidx = (size_t)gdir * P + (size_t)gsr * nx + gcol;
+        return load_elem<S, LD>(fin + gidx);
+    }
+
+    // As run(), with the rows moved through shared memory so that one row of
+    // loads is in flight while the warp computes, without holding it in
+    // registers (8-site 16-bit lanes, 128-bit vectors, NW == 4).  `buf` is the
+    // warp's [2][9][32] 16-byte vectors: a landing slot for the row being
+    // copied and a stash for the pulled row waiting to be collided.  Row k+1
+    // is copied while row k is finished and row k-1 collided; the copy into
+    // the landing slot is issued only after the words read from it have been
+    // used (the shuffles of finish_pull), so it cannot overwrite them first.
+    // A lane reads only what it copied or wrote.
+    __device__ __forceinline__ void run_async(int y0, int y1, int dir, const Coef &c,
+                                              uint4 *buf) const {
+        static_assert(NW == 4, "the row buffers hold four words per lane and direction");
+        uint4 *land = buf;
+        uint4 *stash = buf + 9 * 32;
+        int q0 = dir > 0 ? ((y0 == 0) ? ny - 1 : y0 - 1) : (y1 == ny ? 0 : y1);
+        int qm = (q0 == 0) ? ny - 1 : q0 - 1;
+        int qp = (q0 + 1 == ny) ? 0 : q0 + 1;
+
+        float d2[V], d1[V], d0[V];
+        float l1 = 0.f, r1 = 0.f, l0, r0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            d2[v] = 0.f;
+            d1[v] = 0.f;
+        }
+        const int n = y1 - y0;
+        const int K = n + 2;
+        issue_row_async(qm, q0, qp, land);
+        uint32_t gnext = load_helper(qm, q0, qp);
+        for (int k = 0; k < K; ++k) {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            uint32_t w[9][NW];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const uint4 u = land[i * 32 + lane];
+                w[i][0] = u.x;
+                w[i][1] = u.y;
+                w[i][2] = u.z;
+                w[i][3] = u.w;
+            }
+            const uint32_t g = gnext;
+            advance(qm, q0, qp, dir);
+            finish_pull(w, g, d0, l0, r0);
+            if (k + 1 < K) {
+                issue_row_async(qm, q0, qp, land);
+                gnext = load_helper(qm, q0, qp);
+            }
+            if (k >= 2) {
+                uint32_t wc[9][NW];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const uint4 u = stash[i * 32 + lane];
+                    wc[i][0] = u.x;
+                    wc[i][1] = u.y;
+                    wc[i][2] = u.z;
+                    wc[i][3] = u.w;
+                    stash[i * 32 + lane] = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+                }
+                const int r = dir > 0 ? y0 + (k - 2) : y1 - 1 - (k - 2);
+                if (dir > 0)
+                    collide_store(r, wc, d1, d2, d0, l1, r1, c);
+                else
+                    collide_store(r, wc, d1, d0, d2, l1, r1, c);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    stash[i * 32 + lane] = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                d2[v] = d1[v];
+                d1[v] = d0[v];
+            }
+            l1 = l0;
+            r1 = r0;
+        }
+    }
+
     // As run(), with the loads of the next pulled row issued before the
     // current row is finished and the row before it collided, so that every
     // warp keeps one row of loads in flight while it computes.  Needs a third
