@@ -106,10 +106,11 @@ int lbm_init(lbm_t h, const double *rho, const double *ux, const double *uy,
              int on_device);
 
 /* Queues n >= 0 time steps of Eq. 5 (stream, moments, central grad(rho),
- * collide with force) on the handle's stream.  From 64 steps on (while
- * persistent mode is on, the default) the steps run as one persistent launch:
+ * collide with force) on the handle's stream.  From 64 steps on, or from 8
+ * on grids of at least 2^20 sites (while persistent mode is on, the default,
+ * and without a c2 field or a drive), the steps run as one persistent launch:
  * the batched kernel (see lbm_batch_create) with this grid alone, warps taking
- * tiles dynamically, a bounded grid barrier between steps.  Shorter calls
+ * tiles dynamically, a bounded grid barrier between steps.  Other calls
  * launch the step kernel with the handle's tile configuration, replayed from
  * CUDA graphs from 8 steps on.  All forms give bitwise the same result.
  * Asynchronous: errors of the kernels surface at the next synchronising call
@@ -243,40 +244,46 @@ int lbm_kernel_ms(lbm_t h, double *ms, long long *launches);
 
 /* ---- Batches: many uneven grids advanced in one persistent launch ------- */
 
-/* Groups n >= 1 existing handles (any sizes, tau, c2 and storage; all on the
- * same device) into a batch stepped by one persistent cooperative kernel over
- * a tile work-list, with a grid-wide barrier between time steps.  The batch
- * refers to the handles; they must outlive it and must not be stepped
- * individually while it is being stepped.  The batch's work runs on the
- * stream of grids[0]. */
+/* Groups n >= 1 existing handles (any sizes, tau, c2, storage and rounding;
+ * all on the same device) into a batch stepped by persistent cooperative
+ * kernels over a tile work-list, with a grid-wide barrier between time steps
+ * (one launch per kind group, see lbm_batch_get_groups).  Every grid reaches
+ * bitwise the state it reaches when stepped alone.  The batch refers to the
+ * handles; they must outlive it and must not be stepped individually while
+ * it is being stepped.  The batch's work runs on the stream of grids[0].
+ * Grids with a c2 field or a drive are refused (LBM_EINVAL). */
 int lbm_batch_create(const lbm_t *grids, int n, lbm_batch_t *out);
 int lbm_batch_destroy(lbm_batch_t b);
 
 /* Advances grid g of the batch by min(n, limits[g]) steps (limits may be NULL:
- * n steps each), all in one launch replayed from a CUDA graph.  Asynchronous.
- * A barrier wait that exceeds its time limit makes the kernel stop and the
- * next synchronising batch call return LBM_ETIMEOUT. */
+ * n steps each), one persistent launch per kind group, replayed from a CUDA
+ * graph.  Asynchronous.  A barrier wait that exceeds its time limit makes the
+ * kernel stop and the next synchronising batch call return LBM_ETIMEOUT.
+ * LBM_EINVAL if a grid has gained a c2 field or a drive since the batch was
+ * created. */
 int lbm_batch_step(lbm_batch_t b, long long n, const long long *limits);
 
 /* Waits for the batch's stream and returns the kernel's status
  * (LBM_OK or LBM_ETIMEOUT). */
 int lbm_batch_sync(lbm_batch_t b);
 
-/* Tile height (rows per warp) and persistent-grid occupancy of the batch
- * kernel; the autotuner picks them with lbm_batch_tune. */
+/* Tile height (rows per warp) and persistent-grid occupancy (0: as many
+ * blocks per SM as fit) of the batch kernels; lbm_batch_tune picks the tile
+ * height and the 16-bit walk from timed dry steps (the state is unchanged). */
 int lbm_batch_set_config(lbm_batch_t b, int rows, int blocks_per_sm);
 int lbm_batch_tune(lbm_batch_t b);
-/* Current tile height, resident blocks per SM, and whether the batch runs a
- * kernel specialised for one storage kind (every grid the same storage,
- * rounding and a vec of 4) rather than the general kernel. */
+/* Current tile height, resident blocks per SM of the first kind group, and
+ * whether every kind group runs a specialised kernel rather than the general
+ * one. */
 int lbm_batch_get_config(lbm_batch_t b, int *rows, int *blocks_per_sm, int *specialised);
 
 /* Number of persistent launches one lbm_batch_step makes (kind groups).  The
  * grids of one walk (storage kind, sites per lane, rounding; nx a multiple of
- * 4) that together move at least 64 MiB per step run in a launch of their own
- * specialised kernel; the other grids share one launch of the general kernel.  The groups hold disjoint
- * grids and run one after the other on the batch's stream, each advancing
- * its grids by all the steps of the call. */
+ * 4) that together move at least 64 MiB per step run in a launch of their
+ * own specialised kernel; the other grids share one launch of the general
+ * kernel.  A batch of one walk is one group.  The groups hold disjoint grids
+ * and run one after the other on the batch's stream, each advancing its
+ * grids by all the steps of the call. */
 int lbm_batch_get_groups(lbm_batch_t b, int *groups);
 
 /* The walk of 16-bit grids in a batch (results are bitwise the same for all):

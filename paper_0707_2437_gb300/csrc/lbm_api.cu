@@ -270,6 +270,10 @@ static cudaError_t launch_one(lbm_grid *h, int from) {
 
 static const int kGraphPairs = 16;   // a graph holds 32 steps
 static const long long kPersistentMin = 64;  // persistent launch from this many steps
+// ... or from kPersistentMinLarge steps on grids of at least kLargeSites sites,
+// where a step is long enough that the launch's barrier costs little.
+static const long long kPersistentMinLarge = 8;
+static const long long kLargeSites = 1LL << 20;
 static const long long kGraphMin = 8; // use graphs from this many steps on
 
 static int build_graphs(lbm_grid *h) {
@@ -326,7 +330,9 @@ extern "C" int lbm_step(lbm_t h, long long n) {
         h->kernel_launches = n;
         return LBM_OK;
     }
-    if (h->persistent && !h->a15f && !h->drive && n >= kPersistentMin) {
+    const bool large = (long long)h->nx * h->ny >= kLargeSites;
+    if (h->persistent && !h->a15f && !h->drive &&
+        (n >= kPersistentMin || (large && n >= kPersistentMinLarge))) {
         // One persistent launch of all n steps (dynamic tile scheduling,
         // barrier between steps), bitwise the same as n single launches.
         if (!h->self_batch) {

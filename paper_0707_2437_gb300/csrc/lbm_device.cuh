@@ -296,6 +296,18 @@ __device__ __forceinline__ uint32_t sr_bits(uint32_t d_lo, uint32_t d_hi) {
         return ((d_lo << 8) | 0x80u) | (((d_hi << 8) | 0x80u) << 16);
 }
 
+// The same random bits for a pair of sites from their dither words: byte k
+// of `wa` (low element) and of `wb` (high element), in one byte permute.
+template <int S, int K>
+__device__ __forceinline__ uint32_t sr_bits_pair(uint32_t wa, uint32_t wb) {
+    constexpr uint32_t sel = K | (K << 4) | ((4 + K) << 8) | ((4 + K) << 12);
+    const uint32_t x = __byte_perm(wa, wb, sel);  // bytes: a_K, a_K, b_K, b_K
+    if constexpr (S == ST_F16)
+        return ((x & 0x00ff00ffu) << 5) | 0x00100010u;
+    else
+        return (x & 0xff00ff00u) | 0x00800080u;
+}
+
 template <int S>
 __device__ __forceinline__ uint32_t sr_pack2(float lo, float hi, uint32_t rbits) {
     uint32_t out;
@@ -552,9 +564,18 @@ struct Walker {
             if constexpr (SP == 2) {
                 const Dither db = site_dither(site + 1u, rstep);
 #pragma unroll
-                for (int i = 0; i < 9; ++i)
-                    w[i][v0 >> 1] =
-                        sr_pack2<S>(h[0][i], h[1][i], sr_bits<S>(da.get(i), db.get(i)));
+                for (int i = 0; i < 9; ++i) {
+                    const uint32_t wa = i < 4 ? da.w0 : (i < 8 ? da.w1 : da.w2);
+                    const uint32_t wb = i < 4 ? db.w0 : (i < 8 ? db.w1 : db.w2);
+                    uint32_t rb;
+                    switch (i & 3) {
+                        case 0: rb = sr_bits_pair<S, 0>(wa, wb); break;
+                        case 1: rb = sr_bits_pair<S, 1>(wa, wb); break;
+                        case 2: rb = sr_bits_pair<S, 2>(wa, wb); break;
+                        default: rb = sr_bits_pair<S, 3>(wa, wb); break;
+                    }
+                    w[i][v0 >> 1] = sr_pack2<S>(h[0][i], h[1][i], rb);
+                }
             } else {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {

@@ -434,3 +434,20 @@ def test_autotune_keeps_results_and_cache(lbm, tmp_path):
         assert h.tune(cache) == cfg  # read back from the cache
     import json
     assert len(json.load(open(cache))) == 1
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16d"])
+def test_large_grid_short_calls_persistent_equal_single_launches(lbm, storage):
+    """On a grid of 2^20 sites, calls of 8 to 63 steps also run as one
+    persistent launch; the state equals single-step launches bit for bit."""
+    nx, ny = 1024, 1024
+    f = _fields(nx, ny, seed=11)
+    with lbm.Grid(nx, ny, 0.7, 0.25, storage) as a, lbm.Grid(nx, ny, 0.7, 0.25, storage) as b:
+        a.init(*f)
+        b.init(*f)
+        a.step(8)
+        a.step(13)
+        for _ in range(21):
+            b.step(1)
+        assert a.t == b.t == 21
+        assert np.array_equal(a.get_state()[0], b.get_state()[0])
