@@ -234,10 +234,16 @@ def run_native(args):
     stream = torch.cuda.Stream()
     runs = workloads.sweep_2048()[:args.grids]
     storage = args.storage
+    if args.c2_field or args.drive is not None:
+        args.path = "single"  # batches refuse grids with a c2 field or a drive
     grids = []
     with torch.cuda.stream(stream):
         for r in runs:
             g = lbm.Grid(r.nx, r.ny, r.tau, r.c2, storage, stream=stream.cuda_stream)
+            if args.c2_field:
+                g.set_c2_field(workloads.c2_lens(r.nx, r.ny, r.c2))
+            if args.drive is not None:
+                g.set_drive(args.drive, 500.0)
             g.init(*workloads.acoustic_shear(r.nx, r.ny, r.amp))
             if args.config:
                 g.set_config(*args.config)
@@ -318,8 +324,13 @@ def run_native(args):
     # Roofline of the dominant kernel: algorithmic bytes of a launch / its
     # time, averaged over the launches (a launch = `spl` steps of all grids on
     # the batch path, one step of one grid on the single-grid path).
-    per_step_bytes = BYTES_PER_LU[storage] * (sites if batch is not None
-                                              else runs[0].nx * runs[0].ny)
+    # Algorithmic bytes of one launch's step: the distributions, plus the
+    # 4-byte 1.5 alpha of every site with a c2 field, plus the drive's 27 ny
+    # boundary stores.
+    lu_bytes = BYTES_PER_LU[storage] + (4 if args.c2_field else 0)
+    per_step_bytes = lu_bytes * (sites if batch is not None else runs[0].nx * runs[0].ny)
+    if args.drive is not None and batch is None:
+        per_step_bytes += 27 * runs[0].ny * (BYTES_PER_LU[storage] // 18)
     steps_launched = plan if batch is not None else [1] * n_launch
     achieved = per_step_bytes * sum(steps_launched) / (sum(launch_ms) * 1e-3) / 1e9
     per_launch_s = statistics.mean(launch_ms) * 1e-3
@@ -436,6 +447,10 @@ def run_native(args):
                             "grid barrier between steps)"
                             if batch is not None else "one step-kernel launch per grid and step"),
                    "steps_per_launch": spl,
+                   "c2_field": ("acoustic lens, c2 x (1 + 0.5 gaussian), 1.5 alpha per site in FP32"
+                                if args.c2_field else None),
+                   "drive": ({"amplitude": args.drive, "period": 500.0}
+                             if args.drive is not None else None),
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
@@ -443,8 +458,11 @@ def run_native(args):
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
                      "kernel": (f"k_batch_one (persistent, 9 grids, {spl} steps per launch)"
                                 if batch is not None
-                                else f"k_step_tma<{storage},stages={stages}>" if pipelined
-                                else f"k_step<{storage},vec={cfg[0]}>"),
+                                else f"k_step_tma<{storage},stages={stages}>"
+                                if pipelined and stages >= 2
+                                else f"k_step<{storage},vec={cfg[0]}>"
+                                + (" with c2 field" if args.c2_field else "")
+                                + (" + k_drive_x" if args.drive is not None else "")),
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "mean_launch_ms": per_launch_s * 1e3},
         "e2e": {"value": e2e_value, "unit": "MLUPS",
@@ -454,7 +472,7 @@ def run_native(args):
                         f"({'one batch launch' if batch is not None else 'lbm_step per grid'}), "
                         f"lbm_moments to host, for all {len(runs)} grids",
                 "jobs": args.e2e_jobs},
-        "gpu_launches": n_launch,
+        "gpu_launches": n_launch * (2 if args.drive is not None else 1),
         "clocks": clk,
         "single_grid_kernel": single,
         "batch_one_step_per_launch": one_step,
@@ -587,6 +605,10 @@ def main():
     ap.add_argument("--batch-rows", type=int, default=0)
     ap.add_argument("--walk16", default=None, choices=["auto", "v8", "v4", "v4pf2"],
                     help="walk of 16-bit grids in batch kernels (default: the library's)")
+    ap.add_argument("--c2-field", action="store_true",
+                    help="per-site c2 (an acoustic lens) on every grid; single-grid path")
+    ap.add_argument("--drive", type=float, default=None,
+                    help="driven channel with this amplitude (period 500); single-grid path")
     ap.add_argument("--steps-per-launch", type=int, default=20,
                     help="steps of all grids per persistent launch on the batch path")
     ap.add_argument("--tune", action="store_true")

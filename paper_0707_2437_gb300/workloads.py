@@ -18,6 +18,8 @@ synthetic.  Recipes (seeds are numpy ``default_rng`` seeds):
 * ``fourier_modes``    rho = 1 + sum of 8 seeded plane waves with integer
                        wave numbers in [-4, 4]^2 \\ {0}, scaled to max
                        |rho - 1| = amp, u = 0
+* ``c2_lens``          a per-site c^2 field: c^2 (1 + 0.5 exp(-r^2 / (2 w^2)))
+                       around the grid's centre (an acoustic lens)
 * ``sweep_2048``       9 runs on 2048^2: c^2 = 0.05 .. 0.45, tau ~ U[0.55, 1.5]
                        (seed 1), amplitudes log-spaced 1e-3 .. 5e-2
 * ``batch_grids``      512 grids with log-uniform site counts 64^2 .. 1024^2,
@@ -83,6 +85,14 @@ def fourier_modes(nx: int, ny: int, amp: float = 1e-3, n_modes: int = 8,
     d *= amp / np.max(np.abs(d))
     z = np.zeros((ny, nx))
     return 1.0 + d, z, z.copy()
+
+
+def c2_lens(nx: int, ny: int, c2: float, contrast: float = 0.5, width: float = 0.15):
+    """A smooth acoustic lens: c^2 raised by `contrast` (relative) in a
+    Gaussian bump of relative width `width` at the grid's centre."""
+    x = (np.arange(nx, dtype=np.float64)[None, :] + 0.5) / nx - 0.5
+    y = (np.arange(ny, dtype=np.float64)[:, None] + 0.5) / ny - 0.5
+    return c2 * (1.0 + contrast * np.exp(-(x * x + y * y) / (2 * width * width)))
 
 
 @dataclass
