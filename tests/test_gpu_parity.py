@@ -451,3 +451,17 @@ def test_large_grid_short_calls_persistent_equal_single_launches(lbm, storage):
             b.step(1)
         assert a.t == b.t == 21
         assert np.array_equal(a.get_state()[0], b.get_state()[0])
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16d", "bf16d"])
+def test_y_uniform_state_stays_y_uniform_on_gpu(lbm, storage):
+    """A y-uniform plane wave stays exactly y-uniform on the GPU (every row
+    bitwise equal), as the paper's 4-row runs require."""
+    nx, ny = 1024, 4
+    f = workloads.progressive_wave(nx, ny, 2e-3, 0.4)
+    with lbm.Grid(nx, ny, 0.6, 0.16, storage) as g:
+        g.init(*f)
+        g.step(300)
+        rho, ux, uy = g.moments()
+    for a in (rho, ux, uy):
+        assert all(np.array_equal(a[0], a[y]) for y in range(1, ny))

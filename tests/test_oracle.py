@@ -446,3 +446,39 @@ def test_linear_mode_prediction_matches_small_amplitude_run():
     z = 2 * np.mean((r - 1) * np.exp(-1j * (kx * x + ky * y)))
     pred = linear_mode_prediction(z0, kx, ky, tau, alpha, steps)
     assert abs(z - pred) < 1e-6 * abs(z0)
+
+
+def test_alpha_zero_is_textbook_lbgk():
+    """With alpha = 0 (c^2 = 1/3) the force vanishes and Eq. 5 is the standard
+    D2Q9 LBGK update (Section 2): an independent numpy LBGK (push streaming by
+    array rolls, the standard equilibrium) gives the same state."""
+    nx, ny, tau, steps = 24, 17, 0.7, 40
+    rho, ux, uy = workloads.fourier_modes(nx, ny, amp=2e-2, seed=6)
+    ux = 0.02 * np.sin(2 * np.pi * np.arange(ny) / ny)[:, None] * np.ones((1, nx))
+    f = oracle.init(rho, ux, uy)
+    g = f.copy()
+    oracle.run(f, tau, 0.0, steps)
+    ex, ey = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1]), np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    for _ in range(steps):
+        r = g.sum(axis=0)
+        vx = np.tensordot(ex, g, axes=1) / r
+        vy = np.tensordot(ey, g, axes=1) / r
+        for i in range(9):
+            eu = ex[i] * vx + ey[i] * vy
+            feq = w[i] * r * (1 + 3 * eu + 4.5 * eu ** 2 - 1.5 * (vx ** 2 + vy ** 2))
+            g[i] = g[i] - (g[i] - feq) / tau
+        for i in range(9):
+            g[i] = np.roll(np.roll(g[i], ey[i], axis=0), ex[i], axis=1)
+    np.testing.assert_allclose(f, g, rtol=0, atol=1e-14)
+
+
+def test_y_uniform_state_stays_y_uniform_bitwise():
+    """Section 4 runs plane waves on grids 4 sites high: a state uniform in y
+    stays exactly uniform (every row bitwise equal), for any alpha."""
+    nx, ny = 64, 5
+    rho, ux, uy = workloads.progressive_wave(nx, ny, 2e-3, 0.4)
+    f = oracle.init(rho, ux, uy)
+    oracle.run(f, 0.6, oracle.alpha_from_c2(0.16), 50)
+    for i in range(9):
+        assert all(np.array_equal(f[i][0], f[i][y]) for y in range(1, ny))
