@@ -346,49 +346,50 @@ def run_native(args):
             # `spl` steps moves `spl` times the bytes of one step.
             traffic = entry["dram_bytes_per_step"] * spl
 
-    # The same batch with one step per launch, for the launch overhead.
+    # The same batch with one step per launch, for the launch overhead, and
+    # the plain single-grid step kernel on the same grids (one launch per grid
+    # and step).  Both are timed as back-to-back sequences of launches with one
+    # event pair around the sequence: the host enqueues faster than the GPU
+    # runs, so the mean per launch is the kernel time plus the real gap between
+    # kernels (events around each launch would also count the host's enqueue
+    # latency, during which the GPU waits).
+    def sequence_ms(n, launch):
+        launch()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
     one_step = None
     if batch is not None and spl > 1:
         n1 = max(20, args.steps // 20)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(n1)]
-        batch.step(1)
-        torch.cuda.synchronize()
-        for a, b_ in ev:
-            a.record(stream)
-            batch.step(1)
-            b_.record(stream)
-        torch.cuda.synchronize()
-        ms1 = statistics.mean(a.elapsed_time(b_) for a, b_ in ev)
+        ms1 = sequence_ms(n1, lambda: batch.step(1))
         one_step = {"launches": n1, "mean_launch_ms": ms1,
                     "achieved": per_step_bytes / (ms1 * 1e-3) / 1e9,
                     "frac": per_step_bytes / (ms1 * 1e-3) / 1e9 / peak,
-                    "mlups": sites / (ms1 * 1e-3) / 1e6}
+                    "mlups": sites / (ms1 * 1e-3) / 1e6,
+                    "timing": "back-to-back launches, one event pair"}
 
-    # The plain single-grid step kernel on the same grids (one launch per grid
-    # and step), for its own roofline fraction.
     single = None
     if batch is not None and not args.no_single:
         n1 = max(20, args.steps // 10)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(n1 * len(grids))]
-        for g in grids:
-            g.step(1)
-        torch.cuda.synchronize()
-        k = 0
-        for _ in range(n1):
+
+        def all_grids_one_step():
             for g in grids:
-                ev[k][0].record(stream)
                 g.step(1)
-                ev[k][1].record(stream)
-                k += 1
-        torch.cuda.synchronize()
-        ms1 = statistics.mean(a.elapsed_time(b_) for a, b_ in ev)
+
+        ms1 = sequence_ms(n1, all_grids_one_step) / len(grids)
         b1 = BYTES_PER_LU[storage] * runs[0].nx * runs[0].ny
         single = {"kernel": f"k_step<{storage},vec={cfg[0]}>", "launches": n1 * len(grids),
                   "mean_launch_ms": ms1, "achieved": b1 / (ms1 * 1e-3) / 1e9,
                   "frac": b1 / (ms1 * 1e-3) / 1e9 / measured_peak()[0],
-                  "mlups": runs[0].nx * runs[0].ny / (ms1 * 1e-3) / 1e6}
+                  "mlups": runs[0].nx * runs[0].ny / (ms1 * 1e-3) / 1e6,
+                  "timing": "back-to-back launches, one event pair"}
 
     # End to end through the C ABI with host buffers: one job = lbm_init from
     # pinned host fields, e2e_steps steps, lbm_moments back to pinned host

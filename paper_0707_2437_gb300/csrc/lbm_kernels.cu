@@ -26,6 +26,35 @@ bool valid_vec(int storage, int nx, int vec) {
 }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  The single-grid step kernels are launched
+// with programmatic stream serialization allowed: each block first lets the next launch on the stream
+// start (the next grid is launched once every block of this one has started
+// or exited, so its blocks only take SM slots this grid no longer needs), then
+// waits until the previous grid has completed and its memory is visible, and
+// only then touches global memory.  The next step's launch latency is thereby
+// hidden behind this step's tail.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block,
+                              size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// ---------------------------------------------------------------------------
 // Fused step: one warp per (strip, row segment) tile.
 
 template <int S, int V, bool PF, int RND = 0, int VA = 0>
@@ -33,6 +62,7 @@ __global__ void __launch_bounds__(256, 2)
     k_step(const void *__restrict__ fin, void *__restrict__ fout, int nx, int ny, size_t P,
            int nstrips, long long ntiles, int rows, Coef c, const uint32_t *tdev,
            uint32_t toff, const float *__restrict__ a15f) {
+    pdl_enter();
     long long tile = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (tile >= ntiles) return;  // whole warps leave together
     int strip = (int)(tile % nstrips);
@@ -60,6 +90,7 @@ template <int S>
 __global__ void __launch_bounds__(256, 1)
     k_step_wide(const void *__restrict__ fin, void *__restrict__ fout, int nx, int ny, size_t P,
                 int nstrips, long long ntiles, int rows, Coef c) {
+    pdl_enter();
     long long tile = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (tile >= ntiles) return;
     int strip = (int)(tile % nstrips);
@@ -79,6 +110,7 @@ template <int S, int NST>
 __global__ void __launch_bounds__(256, 2)
     k_step_tma(const void *__restrict__ fin, void *__restrict__ fout, int nx, int ny, size_t P,
                int nstrips, long long ntiles, int rows, Coef c, int *status) {
+    pdl_enter();
     extern __shared__ __align__(128) unsigned char smem[];
     const int nwb = blockDim.x >> 5;
     const int wib = threadIdx.x >> 5;
@@ -109,15 +141,13 @@ static Err launch_step_t(const TileCfg &cfg, const void *fin, void *fout, int nx
         if constexpr (RND == 0 && V <= 4) {
             if (uses_prefetch(S, cfg)) {
                 if constexpr (Pack<S, V>::BYTES == 8)
-                    k_step<S, V, true, 0, 1><<<nb, nt, 0, st>>>(fin, fout, nx, ny, P, g.nstrips,
-                                                              g.ntiles, cfg.rows, c, tdev, toff,
-                                                              a15f);
+                    return launch_pdl(k_step<S, V, true, 0, 1>, nb, nt, 0, st, fin, fout, nx, ny,
+                                      P, g.nstrips, g.ntiles, cfg.rows, c, tdev, toff, a15f);
                 else
                     return cudaErrorInvalidValue;
             } else {
-                k_step<S, V, false, 0, 1><<<nb, nt, 0, st>>>(fin, fout, nx, ny, P, g.nstrips,
-                                                           g.ntiles, cfg.rows, c, tdev, toff,
-                                                           a15f);
+                return launch_pdl(k_step<S, V, false, 0, 1>, nb, nt, 0, st, fin, fout, nx, ny, P,
+                                  g.nstrips, g.ntiles, cfg.rows, c, tdev, toff, a15f);
             }
             return cudaGetLastError();
         } else {
@@ -126,19 +156,20 @@ static Err launch_step_t(const TileCfg &cfg, const void *fin, void *fout, int nx
     }
     if (uses_prefetch(S, cfg) && V == 8) {
         if constexpr (S != ST_F32 && V == 8 && RND == 0)
-            k_step_wide<S><<<nb, nt, 0, st>>>(fin, fout, nx, ny, P, g.nstrips, g.ntiles, cfg.rows,
-                                              c);
+            return launch_pdl(k_step_wide<S>, nb, nt, 0, st, fin, fout, nx, ny, P, g.nstrips,
+                              g.ntiles, cfg.rows, c);
         else
             return cudaErrorInvalidValue;
     } else if (uses_prefetch(S, cfg)) {
         if constexpr (Pack<S, V>::BYTES == 8)
-            k_step<S, V, true, RND><<<nb, nt, 0, st>>>(fin, fout, nx, ny, P, g.nstrips, g.ntiles,
-                                                      cfg.rows, c, tdev, toff, nullptr);
+            return launch_pdl(k_step<S, V, true, RND>, nb, nt, 0, st, fin, fout, nx, ny, P,
+                              g.nstrips, g.ntiles, cfg.rows, c, tdev, toff,
+                              (const float *)nullptr);
         else
             return cudaErrorInvalidValue;
     } else {
-        k_step<S, V, false, RND><<<nb, nt, 0, st>>>(fin, fout, nx, ny, P, g.nstrips, g.ntiles,
-                                                   cfg.rows, c, tdev, toff, nullptr);
+        return launch_pdl(k_step<S, V, false, RND>, nb, nt, 0, st, fin, fout, nx, ny, P,
+                          g.nstrips, g.ntiles, cfg.rows, c, tdev, toff, (const float *)nullptr);
     }
     return cudaGetLastError();
 }
@@ -149,9 +180,8 @@ static Err launch_tma_t(const TileCfg &cfg, const void *fin, void *fout, int nx,
     StepGeom g = step_geom(nx, ny, cfg);
     long long blocks = (g.ntiles + cfg.warps - 1) / cfg.warps;
     int smem = tma_smem_bytes<S>(cfg.warps, NST);
-    k_step_tma<S, NST><<<(unsigned)blocks, 32 * cfg.warps, smem, st>>>(
-        fin, fout, nx, ny, P, g.nstrips, g.ntiles, cfg.rows, c, status);
-    return cudaGetLastError();
+    return launch_pdl(k_step_tma<S, NST>, (unsigned)blocks, 32u * cfg.warps, (size_t)smem, st, fin,
+                      fout, nx, ny, P, g.nstrips, g.ntiles, cfg.rows, c, status);
 }
 
 template <int S, int NST>
