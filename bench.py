@@ -234,8 +234,8 @@ def run_native(args):
     stream = torch.cuda.Stream()
     runs = workloads.sweep_2048()[:args.grids]
     storage = args.storage
-    if args.c2_field or args.drive is not None:
-        args.path = "single"  # batches refuse grids with a c2 field or a drive
+    if args.drive is not None:
+        args.path = "single"  # batches refuse driven grids
     grids = []
     with torch.cuda.stream(stream):
         for r in runs:
@@ -329,6 +329,7 @@ def run_native(args):
     # boundary stores.
     lu_bytes = BYTES_PER_LU[storage] + (4 if args.c2_field else 0)
     per_step_bytes = lu_bytes * (sites if batch is not None else runs[0].nx * runs[0].ny)
+    b1 = lu_bytes * runs[0].nx * runs[0].ny  # one grid-step of the single-grid kernel
     if args.drive is not None and batch is None:
         per_step_bytes += 27 * runs[0].ny * (BYTES_PER_LU[storage] // 18)
     steps_launched = plan if batch is not None else [1] * n_launch
@@ -384,7 +385,6 @@ def run_native(args):
                 g.step(1)
 
         ms1 = sequence_ms(n1, all_grids_one_step) / len(grids)
-        b1 = BYTES_PER_LU[storage] * runs[0].nx * runs[0].ny
         single = {"kernel": f"k_step<{storage},vec={cfg[0]}>", "launches": n1 * len(grids),
                   "mean_launch_ms": ms1, "achieved": b1 / (ms1 * 1e-3) / 1e9,
                   "frac": b1 / (ms1 * 1e-3) / 1e9 / measured_peak()[0],
@@ -607,7 +607,7 @@ def main():
     ap.add_argument("--walk16", default=None, choices=["auto", "v8", "v4", "v4pf2"],
                     help="walk of 16-bit grids in batch kernels (default: the library's)")
     ap.add_argument("--c2-field", action="store_true",
-                    help="per-site c2 (an acoustic lens) on every grid; single-grid path")
+                    help="per-site c2 (an acoustic lens) on every grid")
     ap.add_argument("--drive", type=float, default=None,
                     help="driven channel with this amplitude (period 500); single-grid path")
     ap.add_argument("--steps-per-launch", type=int, default=20,

@@ -108,7 +108,7 @@ int lbm_init(lbm_t h, const double *rho, const double *ux, const double *uy,
 /* Queues n >= 0 time steps of Eq. 5 (stream, moments, central grad(rho),
  * collide with force) on the handle's stream.  From 64 steps on, or from 8
  * on grids of at least 2^20 sites (while persistent mode is on, the default,
- * and without a c2 field or a drive), the steps run as one persistent launch:
+ * and without a drive), the steps run as one persistent launch:
  * the batched kernel (see lbm_batch_create) with this grid alone, warps taking
  * tiles dynamically, a bounded grid barrier between steps.  Other calls
  * launch the step kernel with the handle's tile configuration, replayed from
@@ -169,10 +169,9 @@ int lbm_set_drive(lbm_t h, int on, double amplitude, double period);
  * [ny][nx] array of c_e^2 > 0 (host if on_device == 0, else device; host
  * values are checked); the force at site x uses alpha(x) = 1/3 - c2(x) in
  * Eq. 5.  NULL returns to the grid's uniform c2.  The field costs one more
- * 4-byte read per site and step.  While a field is set: lbm_step uses the
- * step kernel (vec <= 4, no bulk-copy pipeline, nearest rounding), and the
- * grid cannot join a batch (lbm_batch_create and lbm_batch_step return
- * LBM_EINVAL). */
+ * 4-byte read per site and step.  While a field is set the walks use at most
+ * 4 sites per lane, no bulk-copy pipeline and nearest rounding; the grid can
+ * join a batch and long lbm_step calls still run one persistent launch. */
 int lbm_set_c2_field(lbm_t h, const double *c2, int on_device);
 
 /* Steps taken since lbm_init / lbm_set_state. */
@@ -251,7 +250,7 @@ int lbm_kernel_ms(lbm_t h, double *ms, long long *launches);
  * bitwise the state it reaches when stepped alone.  The batch refers to the
  * handles; they must outlive it and must not be stepped individually while
  * it is being stepped.  The batch's work runs on the stream of grids[0].
- * Grids with a c2 field or a drive are refused (LBM_EINVAL). */
+ * Grids with a c2 field may join; driven grids are refused (LBM_EINVAL). */
 int lbm_batch_create(const lbm_t *grids, int n, lbm_batch_t *out);
 int lbm_batch_destroy(lbm_batch_t b);
 
@@ -259,8 +258,9 @@ int lbm_batch_destroy(lbm_batch_t b);
  * n steps each), one persistent launch per kind group, replayed from a CUDA
  * graph.  Asynchronous.  A barrier wait that exceeds its time limit makes the
  * kernel stop and the next synchronising batch call return LBM_ETIMEOUT.
- * LBM_EINVAL if a grid has gained a c2 field or a drive since the batch was
- * created. */
+ * If a grid's c2 field or rounding mode changed since the batch was built,
+ * the work-list is rebuilt first (the call then waits for the stream).
+ * LBM_EINVAL if a grid has gained a drive. */
 int lbm_batch_step(lbm_batch_t b, long long n, const long long *limits);
 
 /* Waits for the batch's stream and returns the kernel's status

@@ -331,7 +331,7 @@ extern "C" int lbm_step(lbm_t h, long long n) {
         return LBM_OK;
     }
     const bool large = (long long)h->nx * h->ny >= kLargeSites;
-    if (h->persistent && !h->a15f && !h->drive &&
+    if (h->persistent && !h->drive &&
         (n >= kPersistentMin || (large && n >= kPersistentMinLarge))) {
         // One persistent launch of all n steps (dynamic tile scheduling,
         // barrier between steps), bitwise the same as n single launches.

@@ -24,6 +24,7 @@ namespace {
 
 struct GridDesc {
     void *buf[2];
+    const float *a15f;  // 1.5 alpha per site for a grid with a c2 field, else NULL
     size_t P;
     int nx, ny;
     int kind;  // kind_code(storage, vec, stochastic rounding)
@@ -36,9 +37,11 @@ struct Tile {
 };
 
 // A grid's walk in the batch kernels: storage kind, sites per lane (1, 4 or
-// 8) and stochastic rounding.
-constexpr int kind_code(int storage, int vec, int sr) { return storage * 32 + vec + 16 * sr; }
-constexpr int kKindCodes = 3 * 32;
+// 8), stochastic rounding, and a per-site c2 field.
+constexpr int kind_code(int storage, int vec, int sr, int va = 0) {
+    return storage * 64 + vec + 16 * sr + 32 * va;
+}
+constexpr int kKindCodes = 3 * 64;
 
 constexpr int kBatchWarps = 4;  // warps per block of the persistent kernel
 
@@ -118,9 +121,10 @@ __device__ __forceinline__ void reset_counter(unsigned *bar, long long k) {
     if (k >= 1 && blockIdx.x == 0 && threadIdx.x == 0) *step_counter(bar, k - 1) = 0u;
 }
 
-template <int S, int V, bool PF = false, int RND = 0>
+template <int S, int V, bool PF = false, int RND = 0, int VA = 0>
 __device__ __noinline__ void do_tile(const GridDesc &g, int par, const Tile &t, uint32_t step) {
-    Walker<S, V, LD_CG, RND> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P, t.x0);
+    Walker<S, V, LD_CG, RND, VA> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P, t.x0);
+    if constexpr (VA) w.a15f = g.a15f;
     if constexpr (RND) w.rstep = step;
     if constexpr (PF)
         w.run_prefetch(t.y0, t.y1, t.dir, g.c);
@@ -185,6 +189,24 @@ __global__ void __launch_bounds__(32 * kBatchWarps, 3)
                 case kind_code(ST_BF16, 1, 1):
                     do_tile<ST_BF16, 1, false, 1>(g, par, t, step);
                     break;
+                case kind_code(ST_F32, 4, 0, 1):
+                    do_tile<ST_F32, 4, false, 0, 1>(g, par, t, step);
+                    break;
+                case kind_code(ST_F32, 1, 0, 1):
+                    do_tile<ST_F32, 1, false, 0, 1>(g, par, t, step);
+                    break;
+                case kind_code(ST_F16, 4, 0, 1):
+                    do_tile<ST_F16, 4, true, 0, 1>(g, par, t, step);
+                    break;
+                case kind_code(ST_F16, 1, 0, 1):
+                    do_tile<ST_F16, 1, false, 0, 1>(g, par, t, step);
+                    break;
+                case kind_code(ST_BF16, 4, 0, 1):
+                    do_tile<ST_BF16, 4, true, 0, 1>(g, par, t, step);
+                    break;
+                case kind_code(ST_BF16, 1, 0, 1):
+                    do_tile<ST_BF16, 1, false, 0, 1>(g, par, t, step);
+                    break;
                 default:
                     break;
             }
@@ -198,7 +220,7 @@ __global__ void __launch_bounds__(32 * kBatchWarps, 3)
 // inlined, so the kernel keeps the single-grid kernel's register budget (128,
 // 16 warps per SM; 170 and 12 warps per SM for the two-row prefetch) instead
 // of paying for calls.  Same time-step loop and bounded barrier as k_batch.
-template <int S, int V, int PD, int RND>
+template <int S, int V, int PD, int RND, int VA = 0>
 __global__ void __launch_bounds__(32 * kBatchWarps, PD == 2 ? 3 : 4)
     k_batch_one(const GridDesc *__restrict__ grids, const Tile *__restrict__ tiles, int ntiles,
                 const long long *__restrict__ limit, const int *__restrict__ parity0,
@@ -219,7 +241,8 @@ __global__ void __launch_bounds__(32 * kBatchWarps, PD == 2 ? 3 : 4)
             const GridDesc &g = grids[t.grid];
             const int par = (parity0[t.grid] + (int)(k & 1)) & 1;
             const Coef c = g.c;
-            Walker<S, V, LD_CG, RND> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P, t.x0);
+            Walker<S, V, LD_CG, RND, VA> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P, t.x0);
+            if constexpr (VA) w.a15f = g.a15f;
             if constexpr (RND) w.rstep = t0[t.grid] + (uint32_t)k;
             if constexpr (S != ST_F32 && V == 8)
                 w.run_async(t.y0, t.y1, t.dir, c, &rowbuf[threadIdx.x >> 5][0]);
@@ -264,6 +287,12 @@ BatchKernel kernel_for(const std::vector<int> &kinds, int walk16) {
                 return two ? k_batch_one<ST_F16, 4, 2, 1> : k_batch_one<ST_F16, 4, 1, 1>;
             case kind_code(ST_BF16, 4, 1):
                 return two ? k_batch_one<ST_BF16, 4, 2, 1> : k_batch_one<ST_BF16, 4, 1, 1>;
+            case kind_code(ST_F32, 4, 0, 1):
+                return k_batch_one<ST_F32, 4, 0, 0, 1>;
+            case kind_code(ST_F16, 4, 0, 1):
+                return k_batch_one<ST_F16, 4, 1, 0, 1>;
+            case kind_code(ST_BF16, 4, 0, 1):
+                return k_batch_one<ST_BF16, 4, 1, 0, 1>;
             default:
                 break;
         }
@@ -275,6 +304,10 @@ BatchKernel kernel_for(const std::vector<int> &kinds, int walk16) {
 
 struct lbm_batch {
     std::vector<lbm_grid *> grids;
+    // Per grid, the c2 field pointer and rounding mode the work-list was built
+    // for (a change rebuilds it at the next step call).
+    std::vector<const float *> built_a15f;
+    std::vector<int> built_rounding;
     cudaStream_t stream = nullptr;
     int device = 0;
     int rows = 16;
@@ -342,7 +375,8 @@ static void drop_graph(lbm_batch *b) {
 // run 13 % faster than 4; with stochastic rounding the 8-site kernel spills
 // and runs 25 % slower.)
 static int batch_vec(const lbm_batch *b, const lbm_grid *g) {
-    const bool eight = b->walk16 == LBM_WALK16_V8 || (b->walk16 == LBM_WALK16_AUTO && !g->rounding);
+    const bool eight = !g->a15f && (b->walk16 == LBM_WALK16_V8 ||
+                                    (b->walk16 == LBM_WALK16_AUTO && !g->rounding));
     if (g->storage != ST_F32 && eight && g->nx % 8 == 0) return 8;
     return g->nx % 4 == 0 ? 4 : 1;
 }
@@ -356,11 +390,12 @@ static int build_worklist(lbm_batch *b) {
         GridDesc &d = gd[k];
         d.buf[0] = g->buf[0];
         d.buf[1] = g->buf[1];
+        d.a15f = g->a15f;
         d.P = g->P;
         d.nx = g->nx;
         d.ny = g->ny;
         int v = batch_vec(b, g);
-        d.kind = kind_code(g->storage, v, g->rounding ? 1 : 0);
+        d.kind = kind_code(g->storage, v, g->rounding ? 1 : 0, g->a15f ? 1 : 0);
         d.pad = 0;
         d.c = g->coef;
         int w = 32 * v;
@@ -381,7 +416,8 @@ static int build_worklist(lbm_batch *b) {
     std::vector<int> count(kKindCodes, 0);
     for (size_t k = 0; k < b->grids.size(); ++k) {
         const lbm_grid *g = b->grids[k];
-        bytes[gd[k].kind] += (double)g->nx * g->ny * (g->storage == ST_F32 ? 72.0 : 36.0);
+        bytes[gd[k].kind] += (double)g->nx * g->ny *
+                             ((g->storage == ST_F32 ? 72.0 : 36.0) + (g->a15f ? 4.0 : 0.0));
     }
     for (const Tile &t : tiles) count[gd[t.grid].kind]++;
     int kinds_present = 0;
@@ -430,6 +466,12 @@ static int build_worklist(lbm_batch *b) {
     BCK(cudaMemcpy(b->d_tiles, ordered.data(), sizeof(Tile) * ordered.size(),
                    cudaMemcpyHostToDevice));
     b->ntiles = (int)ordered.size();
+    b->built_a15f.clear();
+    b->built_rounding.clear();
+    for (const lbm_grid *g : b->grids) {
+        b->built_a15f.push_back(g->a15f);
+        b->built_rounding.push_back(g->rounding);
+    }
     drop_graph(b);
     return LBM_OK;
 }
@@ -459,8 +501,6 @@ extern "C" int lbm_batch_create(const lbm_t *grids, int n, lbm_batch_t *out) {
     *out = nullptr;
     for (int k = 0; k < n; ++k) {
         if (!grids[k]) return bfail(LBM_EINVAL, "lbm_batch_create: NULL grid");
-        if (grids[k]->a15f)
-            return bfail(LBM_EINVAL, "lbm_batch_create: grids with a c2 field are not batched");
         if (grids[k]->drive)
             return bfail(LBM_EINVAL, "lbm_batch_create: driven grids are not batched");
     }
@@ -599,9 +639,18 @@ static int run_batch(lbm_batch *b, long long n, const long long *limits, bool ad
 extern "C" int lbm_batch_step(lbm_batch_t b, long long n, const long long *limits) {
     if (!b || n < 0) return bfail(LBM_EINVAL, "lbm_batch_step: bad argument");
     if (n == 0) return LBM_OK;
-    for (lbm_grid *g : b->grids)
-        if (g->a15f || g->drive)
-            return bfail(LBM_EINVAL, "lbm_batch_step: a grid gained a c2 field or a drive");
+    bool stale = false;
+    for (size_t k = 0; k < b->grids.size(); ++k) {
+        const lbm_grid *g = b->grids[k];
+        if (g->drive) return bfail(LBM_EINVAL, "lbm_batch_step: a grid has a drive");
+        stale = stale || g->a15f != b->built_a15f[k] || g->rounding != b->built_rounding[k];
+    }
+    if (stale) {
+        // A grid's c2 field or rounding changed since the work-list was built.
+        BCK(cudaStreamSynchronize(b->stream));
+        int rc = build_worklist(b);
+        if (rc != LBM_OK) return rc;
+    }
     return run_batch(b, n, limits, true);
 }
 
