@@ -341,23 +341,50 @@ __device__ __forceinline__ double wd(int i) {
     return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
 }
 
-// Equilibrium initialisation (Section 2, Eq. 2): the pre-collision value at
-// site x is plane i at x - e_i, so plane i at y holds the equilibrium of the
-// fields at y + e_i.  Stored as h_i = (fbar_i - w_i rho0)/w_i, computed in FP64.
+template <int S>
+__device__ __forceinline__ float ld_elem_f(const void *f, size_t idx) {
+    if constexpr (S == ST_F32)
+        return reinterpret_cast<const float *>(f)[idx];
+    else if constexpr (S == ST_F16)
+        return __half2float(reinterpret_cast<const __half *>(f)[idx]);
+    else
+        return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(f)[idx]);
+}
+
+template <int S>
+__device__ __forceinline__ void st_elem_f(void *f, size_t idx, float v) {
+    if constexpr (S == ST_F32)
+        reinterpret_cast<float *>(f)[idx] = v;
+    else if constexpr (S == ST_F16)
+        reinterpret_cast<__half *>(f)[idx] = __float2half_rn(v);
+    else
+        reinterpret_cast<__nv_bfloat16 *>(f)[idx] = __float2bfloat16_rn(v);
+}
+
+// Equilibrium initialisation (Section 2, Eq. 2).  Each site computes the
+// equilibrium of its own fields in FP32, as h_i = (fbar_i - w_i rho0)/w_i =
+// drho + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u.u), and writes direction i where
+// the pull of that site will find it: plane i at x - e_i.  Only the deviation
+// drho = rho - rho0 is formed in FP64 (it can be far below FP32's resolution
+// of rho near 1).
 template <int S>
 __global__ void k_init(void *f, int nx, int ny, size_t P, double rho0, const double *rho,
                        const double *ux, const double *uy) {
     long long n = (long long)nx * ny;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n;
          s += (long long)gridDim.x * blockDim.x) {
-        int x = (int)(s % nx), y = (int)(s / nx);
+        const int x = (int)(s % nx), y = (int)(s / nx);
+        const double r = rho[s];
+        const float dr = (float)(r - rho0);
+        const float rf = (float)r;
+        const float u = (float)ux[s], v = (float)uy[s];
+        const float m15usq = -1.5f * __fmaf_rn(u, u, __fmul_rn(v, v));
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            size_t src = (size_t)wrapi(y + EYi(i), ny) * nx + wrapi(x + EXi(i), nx);
-            double r = rho[src], u = ux[src], v = uy[src];
-            double eu = EXi(i) * u + EYi(i) * v;
-            double h = (r - rho0) + r * (3.0 * eu + 4.5 * eu * eu - 1.5 * (u * u + v * v));
-            st_elem_d<S>(f, (size_t)i * P + s, h);
+            const float eu = EXi(i) * u + EYi(i) * v;  // e components are 0 and +-1
+            const float poly = __fmaf_rn(__fmul_rn(4.5f, eu), eu, __fmaf_rn(3.0f, eu, m15usq));
+            const size_t dst = (size_t)wrapi(y - EYi(i), ny) * nx + wrapi(x - EXi(i), nx);
+            st_elem_f<S>(f, (size_t)i * P + dst, __fmaf_rn(rf, poly, dr));
         }
     }
 }
@@ -404,19 +431,33 @@ __device__ __forceinline__ void site_moments_d(const void *f, int nx, int ny, si
     }
 }
 
+// Moments (Section 2, Eq. 3) of every site, in FP32 arithmetic: drho = sum
+// w_i h_i and j = sum w_i h_i e_i of the pulled values, u = j / rho.  The
+// outputs are FP64 arrays with rho = rho0 + drho formed in FP64.  (The FP64
+// reductions below use FP64 per-site moments: their totals and Fourier
+// coefficients carry the accuracy of the mass checks and wave fits.)
 template <int S>
 __global__ void k_moments(const void *f, int nx, int ny, size_t P, double rho0, double *rho,
                           double *ux, double *uy) {
     long long n = (long long)nx * ny;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n;
          s += (long long)gridDim.x * blockDim.x) {
-        int x = (int)(s % nx), y = (int)(s / nx);
-        double dr, jx, jy;
-        site_moments_d<S>(f, nx, ny, P, x, y, rho0, dr, jx, jy);
-        double r = rho0 + dr;
+        const int x = (int)(s % nx), y = (int)(s / nx);
+        float dr = 0.f, jx = 0.f, jy = 0.f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const size_t src = (size_t)wrapi(y - EYi(i), ny) * nx + wrapi(x - EXi(i), nx);
+            const float wi = i == 0 ? 4.0f / 9.0f : (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
+            const float g = __fmul_rn(wi, ld_elem_f<S>(f, (size_t)i * P + src));
+            dr = __fadd_rn(dr, g);
+            if (EXi(i)) jx = EXi(i) > 0 ? __fadd_rn(jx, g) : __fsub_rn(jx, g);
+            if (EYi(i)) jy = EYi(i) > 0 ? __fadd_rn(jy, g) : __fsub_rn(jy, g);
+        }
+        const double r = rho0 + (double)dr;
+        const float rf = (float)r;
         if (rho) rho[s] = r;
-        if (ux) ux[s] = jx / r;
-        if (uy) uy[s] = jy / r;
+        if (ux) ux[s] = (double)__fdiv_rn(jx, rf);
+        if (uy) uy[s] = (double)__fdiv_rn(jy, rf);
     }
 }
 

@@ -486,3 +486,17 @@ def test_tiny_grids_match_oracle(lbm, storage, tol, nx, ny):
     ref = oracle.simulate(rho, ux, uy, tau, c2, 73)
     err = max(np.abs(a - b).max() for a, b in zip(got, ref))
     assert err <= tol, err
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 2e-9), ("f16d", 1e-6), ("bf16d", 1e-5)])
+def test_init_then_moments_returns_the_fields(lbm, storage, tol):
+    """The equilibrium of Eq. 2 has the moments of Eq. 3 exactly (sum w_i = 1,
+    sum w_i e_i = 0, sum w_i e_i e_i = I/3), so moments right after init
+    return the given fields up to the storage's rounding."""
+    nx, ny = 300, 70
+    rho, ux, uy = _fields(nx, ny, amp=1e-3, seed=21, u=1e-3)
+    with lbm.Grid(nx, ny, 0.8, 0.2, storage) as g:
+        g.init(rho, ux, uy)
+        r, u, v = g.moments()
+    err = max(np.abs(r - rho).max(), np.abs(u - ux).max(), np.abs(v - uy).max())
+    assert err <= tol, err
