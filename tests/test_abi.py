@@ -68,3 +68,48 @@ def test_bytes_required():
     # planes are padded to 64 elements
     assert lib.lbm_bytes_required(3, 3, 0) == 2 * 9 * 64 * 4
     assert lib.lbm_bytes_required(0, 3, 0) == 0
+
+
+def test_every_handle_call_rejects_null_before_device_work():
+    """Every call that takes a grid or batch handle returns LBM_EINVAL for
+    NULL, with no CUDA call (this host has no GPU)."""
+    lib = lbm.load()
+    i = ctypes.c_int()
+    d = ctypes.c_double()
+    ll = ctypes.c_longlong()
+    buf = (ctypes.c_double * 8)()
+    grid_calls = [
+        lambda: lib.lbm_moments(None, None, None, None, 0),
+        lambda: lib.lbm_sums(None, buf),
+        lambda: lib.lbm_mode(None, 0, 1, 0, buf),
+        lambda: lib.lbm_set_drive(None, 1, 1e-3, 500.0),
+        lambda: lib.lbm_set_c2_field(None, None, 0),
+        lambda: lib.lbm_sync(None),
+        lambda: lib.lbm_get_state(None, buf, ctypes.byref(ll)),
+        lambda: lib.lbm_set_state(None, buf, 0),
+        lambda: lib.lbm_set_config(None, 4, 16, 4),
+        lambda: lib.lbm_get_config(None, ctypes.byref(i), ctypes.byref(i), ctypes.byref(i)),
+        lambda: lib.lbm_set_pipeline(None, 1),
+        lambda: lib.lbm_get_pipeline(None, ctypes.byref(i), ctypes.byref(i)),
+        lambda: lib.lbm_set_rounding(None, 0),
+        lambda: lib.lbm_get_rounding(None, ctypes.byref(i)),
+        lambda: lib.lbm_tune(None, None),
+        lambda: lib.lbm_set_timing(None, 1),
+        lambda: lib.lbm_kernel_ms(None, ctypes.byref(d), ctypes.byref(ll)),
+        lambda: lib.lbm_set_persistent(None, 1),
+    ]
+    batch_calls = [
+        lambda: lib.lbm_batch_step(None, 1, None),
+        lambda: lib.lbm_batch_sync(None),
+        lambda: lib.lbm_batch_set_config(None, 16, 0),
+        lambda: lib.lbm_batch_tune(None),
+        lambda: lib.lbm_batch_get_config(None, ctypes.byref(i), ctypes.byref(i), ctypes.byref(i)),
+        lambda: lib.lbm_batch_get_groups(None, ctypes.byref(i)),
+        lambda: lib.lbm_batch_set_walk16(None, 0),
+        lambda: lib.lbm_batch_get_walk16(None, ctypes.byref(i)),
+        lambda: lib.lbm_batch_set_timeout_us(None, 1000),
+    ]
+    for k, call in enumerate(grid_calls + batch_calls):
+        assert call() == -1, k
+    assert lib.lbm_batch_destroy(None) == 0
+    assert lib.lbm_state_bytes(None) == 0
