@@ -1,0 +1,145 @@
+"""Host logic of the continuous-batching server, on the CPU: the device layer
+(grids, batches, free memory) is replaced by a fake that keeps the same
+bookkeeping, so admission by free memory, slot limits, arrival order, the
+per-grid step limits and retirement are checked without a GPU."""
+import pytest
+
+from paper_0707_2437_gb300 import serve, workloads
+
+
+class _FakeDevice:
+    def __init__(self, total):
+        self.total = total
+        self.used = 0
+        self.live = 0
+        self.max_live = 0
+        self.max_used = 0
+        self.created = []
+
+    # the subset of the lbm module the server uses
+    def load(self):
+        return None
+
+    def mem_info(self):
+        return self.total - self.used, self.total
+
+    def bytes_required(self, nx, ny, storage):
+        return nx * ny * (72 if storage == "f32" else 36)
+
+
+def _fake_lbm(dev):
+    class Grid:
+        def __init__(self, nx, ny, tau, c2, storage="f32", stream=None):
+            self.nx, self.ny, self.storage = nx, ny, storage
+            self.bytes = dev.bytes_required(nx, ny, storage)
+            dev.used += self.bytes
+            dev.max_used = max(dev.max_used, dev.used)
+            dev.live += 1
+            dev.max_live = max(dev.max_live, dev.live)
+            dev.created.append(self)
+            self.t = 0
+            self.closed = False
+            self.steps_at_close = None
+
+        def init(self, rho, ux, uy):
+            assert rho.shape == (self.ny, self.nx)
+
+        def moments(self):
+            return (None, None, None)
+
+        def sync(self):
+            pass
+
+        def close(self):
+            assert not self.closed
+            self.closed = True
+            self.steps_at_close = self.t
+            dev.used -= self.bytes
+            dev.live -= 1
+
+    class Batch:
+        def __init__(self, grids):
+            assert all(not g.closed for g in grids)
+            self.grids = list(grids)
+
+        def step(self, n, limits=None):
+            limits = limits or [n] * len(self.grids)
+            for g, lim in zip(self.grids, limits):
+                assert 0 <= lim <= n
+                g.t += lim
+
+        def sync(self):
+            return 0
+
+        def close(self):
+            pass
+
+    ns = type("FakeLbm", (), {})()
+    ns.load, ns.mem_info, ns.bytes_required = dev.load, dev.mem_info, dev.bytes_required
+    ns.Grid, ns.Batch = Grid, Batch
+    return ns
+
+
+def _requests(n=12, seed=7):
+    return workloads.serve_trace(count=n, rate_hz=1000.0, seed=seed, lo=64, hi=256,
+                                 steps_lo=100, steps_hi=1500)
+
+
+def test_every_request_runs_exactly_its_steps(monkeypatch):
+    dev = _FakeDevice(total=1 << 40)
+    monkeypatch.setattr(serve, "lbm", _fake_lbm(dev))
+    reqs = _requests()
+    stats = serve.Server(quantum=256, reserve_bytes=0).run(reqs, realtime=False)
+    assert sorted(r.rid for r in stats.results) == [q.rid for q in reqs]
+    by_rid = {g_rid: g for g_rid, g in zip([q.rid for q in reqs], dev.created)}
+    for q in reqs:
+        assert by_rid[q.rid].steps_at_close == q.steps
+    assert dev.live == 0 and dev.used == 0
+    assert stats.lattice_updates == sum(q.steps * q.nx * q.ny for q in reqs)
+    longest = max(q.steps for q in reqs)
+    assert stats.quanta >= -(-longest // 256)
+
+
+def test_admission_is_bounded_by_free_memory(monkeypatch):
+    reqs = _requests()
+    need = max(serve.Server(reserve_bytes=0)._need(q) for q in reqs)
+    reserve = 1000
+    dev = _FakeDevice(total=reserve + 2 * need + need // 2)  # room for two at a time
+    monkeypatch.setattr(serve, "lbm", _fake_lbm(dev))
+    stats = serve.Server(quantum=128, reserve_bytes=reserve).run(reqs, realtime=False)
+    assert len(stats.results) == len(reqs)
+    assert dev.max_live >= 2 and stats.max_active == dev.max_live
+    assert dev.max_used <= dev.total - reserve   # the reserve is never touched
+    assert dev.max_live < len(reqs)             # memory, not the trace, set the bound
+    assert dev.used == 0
+
+
+def test_slot_limit_and_arrival_order(monkeypatch):
+    dev = _FakeDevice(total=1 << 40)
+    monkeypatch.setattr(serve, "lbm", _fake_lbm(dev))
+    reqs = _requests(n=10)
+    stats = serve.Server(quantum=64, reserve_bytes=0, max_slots=3).run(reqs, realtime=False)
+    assert stats.max_active == 3 and dev.max_live == 3
+    admitted = sorted(stats.results, key=lambda r: (r.admitted_s, r.rid))
+    assert [r.rid for r in admitted] == sorted(r.rid for r in stats.results)
+    assert all(r.arrival_s == 0.0 for r in stats.results)  # all present at time 0
+
+
+def test_request_larger_than_the_device_is_refused(monkeypatch):
+    reqs = _requests(n=3)
+    dev = _FakeDevice(total=10)
+    monkeypatch.setattr(serve, "lbm", _fake_lbm(dev))
+    with pytest.raises(MemoryError):
+        serve.Server(quantum=64, reserve_bytes=0).run(reqs, realtime=False)
+
+
+def test_summary_percentiles():
+    st = serve.ServeStats()
+    for k in range(100):
+        st.results.append(serve.Result(k, 0.0, 0.0, float(k + 1), 10, 100, "f32"))
+    st.makespan_s = 100.0
+    st.lattice_updates = 1000
+    s = st.summary()
+    assert s["requests"] == 100
+    assert abs(s["p50_s"] - 50.5) < 1e-9 and 98.9 < s["p99_s"] < 99.1
+    assert s["mlups"] == pytest.approx(1e-5)
