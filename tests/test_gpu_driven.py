@@ -149,3 +149,60 @@ def test_sound_speed_against_alpha_fig1(lbm):
         assert abs(ci / li - 1) < tol, (ce, ci, li)
         if ce > 0.3:
             assert abs(ct / ce - 1) < 5e-4 and abs(ci / ce - 1) < 5e-4, (ce, ct, ci)
+
+
+def _driven_run(lbm, kind, ce, tau=0.53, amp=1e-4, period=500.0, nx=8192):
+    x1, D, t0, t1, every = driven_plan(ce, period)
+    with lbm.Grid(nx, 4, tau, ce * ce, kind.replace("-sr", "")) as g:
+        if kind.endswith("-sr"):
+            g.set_rounding("stochastic")
+        g.set_drive(amp, period)
+        g.init(np.ones((4, nx)), np.zeros((4, nx)), np.zeros((4, nx)))
+        g.step(t0)
+        ts, r1, r2, u1 = [], [], [], []
+        while g.t < t1:
+            r, u, _ = g.moments()
+            ts.append(g.t)
+            r1.append(r[:, x1].mean())
+            r2.append(r[:, x1 + D].mean())
+            u1.append(u[:, x1].mean())
+            g.step(every)
+        r, _, _ = g.moments()
+    c_tof, c_imp = driven_estimates(ts, r1, r2, u1, D, 2 * np.pi / period)
+    return c_tof, c_imp, r
+
+
+@pytest.mark.parametrize("kind", ["f16d-sr", "bf16d-sr"])
+def test_sound_speed_fig1_with_16bit_stochastic_storage(lbm, kind):
+    """The Fig. 1 measurement with 16-bit deviation storage and stochastic
+    rounding: both c_e estimates stay within 2e-3 of the driven-wave theory
+    at c_e = 0.2, 0.58 and 0.9 (the FP32 run agrees to 2e-4)."""
+    tau, period = 0.53, 500.0
+    for ce in (0.2, 0.5774, 0.9):
+        c_tof, c_imp, _ = _driven_run(lbm, kind, ce, tau)
+        lin = linear.driven_wave(2 * np.pi / period, tau, 1 / 3 - ce * ce)
+        print(f"{kind} c_e={ce}: tof {c_tof:.5f} imp {c_imp:.5f} theory {lin['c_phase']:.5f}")
+        assert abs(c_tof / lin["c_phase"] - 1) < 2e-3
+        assert abs(c_imp / abs(lin["impedance"]) - 1) < 2e-3
+
+
+def test_stochastic_rounding_seeds_transverse_growth_above_ce_1_08(lbm):
+    """Above c_e = 1.079 (tau = 0.53) the transverse mode k_y = pi/2 of the
+    4-row channel grows (linear analysis).  A deterministic rounding keeps the
+    run exactly y-uniform, so the mode is never seeded and FP16-D with nearest
+    rounding measures c_e = 1.1 like FP32; stochastic rounding dithers every
+    row differently, seeds it, and the rows drift apart."""
+    tau, ce, period = 0.53, 1.1, 500.0
+    alpha = 1 / 3 - ce * ce
+    ks = 2 * np.pi * np.arange(0, 4096, 8) / 4096
+    assert max(linear.spectral_radius(k, np.pi / 2, tau, alpha) for k in ks) > 1.005
+    assert max(linear.spectral_radius(k, 0.0, tau, alpha) for k in ks) <= 1 + 1e-12
+    lin = linear.driven_wave(2 * np.pi / period, tau, alpha)
+    c_tof, c_imp, r = _driven_run(lbm, "f16d", ce, tau)
+    assert all(np.array_equal(r[0], r[y]) for y in range(1, 4))
+    assert abs(c_tof / lin["c_phase"] - 1) < 2e-3
+    _, _, r_sr = _driven_run(lbm, "f16d-sr", ce, tau)
+    spread = np.abs(r_sr - r_sr.mean(axis=0)).max()
+    print(f"c_e = 1.1: nearest tof {c_tof:.5f} (theory {lin['c_phase']:.5f}); "
+          f"stochastic rounding row spread {spread:.2e}")
+    assert spread > 1e-6
