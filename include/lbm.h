@@ -57,7 +57,8 @@ extern "C" {
 /* Storage of the distributions in device memory.  Arithmetic is FP32 in all
  * cases.  Every storage keeps h_i = (f_i - w_i rho0) / w_i, the deviation from
  * the rest equilibrium scaled by the weight, so that small waves keep their
- * precision; the 16-bit kinds round h_i to nearest-even on every store. */
+ * precision; the 16-bit kinds round h_i on every store, to nearest-even or
+ * stochastically (lbm_set_rounding). */
 #define LBM_F32 0
 #define LBM_F16D 1
 #define LBM_BF16D 2
@@ -225,7 +226,11 @@ int lbm_get_pipeline(lbm_t h, int *stages, int *active);
  * stay deterministic and independent of the tile configuration and of
  * batching.  Stochastic rounding uses the register walks (vec 1, 2 or 4; it
  * moves a vec of 8 to 4 and turns the bulk-copy pipeline off).  FP32 storage
- * accepts only LBM_ROUND_NEAREST. */
+ * accepts only LBM_ROUND_NEAREST.  Because the dither differs from site to
+ * site, it breaks symmetries a deterministic rounding keeps exactly: above c2
+ * of about 1.16 (c_e > 1.08) a grid started uniform in y has transverse modes
+ * that grow (linear analysis), and the dither seeds them, so keep nearest
+ * rounding there. */
 int lbm_set_rounding(lbm_t h, int mode);
 int lbm_get_rounding(lbm_t h, int *mode);
 
