@@ -221,10 +221,10 @@ int lbm_get_pipeline(lbm_t h, int *stages, int *active);
  * slow processes freeze: the viscous decay of a shear wave of amplitude 1e-3
  * and wavelength 256 (tau = 0.9) stops completely in FP16 storage.
  * LBM_ROUND_STOCHASTIC rounds up with probability equal to the discarded
- * fraction (1/256 resolution), so each stored value is the FP32 result in
- * expectation; the random bits are a hash of (site, direction, step), so runs
- * stay deterministic and independent of the tile configuration and of
- * batching.  Stochastic rounding uses the register walks (vec 1, 2 or 4; it
+ * fraction (as many random bits as dropped bits: 13 for FP16, 16 for BF16),
+ * so each stored value is the FP32 result in expectation; the random bits are
+ * a hash of (pair of sites, direction, step), so runs stay deterministic and
+ * independent of the tile configuration and of batching.  Stochastic rounding uses the register walks (vec 1, 2 or 4; it
  * moves a vec of 8 to 4 and turns the bulk-copy pipeline off).  FP32 storage
  * accepts only LBM_ROUND_NEAREST.  Because the dither differs from site to
  * site, it breaks symmetries a deterministic rounding keeps exactly: above c2
@@ -292,9 +292,8 @@ int lbm_batch_get_config(lbm_batch_t b, int *rows, int *blocks_per_sm, int *spec
 int lbm_batch_get_groups(lbm_batch_t b, int *groups);
 
 /* The walk of 16-bit grids in a batch (results are bitwise the same for all):
- *   LBM_WALK16_AUTO    LBM_WALK16_V8 for grids with round-to-nearest stores,
- *                      LBM_WALK16_V4 for stochastic rounding (the faster of
- *                      the two for each on GB300); the default
+ *   LBM_WALK16_AUTO    the default: LBM_WALK16_V8, the faster on GB300 for
+ *                      both roundings
  *   LBM_WALK16_V8      8 sites per lane, 128-bit loads, when nx is a multiple
  *                      of 8 (else as LBM_WALK16_V4)
  *   LBM_WALK16_V4      4 sites per lane, 64-bit loads, one row of loads in

@@ -260,21 +260,26 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
     return x;
 }
 
-// Nine 8-bit dithers (one per direction) for a site and step, packed in 3 words.
-struct Dither {
-    uint32_t w0, w1, w2;
-    __device__ __forceinline__ uint32_t get(int i) const {
-        const uint32_t w = i < 4 ? w0 : (i < 8 ? w1 : w2);
-        return (w >> (8 * (i & 3))) & 0xffu;
-    }
-};
-__device__ __forceinline__ Dither site_dither(uint32_t site, uint32_t step) {
-    const uint32_t b = mix32(site ^ mix32(step * 0x9e3779b9u + 0x632be5abu));
-    Dither d;
-    d.w0 = b;
-    d.w1 = mix32(b + 0x85157af5u);
-    d.w2 = mix32(b + 0x3c6ef372u);
-    return d;
+// Random bits for stochastic rounding, from a counter-based hash of (pair of
+// sites, direction, step): one 32-bit word per direction for the sites 2p and
+// 2p+1 of the grid's row-major order (p = site >> 1); its low half rounds site
+// 2p and its high half site 2p+1.  The word depends on nothing else, so runs
+// are deterministic and independent of tile shape, sites per lane and
+// batching (with 2, 4 or 8 sites per lane nx is even, so the two sites of a
+// packed word are always such a pair; a 1-site lane takes its half).  The
+// pair hash is the full mix; the nine direction words use a lighter one.
+__device__ __forceinline__ uint32_t sr_step_key(uint32_t step) {
+    return mix32(step * 0x9e3779b9u + 0x632be5abu);
+}
+__device__ __forceinline__ uint32_t sr_pair_base(uint32_t site, uint32_t key) {
+    return mix32((site >> 1) ^ key);
+}
+__device__ __forceinline__ uint32_t sr_word(uint32_t base, int i) {
+    uint32_t x = base + (uint32_t)(i + 1) * 0x85ebca6bu;
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    return x;
 }
 
 // FP32 -> 16-bit with round up probability equal to the discarded fraction,
@@ -282,32 +287,9 @@ __device__ __forceinline__ Dither site_dither(uint32_t site, uint32_t step) {
 // .rs rounding): the conversion adds the caller's random bits to the bits
 // the 16-bit format drops and truncates (FP16 drops 13 bits and takes the low
 // 13 random bits of its half of rbits, BF16 drops 16 and takes all 16; the
-// low half of rbits rounds the low element).  The random bits here are an
-// 8-bit dither d per element placed as (d + 1/2)/256 of a unit in the last
-// kept place; the half step centres the 256 levels, so the rounding is
-// unbiased on average (without it the levels d/256 round up too often by
-// 1/512 unit, which slows the decay of slow modes).  One instruction
-// converts a pair of elements.
-template <int S>
-__device__ __forceinline__ uint32_t sr_bits(uint32_t d_lo, uint32_t d_hi) {
-    if constexpr (S == ST_F16)
-        return ((d_lo << 5) | 0x10u) | (((d_hi << 5) | 0x10u) << 16);
-    else
-        return ((d_lo << 8) | 0x80u) | (((d_hi << 8) | 0x80u) << 16);
-}
-
-// The same random bits for a pair of sites from their dither words: byte k
-// of `wa` (low element) and of `wb` (high element), in one byte permute.
-template <int S, int K>
-__device__ __forceinline__ uint32_t sr_bits_pair(uint32_t wa, uint32_t wb) {
-    constexpr uint32_t sel = K | (K << 4) | ((4 + K) << 8) | ((4 + K) << 12);
-    const uint32_t x = __byte_perm(wa, wb, sel);  // bytes: a_K, a_K, b_K, b_K
-    if constexpr (S == ST_F16)
-        return ((x & 0x00ff00ffu) << 5) | 0x00100010u;
-    else
-        return (x & 0xff00ff00u) | 0x00800080u;
-}
-
+// low half of rbits rounds the low element).  With as many random bits as
+// dropped bits the rounding is exactly unbiased.  One instruction converts a
+// pair of elements.
 template <int S>
 __device__ __forceinline__ uint32_t sr_pack2(float lo, float hi, uint32_t rbits) {
     uint32_t out;
@@ -318,10 +300,10 @@ __device__ __forceinline__ uint32_t sr_pack2(float lo, float hi, uint32_t rbits)
     return out;
 }
 
-// One element (in the low half of the result).
+// One element (in the low half of the result), with the 16 random bits `r`.
 template <int S>
-__device__ __forceinline__ uint32_t sr_round(float x, uint32_t d) {
-    return sr_pack2<S>(x, 0.0f, sr_bits<S>(d, 0u)) & 0xffffu;
+__device__ __forceinline__ uint32_t sr_round(float x, uint32_t r) {
+    return sr_pack2<S>(x, 0.0f, r & 0xffffu) & 0xffffu;
 }
 
 // Sites per packed word: the 16-bit kinds convert two sites at a time.
@@ -560,26 +542,17 @@ struct Walker {
             }
         } else {
             const uint32_t site = (uint32_t)r * (uint32_t)nx + (uint32_t)(xs + v0);
-            const Dither da = site_dither(site, rstep);
+            const uint32_t base = sr_pair_base(site, sr_step_key(rstep));
             if constexpr (SP == 2) {
-                const Dither db = site_dither(site + 1u, rstep);
+                // site is even: the word's two sites are the pair (site, site + 1)
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const uint32_t wa = i < 4 ? da.w0 : (i < 8 ? da.w1 : da.w2);
-                    const uint32_t wb = i < 4 ? db.w0 : (i < 8 ? db.w1 : db.w2);
-                    uint32_t rb;
-                    switch (i & 3) {
-                        case 0: rb = sr_bits_pair<S, 0>(wa, wb); break;
-                        case 1: rb = sr_bits_pair<S, 1>(wa, wb); break;
-                        case 2: rb = sr_bits_pair<S, 2>(wa, wb); break;
-                        default: rb = sr_bits_pair<S, 3>(wa, wb); break;
-                    }
-                    w[i][v0 >> 1] = sr_pack2<S>(h[0][i], h[1][i], rb);
-                }
+                for (int i = 0; i < 9; ++i)
+                    w[i][v0 >> 1] = sr_pack2<S>(h[0][i], h[1][i], sr_word(base, i));
             } else {
+                const uint32_t sh = (site & 1u) * 16u;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
-                    const uint32_t b = sr_round<S>(h[0][i], da.get(i));
+                    const uint32_t b = sr_round<S>(h[0][i], sr_word(base, i) >> sh);
                     if constexpr (V == 1)
                         w[i][0] = b;
                     else

@@ -365,9 +365,9 @@ class Batch:
                 "walk16": WALK16_NAMES[wk.value], "groups": ng.value}
 
     def set_walk16(self, walk: str):
-        """Walk of the batch's 16-bit grids: 'auto' (the default: 'v8' with
-        nearest rounding, 'v4' with stochastic rounding), 'v8' (8 sites per
-        lane), 'v4' (4 per lane, one row prefetched) or 'v4pf2' (two rows)."""
+        """Walk of the batch's 16-bit grids: 'auto' (the default, 'v8'), 'v8'
+        (8 sites per lane), 'v4' (4 per lane, one row prefetched) or 'v4pf2'
+        (two rows)."""
         _check(self.lib.lbm_batch_set_walk16(self.b, WALK16[walk]), "lbm_batch_set_walk16")
 
     def set_timeout_us(self, us: int):

@@ -172,18 +172,20 @@ def _driven_run(lbm, kind, ce, tau=0.53, amp=1e-4, period=500.0, nx=8192):
     return c_tof, c_imp, r
 
 
-@pytest.mark.parametrize("kind", ["f16d-sr", "bf16d-sr"])
-def test_sound_speed_fig1_with_16bit_stochastic_storage(lbm, kind):
+@pytest.mark.parametrize("kind,tol", [("f16d-sr", 2e-3), ("bf16d-sr", 5e-3)])
+def test_sound_speed_fig1_with_16bit_stochastic_storage(lbm, kind, tol):
     """The Fig. 1 measurement with 16-bit deviation storage and stochastic
-    rounding: both c_e estimates stay within 2e-3 of the driven-wave theory
-    at c_e = 0.2, 0.58 and 0.9 (the FP32 run agrees to 2e-4)."""
+    rounding: both c_e estimates stay within 2e-3 (FP16, 11-bit mantissa) and
+    5e-3 (BF16, 8-bit) of the driven-wave theory at c_e = 0.2, 0.58 and 0.9
+    (the FP32 run agrees to 2e-4).  The error is the rounding noise of the
+    format, a random quantity, hence bounds well above one realisation."""
     tau, period = 0.53, 500.0
     for ce in (0.2, 0.5774, 0.9):
         c_tof, c_imp, _ = _driven_run(lbm, kind, ce, tau)
         lin = linear.driven_wave(2 * np.pi / period, tau, 1 / 3 - ce * ce)
         print(f"{kind} c_e={ce}: tof {c_tof:.5f} imp {c_imp:.5f} theory {lin['c_phase']:.5f}")
-        assert abs(c_tof / lin["c_phase"] - 1) < 2e-3
-        assert abs(c_imp / abs(lin["impedance"]) - 1) < 2e-3
+        assert abs(c_tof / lin["c_phase"] - 1) < tol
+        assert abs(c_imp / abs(lin["impedance"]) - 1) < tol
 
 
 def test_stochastic_rounding_seeds_transverse_growth_above_ce_1_08(lbm):
