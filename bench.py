@@ -634,7 +634,7 @@ def main():
                     help="use the first N of the nine 2048^2 runs (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1000)
-    ap.add_argument("--e2e-jobs", type=int, default=1)
+    ap.add_argument("--e2e-jobs", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
