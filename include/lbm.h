@@ -274,7 +274,9 @@ int lbm_batch_sync(lbm_batch_t b);
 
 /* Tile height (rows per warp) and persistent-grid occupancy (0: as many
  * blocks per SM as fit) of the batch kernels; lbm_batch_tune picks the tile
- * height and the 16-bit walk from timed dry steps (the state is unchanged). */
+ * height and the 16-bit walk from timed dry steps (the grids' states and step
+ * counts are unchanged; on an error the previous configuration is restored
+ * and the error returned). */
 int lbm_batch_set_config(lbm_batch_t b, int rows, int blocks_per_sm);
 int lbm_batch_tune(lbm_batch_t b);
 /* Current tile height, resident blocks per SM of the first kind group, and

@@ -709,12 +709,10 @@ extern "C" int lbm_batch_set_timeout_us(lbm_batch_t b, long long us) {
 // grids, the 16-bit walks, each at its full occupancy; keeps the fastest.
 // A one-step launch does the same per-step work as a step inside a longer
 // launch (the barriers between steps cost microseconds per millisecond step).
-extern "C" int lbm_batch_tune(lbm_batch_t b) {
-    if (!b) return bfail(LBM_EINVAL, "lbm_batch_tune: NULL batch");
-    cudaEvent_t e0, e1;
-    BCK(cudaEventCreate(&e0));
-    BCK(cudaEventCreate(&e1));
-    int best_rows = b->rows, best_walk = b->walk16;
+// Times dry one-step runs of every (walk, tile height) candidate with the
+// events e0/e1 and leaves the fastest in *rows / *walk.
+static int tune_candidates(lbm_batch *b, cudaEvent_t e0, cudaEvent_t e1, int *rows,
+                           int *walk_out) {
     float best = 1e30f;
     const int rowss[] = {8, 12, 16, 24, 32};
     std::vector<std::vector<BatchKernel>> seen;
@@ -739,16 +737,36 @@ extern "C" int lbm_batch_tune(lbm_batch_t b) {
             BCK(cudaEventElapsedTime(&ms, e0, e1));
             if (ms < best) {
                 best = ms;
-                best_rows = r;
-                best_walk = walk;
+                *rows = r;
+                *walk_out = walk;
             }
         }
     }
+    return LBM_OK;
+}
+
+extern "C" int lbm_batch_tune(lbm_batch_t b) {
+    if (!b) return bfail(LBM_EINVAL, "lbm_batch_tune: NULL batch");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BCK(cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return bcuda(e, "cudaEventCreate");
+    }
+    const int rows0 = b->rows, walk0 = b->walk16, bps0 = b->blocks_per_sm;
+    int best_rows = rows0, best_walk = walk0;
+    int rc = tune_candidates(b, e0, e1, &best_rows, &best_walk);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    int rc = lbm_batch_set_walk16(b, best_walk);
-    if (rc != LBM_OK) return rc;
-    return lbm_batch_set_config(b, best_rows, 0);
+    if (rc != LBM_OK) {
+        // The configuration in force before the call is put back.
+        lbm_batch_set_walk16(b, walk0);
+        lbm_batch_set_config(b, rows0, bps0);
+        return rc;
+    }
+    rc = lbm_batch_set_walk16(b, best_walk);
+    return rc != LBM_OK ? rc : lbm_batch_set_config(b, best_rows, 0);
 }
 
 extern "C" int lbm_batch_get_config(lbm_batch_t b, int *rows, int *blocks_per_sm,

@@ -49,6 +49,10 @@ class ServeStats:
     lattice_updates: int = 0
     quanta: int = 0
     max_active: int = 0
+    # Host wall time by phase: grid creation and initial fields, batch
+    # (re)creation, step + wait for the quantum, retirement (results, frees).
+    phase_s: dict = field(default_factory=lambda: {"admit": 0.0, "batch": 0.0,
+                                                   "step": 0.0, "retire": 0.0})
 
     def summary(self) -> dict:
         lat = np.array([r.latency_s for r in self.results]) if self.results else np.zeros(1)
@@ -61,6 +65,7 @@ class ServeStats:
             "mlups": self.lattice_updates / self.makespan_s / 1e6 if self.makespan_s else 0.0,
             "quanta": self.quanta,
             "max_active": self.max_active,
+            "phase_s": dict(self.phase_s),
         }
 
 
@@ -100,8 +105,10 @@ class Server:
         def now():
             return time.perf_counter() - t0
 
+        ph = stats.phase_s
         while i < len(pending) or active:
             # Admit arrived requests while memory and slots allow.
+            ta = time.perf_counter()
             free, _ = lbm.mem_info()
             changed = False
             while i < len(pending) and len(active) < self.max_slots:
@@ -121,12 +128,14 @@ class Server:
                 free -= need
                 changed = True
                 i += 1
+            ph["admit"] += time.perf_counter() - ta
             if not active:
                 # Idle until the next arrival.
                 wait = pending[i].arrival_s - now()
                 if wait > 0:
                     time.sleep(min(wait, 0.05))
                 continue
+            tb = time.perf_counter()
             if changed or batch is None or members != [id(a[1]) for a in active]:
                 if batch is not None:
                     batch.close()
@@ -135,8 +144,12 @@ class Server:
             stats.max_active = max(stats.max_active, len(active))
             q = min(self.quantum, max(a[2] for a in active))
             limits = [min(q, a[2]) for a in active]
+            ts = time.perf_counter()
+            ph["batch"] += ts - tb
             batch.step(q, limits)
             batch.sync()
+            tr = time.perf_counter()
+            ph["step"] += tr - ts
             stats.quanta += 1
             for a, lim in zip(active, limits):
                 a[2] -= lim
@@ -159,6 +172,7 @@ class Server:
                 batch = None
                 members = None
             active = keep
+            ph["retire"] += time.perf_counter() - tr
         if batch is not None:
             batch.close()
         stats.makespan_s = now()

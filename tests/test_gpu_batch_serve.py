@@ -142,3 +142,38 @@ def test_kind_groups_equal_solo_runs(lbm):
     b.close()
     for g in grids:
         g.close()
+
+
+def test_batch_tune_leaves_state_and_results_unchanged(lbm):
+    """lbm_batch_tune times dry one-step runs over tile heights and 16-bit
+    walks: the grids' states and step counts are unchanged (so is the
+    stochastic-rounding stream, keyed by the step), the chosen
+    configuration is one of the candidates, and stepping afterwards gives the
+    same state bit for bit as an untuned batch."""
+    specs = [(512, 128, "f32"), (256, 96, "f16d"), (136, 40, "bf16d")]
+    out = {}
+    for tuned in (False, True):
+        grids = []
+        for nx, ny, st in specs:
+            g = lbm.Grid(nx, ny, 0.8, 0.2, st)
+            g.init(*workloads.fourier_modes(nx, ny, amp=1e-3, seed=nx))
+            if st == "bf16d":
+                g.set_rounding("stochastic")
+            grids.append(g)
+        b = lbm.Batch(grids)
+        if tuned:
+            before = [g.get_state() for g in grids]
+            cfg = b.tune()
+            assert cfg["rows"] in (8, 12, 16, 24, 32)
+            assert cfg["walk16"] in ("auto", "v8", "v4", "v4pf2")
+            for g, (s0, t0) in zip(grids, before):
+                s1, t1 = g.get_state()
+                assert t1 == t0 == 0 and np.array_equal(s0, s1)
+        b.step(25)
+        assert b.sync() == 0
+        out[tuned] = [g.get_state()[0] for g in grids]
+        b.close()
+        for g in grids:
+            g.close()
+    for a, c in zip(out[False], out[True]):
+        assert np.array_equal(a, c)
