@@ -36,7 +36,7 @@ METRIC = "MLUPS (million lattice updates per second), D2Q9 variable-speed-of-sou
 WORKLOAD = "2048x2048 periodic D2Q9, 9 runs c2=0.05..0.45, tau~U[0.55,1.5], acoustic+shear wave"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "batch_sweep2048_traffic.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_0707_2437_gb300", "csrc", f)
-                  for f in ("lbm_device.cuh", "lbm_kernels.cu", "lbm_batch.cu")]
+                  for f in ("lbm_device.cuh", "lbm_kernels.cu", "lbm_batch_kernels.cuh")]
 
 
 def kernel_source_hash() -> str:
@@ -143,24 +143,32 @@ def serve_comparison(args, stream=None):
     from paper_0707_2437_gb300 import serve
     trace = serve.scaled_trace(args.serve_count, args.serve_rate,
                                steps_hi=args.serve_steps_hi)
+    overlap = not args.serve_no_overlap
+
+    def server():
+        return serve.Server(quantum=args.serve_quantum, overlap=overlap)
+
     warm = serve.scaled_trace(8, 1000.0, seed=99, hi=256, steps_hi=2000)
-    serve.Server(quantum=args.serve_quantum).run(warm, realtime=False)
-    srv = serve.Server(quantum=args.serve_quantum).run(trace, realtime=True).summary()
-    fifo = serve.serve_fifo(trace, realtime=True).summary()
+    server().run(warm, realtime=False)
+    srv = server().run(trace, realtime=True).summary()
     out = {"trace": f"{args.serve_count} requests, Poisson {args.serve_rate}/s, sites "
                     f"log-uniform 128^2..2048^2, steps U{{1000..{args.serve_steps_hi}}}, "
                     "half f32 / half f16d",
-           "continuous_batching": srv, "fifo_f32": fifo,
-           "p99_speedup": fifo["p99_s"] / srv["p99_s"] if srv["p99_s"] else None,
-           "mlups_ratio": srv["mlups"] / fifo["mlups"] if fifo["mlups"] else None}
+           "admission": "overlapped with the running quantum" if overlap else "between quanta",
+           "continuous_batching": srv, "fifo_f32": None}
+    if not args.serve_skip_fifo:
+        fifo = serve.serve_fifo(trace, realtime=True).summary()
+        out.update({"fifo_f32": fifo,
+                    "p99_speedup": fifo["p99_s"] / srv["p99_s"] if srv["p99_s"] else None,
+                    "mlups_ratio": srv["mlups"] / fifo["mlups"] if fifo["mlups"] else None})
     # The same requests at 0.7 x the server's measured capacity (lattice
     # updates per second over the mean lattice updates of a request).
     mean_lu = float(np.mean([r.nx * r.ny * r.steps for r in trace]))
     rate07 = 0.7 * srv["mlups"] * 1e6 / mean_lu
     trace07 = serve.scaled_trace(args.serve_count, rate07, steps_hi=args.serve_steps_hi)
-    srv07 = serve.Server(quantum=args.serve_quantum).run(trace07, realtime=True).summary()
+    srv07 = server().run(trace07, realtime=True).summary()
     out["at_0.7_capacity"] = {"rate_hz": rate07, "continuous_batching": srv07}
-    if not args.serve_no_fifo07:
+    if not (args.serve_no_fifo07 or args.serve_skip_fifo):
         fifo07 = serve.serve_fifo(trace07, realtime=True).summary()
         out["at_0.7_capacity"]["fifo_f32"] = fifo07
         out["at_0.7_capacity"]["p99_speedup"] = (fifo07["p99_s"] / srv07["p99_s"]
@@ -619,6 +627,10 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-steps-hi", type=int, default=5000)
     ap.add_argument("--serve-quantum", type=int, default=256)
+    ap.add_argument("--serve-no-overlap", action="store_true",
+                    help="admit requests between quanta instead of during them")
+    ap.add_argument("--serve-skip-fifo", action="store_true",
+                    help="skip the FIFO baseline at both rates")
     ap.add_argument("--serve-no-fifo07", action="store_true",
                     help="skip the FIFO baseline at 0.7x the server's capacity (long traces)")
     ap.add_argument("--config", type=int, nargs=3, default=None,

@@ -30,9 +30,9 @@
  * most recent failure (for example the CUDA error string).
  *
  * Streams: work is queued on the handle's CUDA stream (the one passed to
- * lbm_create, or the legacy default stream if NULL).  lbm_step only queues
- * work; lbm_moments, lbm_sums, lbm_mode, lbm_get_state and lbm_sync wait for
- * the stream.
+ * lbm_create or lbm_set_stream, or the legacy default stream if NULL).
+ * lbm_step only queues work; lbm_moments, lbm_sums, lbm_mode, lbm_get_state
+ * and lbm_sync wait for the stream.
  */
 #ifndef LBM_H
 #define LBM_H
@@ -102,7 +102,10 @@ int lbm_destroy(lbm_t h);
  * (Eq. 2) of the given fields (the paper gives rho and u only).
  *   rho, ux, uy  [ny][nx] doubles, rho > 0; host pointers if on_device == 0,
  *                device pointers otherwise
- * Resets the step counter to 0.  Returns after the fields have been read. */
+ * Resets the step counter to 0.  Returns after the fields have been read:
+ * host fields once they are copied to the device (the initialisation kernel
+ * may still be queued on the stream behind other work), device fields once
+ * the kernel has run. */
 int lbm_init(lbm_t h, const double *rho, const double *ux, const double *uy,
              int on_device);
 
@@ -181,6 +184,15 @@ long long lbm_time(lbm_t h);
 /* Waits for all work queued on the handle's stream. */
 int lbm_sync(lbm_t h);
 
+/* Moves the handle to another stream (NULL: the legacy default stream).
+ * Work queued on it afterwards runs on `cuda_stream`, after the work already
+ * queued on the old stream (an event wait; the host does not block).  If a
+ * long lbm_step call has run as a persistent launch, that launch is waited
+ * for and its status returned first (LBM_ETIMEOUT leaves the stream
+ * unchanged).  Typical use: initialise a grid on a side stream while other
+ * work runs, then move it onto the stream of the batch it joins. */
+int lbm_set_stream(lbm_t h, void *cuda_stream);
+
 /* Bytes of device state (both distribution buffers) a grid of this size and
  * storage needs; 0 for invalid arguments. */
 size_t lbm_bytes_required(int nx, int ny, int storage);
@@ -254,7 +266,11 @@ int lbm_kernel_ms(lbm_t h, double *ms, long long *launches);
  * (one launch per kind group, see lbm_batch_get_groups).  Every grid reaches
  * bitwise the state it reaches when stepped alone.  The batch refers to the
  * handles; they must outlive it and must not be stepped individually while
- * it is being stepped.  The batch's work runs on the stream of grids[0].
+ * it is being stepped.  The batch's work runs on the stream grids[0] had
+ * when the batch was created.  Each step call first makes it wait for the
+ * work queued on every member's current stream, and then makes those streams
+ * wait for the batch's work, so calls on a member's own stream stay ordered
+ * with the batch.
  * Grids with a c2 field may join; driven grids are refused (LBM_EINVAL). */
 int lbm_batch_create(const lbm_t *grids, int n, lbm_batch_t *out);
 int lbm_batch_destroy(lbm_batch_t b);

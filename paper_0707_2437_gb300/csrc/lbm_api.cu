@@ -176,11 +176,14 @@ extern "C" int lbm_create_ex(int nx, int ny, double tau, double c2, double rho0,
     if (e == cudaSuccess) e = cudaMalloc(&h->buf[0], bytes);
     if (e == cudaSuccess) e = cudaMalloc(&h->buf[1], bytes);
     if (e == cudaSuccess) e = cudaMalloc(&h->scratch, sizeof(double) * (3 * 1024 + 16));
-    if (e == cudaSuccess) e = cudaMemset(h->scratch, 0, sizeof(double) * 16);
+    // Stream-ordered, so that creating a grid does not wait for work running
+    // on the legacy default stream.
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->scratch, 0, sizeof(double) * 16, h->stream);
     if (e == cudaSuccess) e = prepare_step(storage, h->cfg);
     if (e == cudaSuccess) e = cudaMallocHost(&h->host_out, sizeof(double) * 8);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev[1]);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->staged, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         int rc = cuda_fail(e, "lbm_create");
         lbm_destroy(h);
@@ -205,6 +208,7 @@ extern "C" int lbm_destroy(lbm_t h) {
         if (h->buf[k]) cudaFree(h->buf[k]);
         if (h->ev[k]) cudaEventDestroy(h->ev[k]);
     }
+    if (h->staged) cudaEventDestroy(h->staged);
     if (h->scratch) cudaFree(h->scratch);
     if (h->a15f) cudaFree(h->a15f);
     if (h->host_out) cudaFreeHost(h->host_out);
@@ -236,6 +240,10 @@ extern "C" int lbm_init(lbm_t h, const double *rho, const double *ux, const doub
     int rc = stage_field(h, rho, on_device, &dr, owned);
     if (rc == LBM_OK) rc = stage_field(h, ux, on_device, &du, owned);
     if (rc == LBM_OK) rc = stage_field(h, uy, on_device, &dv, owned);
+    if (rc == LBM_OK && !on_device) {
+        cudaError_t e = cudaEventRecord(h->staged, h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "lbm_init");
+    }
     if (rc == LBM_OK) {
         cudaError_t e = launch_init(h->storage, h->buf[0], h->nx, h->ny, h->P, h->rho0, dr, du, dv,
                                     h->stream);
@@ -245,7 +253,13 @@ extern "C" int lbm_init(lbm_t h, const double *rho, const double *ux, const doub
     if (rc != LBM_OK) return rc;
     h->cur = 0;
     h->t = 0;
-    CK(cudaStreamSynchronize(h->stream));
+    // Host fields: wait only until the copies have read them (the kernel
+    // stays queued, so the call does not wait for work ahead of it on the
+    // device).  Device fields: wait until the kernel has read them.
+    if (on_device)
+        CK(cudaStreamSynchronize(h->stream));
+    else
+        CK(cudaEventSynchronize(h->staged));
     return LBM_OK;
 }
 
@@ -453,6 +467,27 @@ extern "C" int lbm_mode(lbm_t h, int field, int kx, int ky, double *out2) {
 }
 
 extern "C" long long lbm_time(lbm_t h) { return h ? h->t : -1; }
+
+extern "C" int lbm_set_stream(lbm_t h, void *cuda_stream) {
+    if (!h) return fail(LBM_EINVAL, "lbm_set_stream: NULL handle");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (s == h->stream) return LBM_OK;
+    if (h->self_batch) {
+        // The grid's persistent batch runs on the old stream: its status is
+        // taken and it is rebuilt on the new stream at the next long call.
+        int rb = lbm_batch_sync(h->self_batch);
+        if (rb != LBM_OK) return rb;
+        drop_self_batch(h);
+    }
+    cudaEvent_t ev = nullptr;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
+    cudaEventDestroy(ev);  // released once recorded work completes
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_set_stream");
+    h->stream = s;
+    return LBM_OK;
+}
 
 extern "C" int lbm_sync(lbm_t h) {
     if (!h) return fail(LBM_EINVAL, "lbm_sync: NULL handle");

@@ -126,4 +126,5 @@ struct lbm_grid {
     double kernel_ms = 0;
     long long kernel_launches = 0;
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaEvent_t staged = nullptr;  // lbm_init: host fields copied
 };

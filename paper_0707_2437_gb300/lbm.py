@@ -58,6 +58,7 @@ def load() -> ctypes.CDLL:
             "lbm_mode": ([vp, i, i, i, dp], i),
             "lbm_time": ([vp], ll),
             "lbm_sync": ([vp], i),
+            "lbm_set_stream": ([vp, vp], i),
             "lbm_bytes_required": ([i, i, i], sz),
             "lbm_mem_info": ([ctypes.POINTER(sz), ctypes.POINTER(sz)], i),
             "lbm_state_bytes": ([vp], sz),
@@ -122,6 +123,21 @@ def _ptr(a):
     return a.ctypes.data, 0, a
 
 
+def _stream_handle(stream) -> int:
+    """cudaStream_t value of None, an integer handle or a torch.cuda.Stream."""
+    if stream is None:
+        return 0
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def new_stream():
+    """A new CUDA stream that does not synchronise with the legacy default
+    stream (PyTorch's stream pool creates them non-blocking); pass it, or its
+    ``cuda_stream`` handle, as a ``stream`` argument and keep it alive."""
+    import torch  # streams only
+    return torch.cuda.Stream()
+
+
 def mem_info():
     lib = load()
     f, t = ctypes.c_size_t(), ctypes.c_size_t()
@@ -141,7 +157,7 @@ def sums_noalloc(f_dev_ptr: int, nx: int, ny: int, plane_stride: int, storage: s
     out = np.zeros(3)
     _check(lib.lbm_sums_noalloc(ctypes.c_void_p(int(f_dev_ptr)), nx, ny, plane_stride,
                                 STORAGE[storage], rho0,
-                                ctypes.c_void_p(int(stream) if stream is not None else 0),
+                                ctypes.c_void_p(_stream_handle(stream)),
                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
            "lbm_sums_noalloc")
     return out
@@ -158,7 +174,7 @@ class Grid:
         self.rho0 = rho0
         self._stream = stream
         h = ctypes.c_void_p()
-        st = ctypes.c_void_p(int(stream) if stream is not None else 0)
+        st = ctypes.c_void_p(_stream_handle(stream))
         self.status = _check(self.lib.lbm_create_ex(nx, ny, tau, c2, rho0, STORAGE[storage], st,
                                                      ctypes.byref(h)), "lbm_create")
         self.h = h
@@ -229,6 +245,13 @@ class Grid:
 
     def sync(self):
         _check(self.lib.lbm_sync(self.h), "lbm_sync")
+
+    def set_stream(self, stream):
+        """Moves the grid to `stream` (None: the legacy default stream); work
+        queued later runs there, after the work already queued."""
+        _check(self.lib.lbm_set_stream(self.h, ctypes.c_void_p(_stream_handle(stream))),
+               "lbm_set_stream")
+        self._stream = stream
 
     def get_state(self):
         n = int(self.lib.lbm_state_bytes(self.h))

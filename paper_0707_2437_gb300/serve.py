@@ -49,8 +49,9 @@ class ServeStats:
     lattice_updates: int = 0
     quanta: int = 0
     max_active: int = 0
-    # Host wall time by phase: grid creation and initial fields, batch
-    # (re)creation, step + wait for the quantum, retirement (results, frees).
+    # Host wall time by phase: grid creation and initial fields ("admit"),
+    # batch (re)creation and queueing the quantum ("batch"), waiting for the
+    # quantum to finish ("step"), retirement: results and frees ("retire").
     phase_s: dict = field(default_factory=lambda: {"admit": 0.0, "batch": 0.0,
                                                    "step": 0.0, "retire": 0.0})
 
@@ -75,15 +76,26 @@ def _fields(req: workloads.Request):
 
 
 class Server:
-    """Continuous batching over the batch API."""
+    """Continuous batching over the batch API.
+
+    With ``overlap=True`` (the default) the batch runs on a stream of its own
+    and arriving requests are admitted while a quantum runs: their grids are
+    created and initialised on side streams (host field set-up and copies
+    overlap the kernel; lbm_init returns once host fields are copied), then
+    moved onto the batch's stream (lbm_set_stream), and join the batch at the
+    next quantum.  With ``overlap=False`` admission
+    happens between quanta, on ``stream``."""
 
     def __init__(self, quantum: int = 256, reserve_bytes: int = 4 << 30,
-                 max_slots: int = 512, keep_fields: bool = False, stream=None):
+                 max_slots: int = 512, keep_fields: bool = False, stream=None,
+                 overlap: bool = True, side_streams: int = 8):
         self.quantum = quantum
         self.reserve = reserve_bytes
         self.max_slots = max_slots
         self.keep_fields = keep_fields
         self.stream = stream
+        self.overlap = overlap
+        self.side_streams = side_streams
         lbm.load()
 
     def _need(self, req) -> int:
@@ -95,84 +107,108 @@ class Server:
         follow the wall clock from the start of the call; otherwise every
         request is present at time 0."""
         pending = sorted(requests, key=lambda r: r.arrival_s)
-        active = []  # (req, grid, remaining, admitted_s)
+        active = []  # [req, grid, remaining, admitted_s]
         stats = ServeStats()
+        ph = stats.phase_s
         batch = None
         members = None
+        main, sides = self.stream, [self.stream]
+        if self.overlap:
+            # Each admission initialises on the next of a few side streams, so
+            # that its copies do not queue behind the previous admission's
+            # initialisation kernel (which waits for the quantum's SMs).
+            main = self.stream if self.stream is not None else lbm.new_stream()
+            sides = [lbm.new_stream() for _ in range(self.side_streams)]
+        n_admitted = 0
         t0 = time.perf_counter()
         i = 0
 
         def now():
             return time.perf_counter() - t0
 
-        ph = stats.phase_s
-        while i < len(pending) or active:
-            # Admit arrived requests while memory and slots allow.
+        def admit(incoming):
+            # Admit arrived requests, in order, while memory and slots allow.
+            nonlocal i, n_admitted
             ta = time.perf_counter()
             free, _ = lbm.mem_info()
-            changed = False
-            while i < len(pending) and len(active) < self.max_slots:
+            while i < len(pending) and len(active) + len(incoming) < self.max_slots:
                 req = pending[i]
                 if realtime and req.arrival_s > now():
                     break
                 need = self._need(req)
                 if need > free - self.reserve:
-                    if not active:
+                    if not active and not incoming:
                         raise MemoryError(f"request {req.rid} needs {need} bytes, "
                                           f"{free} free")
                     break
-                g = lbm.Grid(req.nx, req.ny, req.tau, req.c2, req.storage,
-                             stream=self.stream)
+                side = sides[n_admitted % len(sides)]
+                n_admitted += 1
+                g = lbm.Grid(req.nx, req.ny, req.tau, req.c2, req.storage, stream=side)
                 g.init(*_fields(req))
-                active.append([req, g, req.steps, now()])
+                if side is not main:
+                    g.set_stream(main)
+                incoming.append([req, g, req.steps, now()])
                 free -= need
-                changed = True
                 i += 1
             ph["admit"] += time.perf_counter() - ta
-            if not active:
+
+        while i < len(pending) or active:
+            incoming = []
+            if not self.overlap:
+                admit(incoming)
+                active += incoming
+                incoming = []
+            # Queue one quantum for the resident grids (asynchronous).
+            limits = None
+            if active:
+                tb = time.perf_counter()
+                if batch is None or members != [id(a[1]) for a in active]:
+                    if batch is not None:
+                        batch.close()
+                    batch = lbm.Batch([a[1] for a in active])
+                    members = [id(a[1]) for a in active]
+                stats.max_active = max(stats.max_active, len(active))
+                q = min(self.quantum, max(a[2] for a in active))
+                limits = [min(q, a[2]) for a in active]
+                batch.step(q, limits)
+                ph["batch"] += time.perf_counter() - tb
+            if self.overlap:
+                admit(incoming)  # while the quantum is on the GPU
+
+            if limits is not None:
+                ts = time.perf_counter()
+                batch.sync()
+                tr = time.perf_counter()
+                ph["step"] += tr - ts
+                stats.quanta += 1
+                for a, lim in zip(active, limits):
+                    a[2] -= lim
+                    stats.lattice_updates += lim * a[0].nx * a[0].ny
+                keep = []
+                for a in active:
+                    req, g, rem, adm = a
+                    if rem > 0:
+                        keep.append(a)
+                        continue
+                    fields = g.moments() if self.keep_fields else None
+                    if not self.keep_fields:
+                        g.sync()
+                    arrival = req.arrival_s if realtime else 0.0
+                    stats.results.append(Result(req.rid, arrival, adm, now(), req.steps,
+                                                req.nx * req.ny, req.storage, fields))
+                    g.close()
+                if len(keep) != len(active):
+                    batch.close()
+                    batch = None
+                    members = None
+                active = keep
+                ph["retire"] += time.perf_counter() - tr
+            active += incoming
+            if not active and i < len(pending):
                 # Idle until the next arrival.
                 wait = pending[i].arrival_s - now()
                 if wait > 0:
                     time.sleep(min(wait, 0.05))
-                continue
-            tb = time.perf_counter()
-            if changed or batch is None or members != [id(a[1]) for a in active]:
-                if batch is not None:
-                    batch.close()
-                batch = lbm.Batch([a[1] for a in active])
-                members = [id(a[1]) for a in active]
-            stats.max_active = max(stats.max_active, len(active))
-            q = min(self.quantum, max(a[2] for a in active))
-            limits = [min(q, a[2]) for a in active]
-            ts = time.perf_counter()
-            ph["batch"] += ts - tb
-            batch.step(q, limits)
-            batch.sync()
-            tr = time.perf_counter()
-            ph["step"] += tr - ts
-            stats.quanta += 1
-            for a, lim in zip(active, limits):
-                a[2] -= lim
-                stats.lattice_updates += lim * a[0].nx * a[0].ny
-            keep = []
-            for a in active:
-                req, g, rem, adm = a
-                if rem > 0:
-                    keep.append(a)
-                    continue
-                fields = g.moments() if self.keep_fields else None
-                if not self.keep_fields:
-                    g.sync()
-                arrival = req.arrival_s if realtime else 0.0
-                stats.results.append(Result(req.rid, arrival, adm, now(), req.steps,
-                                            req.nx * req.ny, req.storage, fields))
-                g.close()
-            if len(keep) != len(active):
-                batch.close()
-                batch = None
-                members = None
-            active = keep
-            ph["retire"] += time.perf_counter() - tr
         if batch is not None:
             batch.close()
         stats.makespan_s = now()

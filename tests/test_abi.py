@@ -85,6 +85,7 @@ def test_every_handle_call_rejects_null_before_device_work():
         lambda: lib.lbm_set_drive(None, 1, 1e-3, 500.0),
         lambda: lib.lbm_set_c2_field(None, None, 0),
         lambda: lib.lbm_sync(None),
+        lambda: lib.lbm_set_stream(None, None),
         lambda: lib.lbm_get_state(None, buf, ctypes.byref(ll)),
         lambda: lib.lbm_set_state(None, buf, 0),
         lambda: lib.lbm_set_config(None, 4, 16, 4),

@@ -21,9 +21,11 @@ def _trace():
             for k, (nx, ny, st, steps) in enumerate(specs)]
 
 
-def test_served_results_equal_solo_runs(lbm):
+@pytest.mark.parametrize("overlap", [True, False])
+def test_served_results_equal_solo_runs(lbm, overlap):
     reqs = _trace()
-    srv = serve.Server(quantum=48, max_slots=3, keep_fields=True, reserve_bytes=0)
+    srv = serve.Server(quantum=48, max_slots=3, keep_fields=True, reserve_bytes=0,
+                       overlap=overlap)
     stats = srv.run(reqs, realtime=False)
     assert len(stats.results) == len(reqs)
     assert stats.max_active == 3
@@ -177,3 +179,54 @@ def test_batch_tune_leaves_state_and_results_unchanged(lbm):
             g.close()
     for a, c in zip(out[False], out[True]):
         assert np.array_equal(a, c)
+
+
+def test_batch_orders_with_members_streams(lbm):
+    """Grids initialised on streams of their own are batched on another
+    stream: the batch waits for their initialisation, and moments read on a
+    member's own stream right after the step call (no batch sync) see the
+    batch's result.  The heavy first grid keeps the batch's stream busy, so
+    a missing wait would show."""
+    specs = [(2048, 1024, "f32"), (256, 96, "f16d"), (192, 64, "f32")]
+    streams = [lbm.new_stream() for _ in specs]
+    grids, solo = [], []
+    for (nx, ny, st), s in zip(specs, streams):
+        fields = workloads.fourier_modes(nx, ny, amp=1e-3, seed=nx + ny)
+        with lbm.Grid(nx, ny, 0.7, 0.25, st) as g:
+            g.init(*fields)
+            g.step(40)
+            solo.append(g.moments())
+        g = lbm.Grid(nx, ny, 0.7, 0.25, st, stream=s)
+        g.init(*fields)
+        grids.append(g)
+    b = lbm.Batch(grids)
+    b.step(40)
+    got = [g.moments() for g in grids[::-1]]
+    for a, c in zip(got[::-1], solo):
+        for x, y in zip(a, c):
+            assert np.array_equal(x, y)
+    assert b.sync() == 0
+    b.close()
+    for g in grids:
+        g.close()
+
+
+def test_set_stream_keeps_order(lbm):
+    """A grid initialised on one stream and moved to another steps from its
+    initial state; moving it again between step calls changes nothing."""
+    nx, ny = 1024, 512
+    fields = workloads.fourier_modes(nx, ny, amp=1e-3, seed=5)
+    with lbm.Grid(nx, ny, 0.8, 0.2, "f16d") as g:
+        g.init(*fields)
+        g.step(300)
+        ref = g.moments()
+    s1, s2 = lbm.new_stream(), lbm.new_stream()
+    with lbm.Grid(nx, ny, 0.8, 0.2, "f16d", stream=s1) as g:
+        g.init(*fields)
+        g.set_stream(s2)
+        g.step(100)            # persistent launch on s2
+        g.set_stream(s1)       # waits for it, drops the persistent batch
+        g.step(200)
+        got = g.moments()
+    for x, y in zip(got, ref):
+        assert np.array_equal(x, y)

@@ -15,6 +15,8 @@ class _FakeDevice:
         self.max_live = 0
         self.max_used = 0
         self.created = []
+        self.in_flight = None    # the batch whose quantum is queued, until sync
+        self.streams = 0
 
     # the subset of the lbm module the server uses
     def load(self):
@@ -31,6 +33,11 @@ def _fake_lbm(dev):
     class Grid:
         def __init__(self, nx, ny, tau, c2, storage="f32", stream=None):
             self.nx, self.ny, self.storage = nx, ny, storage
+            self.stream = stream
+            # A grid made while a quantum runs must not be on that quantum's stream.
+            self.made_in_flight = dev.in_flight is not None
+            if self.made_in_flight:
+                assert stream is not dev.in_flight.stream
             self.bytes = dev.bytes_required(nx, ny, storage)
             dev.used += self.bytes
             dev.max_used = max(dev.max_used, dev.used)
@@ -45,7 +52,11 @@ def _fake_lbm(dev):
             assert rho.shape == (self.ny, self.nx)
 
         def moments(self):
+            assert dev.in_flight is None
             return (None, None, None)
+
+        def set_stream(self, stream):
+            self.stream = stream
 
         def sync(self):
             pass
@@ -60,15 +71,21 @@ def _fake_lbm(dev):
     class Batch:
         def __init__(self, grids):
             assert all(not g.closed for g in grids)
+            assert dev.in_flight is None
             self.grids = list(grids)
+            self.stream = self.grids[0].stream
+            assert all(g.stream is self.stream for g in self.grids)
 
         def step(self, n, limits=None):
+            assert dev.in_flight is None
             limits = limits or [n] * len(self.grids)
             for g, lim in zip(self.grids, limits):
                 assert 0 <= lim <= n
                 g.t += lim
+            dev.in_flight = self
 
         def sync(self):
+            dev.in_flight = None
             return 0
 
         def close(self):
@@ -77,6 +94,12 @@ def _fake_lbm(dev):
     ns = type("FakeLbm", (), {})()
     ns.load, ns.mem_info, ns.bytes_required = dev.load, dev.mem_info, dev.bytes_required
     ns.Grid, ns.Batch = Grid, Batch
+
+    def new_stream():
+        dev.streams += 1
+        return object()
+
+    ns.new_stream = new_stream
     return ns
 
 
@@ -143,3 +166,22 @@ def test_summary_percentiles():
     assert s["requests"] == 100
     assert abs(s["p50_s"] - 50.5) < 1e-9 and 98.9 < s["p99_s"] < 99.1
     assert s["mlups"] == pytest.approx(1e-5)
+
+
+@pytest.mark.parametrize("overlap", [True, False])
+def test_admission_overlaps_the_running_quantum(monkeypatch, overlap):
+    """With overlap, requests that arrive while a quantum runs are created on
+    a side stream during it and moved onto the batch's stream before they
+    join; every batch holds grids of one stream.  Without overlap nothing is
+    created while a quantum is queued."""
+    dev = _FakeDevice(total=1 << 40)
+    monkeypatch.setattr(serve, "lbm", _fake_lbm(dev))
+    reqs = _requests(n=12)
+    srv = serve.Server(quantum=64, reserve_bytes=0, max_slots=4, overlap=overlap)
+    stats = srv.run(reqs, realtime=False)
+    assert len(stats.results) == len(reqs) and dev.live == 0
+    made = [g.made_in_flight for g in dev.created]
+    assert any(made) == overlap
+    assert dev.streams == (1 + srv.side_streams if overlap else 0)
+    for q, g in zip(reqs, dev.created):
+        assert g.steps_at_close == q.steps
