@@ -433,6 +433,30 @@ def run_native(args):
     e2e_s = max_over_ranks(ws, time.perf_counter() - t0)
     e2e_value = (ws * sites * args.e2e_steps * args.e2e_jobs / e2e_s / 1e6
                  if args.e2e_jobs else None)
+    # One more job, outside the timed region, with a synchronisation after
+    # each phase: where a job's time goes.
+    e2e_phases = None
+    if args.e2e_jobs:
+        ta = time.perf_counter()
+        for g, hin in zip(grids, host_in):
+            g.init(*[t.numpy() for t in hin])
+        for g in grids:
+            g.sync()
+        tb = time.perf_counter()
+        if batch is not None:
+            batch.step(args.e2e_steps)
+            batch.sync()
+        else:
+            for g in grids:
+                g.step(args.e2e_steps)
+            for g in grids:
+                g.sync()
+        tc = time.perf_counter()
+        for g, hout in zip(grids, host_out):
+            g.moments(out=[t.numpy() for t in hout])
+        td = time.perf_counter()
+        e2e_phases = {"init_ms": 1e3 * (tb - ta), "steps_ms": 1e3 * (tc - tb),
+                      "moments_ms": 1e3 * (td - tc)}
 
     line = {
         "metric": METRIC,
@@ -480,7 +504,7 @@ def run_native(args):
                 "step": f"one job: lbm_init from pinned host fields, {args.e2e_steps} steps "
                         f"({'one batch launch' if batch is not None else 'lbm_step per grid'}), "
                         f"lbm_moments to host, for all {len(runs)} grids",
-                "jobs": args.e2e_jobs},
+                "jobs": args.e2e_jobs, "phases_of_one_more_job": e2e_phases},
         "gpu_launches": n_launch * (2 if args.drive is not None else 1),
         "clocks": clk,
         "single_grid_kernel": single,

@@ -197,7 +197,11 @@ int lbm_set_stream(lbm_t h, void *cuda_stream);
  * storage needs; 0 for invalid arguments. */
 size_t lbm_bytes_required(int nx, int ny, int storage);
 
-/* Free and total device memory (cudaMemGetInfo) of the current device. */
+/* Free and total device memory (cudaMemGetInfo) of the current device.
+ * Host fields passed to lbm_init and lbm_moments are staged in device memory
+ * from a pool owned by the library (one per device) that keeps up to 1 GiB
+ * reserved between calls; that reservation counts as used here.  lbm_create
+ * releases it and retries when a grid's buffers do not fit otherwise. */
 int lbm_mem_info(size_t *free_bytes, size_t *total_bytes);
 
 /* Checkpoint: the raw stored distributions (9 planes of nx*ny elements of the

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <fstream>
 #include <map>
+#include <mutex>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -101,18 +102,23 @@ static int *status_ptr(lbm_grid *h) { return reinterpret_cast<int *>(h->scratch 
 // Device step counter that seeds stochastic rounding inside graph replays.
 static uint32_t *step_ptr(lbm_grid *h) { return reinterpret_cast<uint32_t *>(h->scratch + 9); }
 
-// Reads and clears the status word (the stream must be idle), and the status
-// of the grid's own persistent batch, if any.
-static int take_status(lbm_grid *h) {
+// Waits for the grid's stream once and returns the status of the work on it:
+// the copies of the step kernels' status word and of the grid's own
+// persistent batch's status word to pinned host memory are queued first, so
+// one synchronisation serves the caller's results and the status.  A set
+// status word is cleared (stream-ordered) and returned as the error.
+static int sync_status(lbm_grid *h) {
+    int *hs = reinterpret_cast<int *>(h->host_out + 7);
+    CK(cudaMemcpyAsync(hs, status_ptr(h), sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    if (h->self_batch) CK(batch_queue_status(h->self_batch, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     if (h->self_batch) {
-        int rb = lbm_batch_sync(h->self_batch);
-        if (rb != LBM_OK) return rb;
+        int rb = batch_status(h->self_batch);
+        if (rb != LBM_OK) return fail(rb, "a barrier wait in the persistent step kernel ran out");
     }
-    int st = 0;
-    cudaError_t e = cudaMemcpy(&st, status_ptr(h), sizeof(int), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(e, "status read");
-    if (st != 0) {
-        cudaMemset(status_ptr(h), 0, sizeof(int));
+    if (*hs != 0) {
+        int st = *hs;
+        cudaMemsetAsync(status_ptr(h), 0, sizeof(int), h->stream);
         return fail(st, "a bounded wait in the step kernel ran out");
     }
     return LBM_OK;
@@ -132,6 +138,54 @@ static void drop_graphs(lbm_grid *h) {
             h->graph[k] = nullptr;
         }
     h->graph_pairs = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Staging memory for host fields (lbm_init) and host moments (lbm_moments).
+// It comes from a pool owned by the library, one per device, that keeps up
+// to kStagingKeep bytes reserved across synchronisations.  The default pool
+// returns freed memory to the system at every synchronisation, and mapping it
+// again on the next call costs more than the copies it serves.  When a grid's
+// buffers do not fit, the pool is trimmed and the allocation retried.
+
+static constexpr unsigned long long kStagingKeep = 1ull << 30;
+static std::mutex g_pool_mu;
+static std::map<int, cudaMemPool_t> g_pools;
+
+static cudaError_t staging_alloc(lbm_grid *h, double **p, size_t bytes) {
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        auto it = g_pools.find(h->device);
+        if (it != g_pools.end()) {
+            pool = it->second;
+        } else {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = h->device;
+            cudaError_t e = cudaMemPoolCreate(&pool, &props);
+            if (e != cudaSuccess) return e;
+            unsigned long long keep = kStagingKeep;
+            e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) {
+                cudaMemPoolDestroy(pool);
+                return e;
+            }
+            g_pools[h->device] = pool;
+        }
+    }
+    return cudaMallocFromPoolAsync(reinterpret_cast<void **>(p), bytes, pool, h->stream);
+}
+
+// Returns the staging pool's unused reservation of `device` to the system.
+static void trim_staging(int device) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(device);
+    if (it != g_pools.end()) {
+        cudaDeviceSynchronize();
+        cudaMemPoolTrimTo(it->second, 0);
+    }
 }
 
 extern "C" size_t lbm_bytes_required(int nx, int ny, int storage) {
@@ -175,6 +229,14 @@ extern "C" int lbm_create_ex(int nx, int ny, double tau, double c2, double rho0,
     size_t bytes = state_bytes(h);
     if (e == cudaSuccess) e = cudaMalloc(&h->buf[0], bytes);
     if (e == cudaSuccess) e = cudaMalloc(&h->buf[1], bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        // Cached staging memory may be in the way: release it and retry.
+        cudaGetLastError();
+        trim_staging(h->device);
+        e = cudaSuccess;
+        if (!h->buf[0]) e = cudaMalloc(&h->buf[0], bytes);
+        if (e == cudaSuccess && !h->buf[1]) e = cudaMalloc(&h->buf[1], bytes);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&h->scratch, sizeof(double) * (3 * 1024 + 16));
     // Stream-ordered, so that creating a grid does not wait for work running
     // on the legacy default stream.
@@ -225,7 +287,7 @@ static int stage_field(lbm_grid *h, const double *src, int on_device, double **d
     }
     size_t n = (size_t)h->nx * h->ny;
     double *d = nullptr;
-    CK(cudaMallocAsync(&d, n * sizeof(double), h->stream));
+    CK(staging_alloc(h, &d, n * sizeof(double)));
     owned.push_back(d);
     CK(cudaMemcpyAsync(d, src, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     *dev = d;
@@ -407,11 +469,10 @@ extern "C" int lbm_moments(lbm_t h, double *rho, double *ux, double *uy, int on_
         cudaError_t e = launch_moments(h->storage, h->buf[h->cur], h->nx, h->ny, h->P, h->rho0,
                                        rho, ux, uy, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "lbm_moments kernel");
-        CK(cudaStreamSynchronize(h->stream));
-        return take_status(h);
+        return sync_status(h);
     }
     double *d = nullptr;
-    CK(cudaMallocAsync(&d, 3 * n * sizeof(double), h->stream));
+    CK(staging_alloc(h, &d, 3 * n * sizeof(double)));
     cudaError_t e = launch_moments(h->storage, h->buf[h->cur], h->nx, h->ny, h->P, h->rho0,
                                    rho ? d : nullptr, ux ? d + n : nullptr,
                                    uy ? d + 2 * n : nullptr, h->stream);
@@ -424,8 +485,7 @@ extern "C" int lbm_moments(lbm_t h, double *rho, double *ux, double *uy, int on_
                             h->stream);
     cudaFreeAsync(d, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "lbm_moments");
-    CK(cudaStreamSynchronize(h->stream));
-    return take_status(h);
+    return sync_status(h);
 }
 
 extern "C" int lbm_sums(lbm_t h, double *out3) {
@@ -436,8 +496,7 @@ extern "C" int lbm_sums(lbm_t h, double *out3) {
     if (e != cudaSuccess) return cuda_fail(e, "lbm_sums kernel");
     CK(cudaMemcpyAsync(h->host_out, h->scratch, 3 * sizeof(double), cudaMemcpyDeviceToHost,
                        h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    int rs = take_status(h);
+    int rs = sync_status(h);
     if (rs != LBM_OK) return rs;
     out3[0] = (double)h->nx * (double)h->ny * h->rho0 + h->host_out[0];
     out3[1] = h->host_out[1];
@@ -456,8 +515,7 @@ extern "C" int lbm_mode(lbm_t h, int field, int kx, int ky, double *out2) {
     if (e != cudaSuccess) return cuda_fail(e, "lbm_mode kernel");
     CK(cudaMemcpyAsync(h->host_out, h->scratch, 2 * sizeof(double), cudaMemcpyDeviceToHost,
                        h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    int rs = take_status(h);
+    int rs = sync_status(h);
     if (rs != LBM_OK) return rs;
     out2[0] = h->host_out[0];
     out2[1] = h->host_out[1];
@@ -491,8 +549,7 @@ extern "C" int lbm_set_stream(lbm_t h, void *cuda_stream) {
 
 extern "C" int lbm_sync(lbm_t h) {
     if (!h) return fail(LBM_EINVAL, "lbm_sync: NULL handle");
-    CK(cudaStreamSynchronize(h->stream));
-    return take_status(h);
+    return sync_status(h);
 }
 
 // ---------------------------------------------------------------------------
@@ -508,9 +565,9 @@ extern "C" int lbm_get_state(lbm_t h, void *dst_host, long long *t) {
     size_t pitch = h->P * elem_bytes(h->storage);
     CK(cudaMemcpy2DAsync(dst_host, row, h->buf[h->cur], pitch, row, 9, cudaMemcpyDeviceToHost,
                          h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    int rs = sync_status(h);
     if (t) *t = h->t;
-    return take_status(h);
+    return rs;
 }
 
 extern "C" int lbm_set_state(lbm_t h, const void *src_host, long long t) {

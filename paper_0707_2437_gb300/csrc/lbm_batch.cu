@@ -403,6 +403,12 @@ extern "C" int lbm_batch_step(lbm_batch_t b, long long n, const long long *limit
     return run_batch(b, n, limits, true);
 }
 
+cudaError_t batch_queue_status(lbm_batch *b, cudaStream_t st) {
+    return cudaMemcpyAsync(b->h_status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+}
+
+int batch_status(const lbm_batch *b) { return *b->h_status; }
+
 extern "C" int lbm_batch_sync(lbm_batch_t b) {
     if (!b) return bfail(LBM_EINVAL, "lbm_batch_sync: NULL batch");
     BCK(cudaMemcpyAsync(b->h_status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost,

@@ -128,3 +128,9 @@ struct lbm_grid {
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaEvent_t staged = nullptr;  // lbm_init: host fields copied
 };
+
+// Status word of a batch's kernels: batch_queue_status queues its copy to
+// pinned host memory on `st`; once `st` has been synchronised, batch_status
+// returns it (LBM_OK or LBM_ETIMEOUT).  Defined in lbm_batch.cu.
+cudaError_t batch_queue_status(struct lbm_batch *b, cudaStream_t st);
+int batch_status(const struct lbm_batch *b);
