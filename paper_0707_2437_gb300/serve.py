@@ -3,13 +3,14 @@
 Requests (grid size, tau, c^2, step count, storage) arrive over time.  The
 server keeps every admitted grid's distributions resident in HBM and advances
 all of them together with the batch API (one persistent launch per quantum of
-steps, each grid limited to its remaining steps).  Between quanta it retires
-finished grids (their moments are the result), frees their memory, and admits
-waiting requests, in arrival order, as long as the free device memory
+steps, each grid limited to its remaining steps).  While a quantum runs it
+admits waiting requests, in arrival order, as long as the free device memory
 (lbm_mem_info) minus a reserve covers the new grid (lbm_bytes_required plus the
-staging of its initial fields) and a slot is free.  So requests that arrive
-while others are on the GPU join the running set as memory frees up, and their
-work overlaps on the device.
+staging of its initial fields) and a slot is free; their grids are initialised
+on side streams and join at the next quantum.  After each quantum it retires
+finished grids (their moments are the result) and frees their memory.  So
+requests that arrive while others are on the GPU join the running set as
+memory frees up, and their work overlaps on the device.
 
 ``serve_fifo`` is the plain baseline: one grid at a time, in arrival order,
 with the single-grid FP32 kernel.
@@ -83,8 +84,8 @@ class Server:
     created and initialised on side streams (host field set-up and copies
     overlap the kernel; lbm_init returns once host fields are copied), then
     moved onto the batch's stream (lbm_set_stream), and join the batch at the
-    next quantum.  With ``overlap=False`` admission
-    happens between quanta, on ``stream``."""
+    next quantum.  With ``overlap=False`` admission happens between quanta,
+    on ``stream``."""
 
     def __init__(self, quantum: int = 256, reserve_bytes: int = 4 << 30,
                  max_slots: int = 512, keep_fields: bool = False, stream=None,
