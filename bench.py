@@ -114,7 +114,7 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sms, maxes, reasons = [], [], set()
+        sms, maxes, watts, reasons = [], [], [], set()
         for line in out.strip().splitlines():
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
@@ -124,6 +124,10 @@ class ClockSampler:
                 maxes.append(float(f[2]))
             except ValueError:
                 continue
+            try:
+                watts.append(float(f[3]))
+            except ValueError:
+                pass
             for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
                                   "sw_power_cap"), f[5:9]):
                 if val.lower() == "active":
@@ -131,6 +135,8 @@ class ClockSampler:
         if not sms:
             return None
         return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxes),
+                "sm_min_mhz": min(sms),
+                "power_w": statistics.median(watts) if watts else None,
                 "samples": len(sms), "reasons": sorted(reasons)}
 
 
@@ -424,6 +430,8 @@ def run_native(args):
 
     if args.e2e_jobs:
         job(10)  # warm-up (graphs, allocator)
+    e2e_clocks = ClockSampler(local)
+    e2e_clocks.start()
     barrier(ws)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -431,6 +439,7 @@ def run_native(args):
         job(args.e2e_steps)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(ws, time.perf_counter() - t0)
+    e2e_clk = e2e_clocks.stop()
     e2e_value = (ws * sites * args.e2e_steps * args.e2e_jobs / e2e_s / 1e6
                  if args.e2e_jobs else None)
     # One more job, outside the timed region, with a synchronisation after
@@ -504,7 +513,8 @@ def run_native(args):
                 "step": f"one job: lbm_init from pinned host fields, {args.e2e_steps} steps "
                         f"({'one batch launch' if batch is not None else 'lbm_step per grid'}), "
                         f"lbm_moments to host, for all {len(runs)} grids",
-                "jobs": args.e2e_jobs, "phases_of_one_more_job": e2e_phases},
+                "jobs": args.e2e_jobs, "phases_of_one_more_job": e2e_phases,
+                "clocks": e2e_clk},
         "gpu_launches": n_launch * (2 if args.drive is not None else 1),
         "clocks": clk,
         "single_grid_kernel": single,

@@ -103,9 +103,10 @@ int lbm_destroy(lbm_t h);
  *   rho, ux, uy  [ny][nx] doubles, rho > 0; host pointers if on_device == 0,
  *                device pointers otherwise
  * Resets the step counter to 0.  Returns after the fields have been read:
- * host fields once they are copied to the device (the initialisation kernel
- * may still be queued on the stream behind other work), device fields once
- * the kernel has run. */
+ * host fields once they are copied to the device, device fields once the
+ * initialisation kernel has run.  Host fields are copied on a stream of the
+ * library's, so the call does not wait for work already queued on the
+ * handle's stream; the kernel is queued there behind that work. */
 int lbm_init(lbm_t h, const double *rho, const double *ux, const double *uy,
              int on_device);
 

@@ -152,7 +152,28 @@ static constexpr unsigned long long kStagingKeep = 1ull << 30;
 static std::mutex g_pool_mu;
 static std::map<int, cudaMemPool_t> g_pools;
 
-static cudaError_t staging_alloc(lbm_grid *h, double **p, size_t bytes) {
+// Per-device stream for lbm_init's host-to-device copies.  The copies do not
+// queue behind the work on the grid's stream (a running batch, say), so the
+// call returns as soon as the host fields are read; the grid's stream waits
+// for the copies before the initialisation kernel.
+static std::map<int, cudaStream_t> g_copy_streams;
+
+static cudaError_t copy_stream(int device, cudaStream_t *out) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_copy_streams.find(device);
+    if (it != g_copy_streams.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    g_copy_streams[device] = s;
+    *out = s;
+    return cudaSuccess;
+}
+
+static cudaError_t staging_alloc(lbm_grid *h, double **p, size_t bytes, cudaStream_t st) {
     cudaMemPool_t pool = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_pool_mu);
@@ -168,6 +189,12 @@ static cudaError_t staging_alloc(lbm_grid *h, double **p, size_t bytes) {
             if (e != cudaSuccess) return e;
             unsigned long long keep = kStagingKeep;
             e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            // Memory freed on one stream is reused on another only once the
+            // free has completed: the pool never makes the copy stream wait
+            // for a grid's stream.
+            int no = 0;
+            if (e == cudaSuccess)
+                e = cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
             if (e != cudaSuccess) {
                 cudaMemPoolDestroy(pool);
                 return e;
@@ -175,7 +202,7 @@ static cudaError_t staging_alloc(lbm_grid *h, double **p, size_t bytes) {
             g_pools[h->device] = pool;
         }
     }
-    return cudaMallocFromPoolAsync(reinterpret_cast<void **>(p), bytes, pool, h->stream);
+    return cudaMallocFromPoolAsync(reinterpret_cast<void **>(p), bytes, pool, st);
 }
 
 // Returns the staging pool's unused reservation of `device` to the system.
@@ -278,18 +305,19 @@ extern "C" int lbm_destroy(lbm_t h) {
     return LBM_OK;
 }
 
-// Copies a [ny][nx] double field to device scratch if it is on the host.
-static int stage_field(lbm_grid *h, const double *src, int on_device, double **dev,
-                       std::vector<double *> &owned) {
+// Copies a [ny][nx] double field to device scratch on stream `cs` if it is
+// on the host.
+static int stage_field(lbm_grid *h, const double *src, int on_device, cudaStream_t cs,
+                       double **dev, std::vector<double *> &owned) {
     if (on_device) {
         *dev = const_cast<double *>(src);
         return LBM_OK;
     }
     size_t n = (size_t)h->nx * h->ny;
     double *d = nullptr;
-    CK(staging_alloc(h, &d, n * sizeof(double)));
+    CK(staging_alloc(h, &d, n * sizeof(double), cs));
     owned.push_back(d);
-    CK(cudaMemcpyAsync(d, src, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(d, src, n * sizeof(double), cudaMemcpyHostToDevice, cs));
     *dev = d;
     return LBM_OK;
 }
@@ -299,12 +327,17 @@ extern "C" int lbm_init(lbm_t h, const double *rho, const double *ux, const doub
     if (!h || !rho || !ux || !uy) return fail(LBM_EINVAL, "lbm_init: NULL argument");
     std::vector<double *> owned;
     double *dr = nullptr, *du = nullptr, *dv = nullptr;
-    int rc = stage_field(h, rho, on_device, &dr, owned);
-    if (rc == LBM_OK) rc = stage_field(h, ux, on_device, &du, owned);
-    if (rc == LBM_OK) rc = stage_field(h, uy, on_device, &dv, owned);
-    if (rc == LBM_OK && !on_device) {
-        cudaError_t e = cudaEventRecord(h->staged, h->stream);
-        if (e != cudaSuccess) rc = cuda_fail(e, "lbm_init");
+    cudaStream_t cs = h->stream;
+    if (!on_device) CK(copy_stream(h->device, &cs));
+    int rc = stage_field(h, rho, on_device, cs, &dr, owned);
+    if (rc == LBM_OK) rc = stage_field(h, ux, on_device, cs, &du, owned);
+    if (rc == LBM_OK) rc = stage_field(h, uy, on_device, cs, &dv, owned);
+    if (!on_device && !owned.empty()) {
+        // The grid's stream waits for the copies (also when one failed, so
+        // that the frees below stay ordered after them).
+        cudaError_t e = cudaEventRecord(h->staged, cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->staged, 0);
+        if (e != cudaSuccess && rc == LBM_OK) rc = cuda_fail(e, "lbm_init");
     }
     if (rc == LBM_OK) {
         cudaError_t e = launch_init(h->storage, h->buf[0], h->nx, h->ny, h->P, h->rho0, dr, du, dv,
@@ -315,9 +348,10 @@ extern "C" int lbm_init(lbm_t h, const double *rho, const double *ux, const doub
     if (rc != LBM_OK) return rc;
     h->cur = 0;
     h->t = 0;
-    // Host fields: wait only until the copies have read them (the kernel
-    // stays queued, so the call does not wait for work ahead of it on the
-    // device).  Device fields: wait until the kernel has read them.
+    // Host fields: wait only until the copies have read them (they run on
+    // the copy stream; the kernel stays queued on the grid's stream, so the
+    // call does not wait for work ahead of it there).  Device fields: wait
+    // until the kernel has read them.
     if (on_device)
         CK(cudaStreamSynchronize(h->stream));
     else
@@ -472,7 +506,7 @@ extern "C" int lbm_moments(lbm_t h, double *rho, double *ux, double *uy, int on_
         return sync_status(h);
     }
     double *d = nullptr;
-    CK(staging_alloc(h, &d, 3 * n * sizeof(double)));
+    CK(staging_alloc(h, &d, 3 * n * sizeof(double), h->stream));
     cudaError_t e = launch_moments(h->storage, h->buf[h->cur], h->nx, h->ny, h->P, h->rho0,
                                    rho ? d : nullptr, ux ? d + n : nullptr,
                                    uy ? d + 2 * n : nullptr, h->stream);
@@ -643,7 +677,7 @@ extern "C" int lbm_set_c2_field(lbm_t h, const double *c2, int on_device) {
     if (!h->a15f) CK(cudaMalloc(&h->a15f, n * sizeof(float)));
     std::vector<double *> owned;
     double *d = nullptr;
-    int rc = stage_field(h, c2, on_device, &d, owned);
+    int rc = stage_field(h, c2, on_device, h->stream, &d, owned);
     if (rc == LBM_OK) {
         cudaError_t e = launch_a15_from_c2(d, h->a15f, (long long)n, h->stream);
         if (e != cudaSuccess) rc = cuda_fail(e, "lbm_set_c2_field kernel");

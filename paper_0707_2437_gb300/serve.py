@@ -6,8 +6,8 @@ all of them together with the batch API (one persistent launch per quantum of
 steps, each grid limited to its remaining steps).  While a quantum runs it
 admits waiting requests, in arrival order, as long as the free device memory
 (lbm_mem_info) minus a reserve covers the new grid (lbm_bytes_required plus the
-staging of its initial fields) and a slot is free; their grids are initialised
-on side streams and join at the next quantum.  After each quantum it retires
+staging of its initial fields) and a slot is free; their grids are created and
+initialised meanwhile and join at the next quantum.  After each quantum it retires
 finished grids (their moments are the result) and frees their memory.  So
 requests that arrive while others are on the GPU join the running set as
 memory frees up, and their work overlaps on the device.
@@ -81,22 +81,22 @@ class Server:
 
     With ``overlap=True`` (the default) the batch runs on a stream of its own
     and arriving requests are admitted while a quantum runs: their grids are
-    created and initialised on side streams (host field set-up and copies
-    overlap the kernel; lbm_init returns once host fields are copied), then
-    moved onto the batch's stream (lbm_set_stream), and join the batch at the
-    next quantum.  With ``overlap=False`` admission happens between quanta,
-    on ``stream``."""
+    created on the batch's stream and initialised there.  lbm_init copies host
+    fields on the library's copy stream and returns once they are read, with
+    the initialisation kernel queued behind the running quantum, so the host's
+    field set-up and the copies overlap the kernel.  The new grids join the
+    batch at the next quantum.  With ``overlap=False`` admission happens
+    between quanta, on ``stream``."""
 
     def __init__(self, quantum: int = 256, reserve_bytes: int = 4 << 30,
                  max_slots: int = 512, keep_fields: bool = False, stream=None,
-                 overlap: bool = True, side_streams: int = 8):
+                 overlap: bool = True):
         self.quantum = quantum
         self.reserve = reserve_bytes
         self.max_slots = max_slots
         self.keep_fields = keep_fields
         self.stream = stream
         self.overlap = overlap
-        self.side_streams = side_streams
         lbm.load()
 
     def _need(self, req) -> int:
@@ -113,14 +113,11 @@ class Server:
         ph = stats.phase_s
         batch = None
         members = None
-        main, sides = self.stream, [self.stream]
-        if self.overlap:
-            # Each admission initialises on the next of a few side streams, so
-            # that its copies do not queue behind the previous admission's
-            # initialisation kernel (which waits for the quantum's SMs).
-            main = self.stream if self.stream is not None else lbm.new_stream()
-            sides = [lbm.new_stream() for _ in range(self.side_streams)]
-        n_admitted = 0
+        main = self.stream
+        if self.overlap and main is None:
+            # Not the legacy default stream: that one would make the copies
+            # and host calls around the running quantum wait for it.
+            main = lbm.new_stream()
         t0 = time.perf_counter()
         i = 0
 
@@ -129,7 +126,7 @@ class Server:
 
         def admit(incoming):
             # Admit arrived requests, in order, while memory and slots allow.
-            nonlocal i, n_admitted
+            nonlocal i
             ta = time.perf_counter()
             free, _ = lbm.mem_info()
             while i < len(pending) and len(active) + len(incoming) < self.max_slots:
@@ -142,12 +139,8 @@ class Server:
                         raise MemoryError(f"request {req.rid} needs {need} bytes, "
                                           f"{free} free")
                     break
-                side = sides[n_admitted % len(sides)]
-                n_admitted += 1
-                g = lbm.Grid(req.nx, req.ny, req.tau, req.c2, req.storage, stream=side)
+                g = lbm.Grid(req.nx, req.ny, req.tau, req.c2, req.storage, stream=main)
                 g.init(*_fields(req))
-                if side is not main:
-                    g.set_stream(main)
                 incoming.append([req, g, req.steps, now()])
                 free -= need
                 i += 1

@@ -34,10 +34,7 @@ def _fake_lbm(dev):
         def __init__(self, nx, ny, tau, c2, storage="f32", stream=None):
             self.nx, self.ny, self.storage = nx, ny, storage
             self.stream = stream
-            # A grid made while a quantum runs must not be on that quantum's stream.
             self.made_in_flight = dev.in_flight is not None
-            if self.made_in_flight:
-                assert stream is not dev.in_flight.stream
             self.bytes = dev.bytes_required(nx, ny, storage)
             dev.used += self.bytes
             dev.max_used = max(dev.max_used, dev.used)
@@ -170,10 +167,10 @@ def test_summary_percentiles():
 
 @pytest.mark.parametrize("overlap", [True, False])
 def test_admission_overlaps_the_running_quantum(monkeypatch, overlap):
-    """With overlap, requests that arrive while a quantum runs are created on
-    a side stream during it and moved onto the batch's stream before they
-    join; every batch holds grids of one stream.  Without overlap nothing is
-    created while a quantum is queued."""
+    """With overlap, requests that arrive while a quantum runs are created
+    during it, on the batch's own stream (not the legacy default stream), and
+    join at the next quantum; every batch holds grids of one stream.  Without
+    overlap nothing is created while a quantum is queued."""
     dev = _FakeDevice(total=1 << 40)
     monkeypatch.setattr(serve, "lbm", _fake_lbm(dev))
     reqs = _requests(n=12)
@@ -182,6 +179,8 @@ def test_admission_overlaps_the_running_quantum(monkeypatch, overlap):
     assert len(stats.results) == len(reqs) and dev.live == 0
     made = [g.made_in_flight for g in dev.created]
     assert any(made) == overlap
-    assert dev.streams == (1 + srv.side_streams if overlap else 0)
+    assert dev.streams == (1 if overlap else 0)
+    if overlap:
+        assert all(g.stream is not None for g in dev.created)
     for q, g in zip(reqs, dev.created):
         assert g.steps_at_close == q.steps
