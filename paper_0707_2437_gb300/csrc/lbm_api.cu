@@ -165,8 +165,13 @@ static cudaError_t copy_stream(int device, cudaStream_t *out) {
         *out = it->second;
         return cudaSuccess;
     }
+    // Created on the grid's device, whichever device is current.
+    int cur = device;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e == cudaSuccess && cur != device) e = cudaSetDevice(device);
     cudaStream_t s = nullptr;
-    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (cur != device) cudaSetDevice(cur);
     if (e != cudaSuccess) return e;
     g_copy_streams[device] = s;
     *out = s;
