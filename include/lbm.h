@@ -22,7 +22,8 @@
  * Ownership: a handle owns its device memory (two distribution buffers and a
  * small reduction scratch area), freed by lbm_destroy.  Caller pointers are
  * only read or written during the call that receives them.  No call keeps a
- * caller pointer.
+ * caller pointer.  Per device, the library also keeps, for the life of the
+ * process, a pool of staging memory for host fields and a copy stream.
  *
  * Errors: every call returns a status (LBM_OK = 0, negative on error, positive
  * for a warning); no C++ exception crosses this interface.  lbm_strerror maps
@@ -190,8 +191,8 @@ int lbm_sync(lbm_t h);
  * queued on the old stream (an event wait; the host does not block).  If a
  * long lbm_step call has run as a persistent launch, that launch is waited
  * for and its status returned first (LBM_ETIMEOUT leaves the stream
- * unchanged).  Typical use: initialise a grid on a side stream while other
- * work runs, then move it onto the stream of the batch it joins. */
+ * unchanged).  Typical use: move a grid created and initialised on one
+ * stream onto the stream of the batch it joins. */
 int lbm_set_stream(lbm_t h, void *cuda_stream);
 
 /* Bytes of device state (both distribution buffers) a grid of this size and
