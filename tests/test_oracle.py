@@ -482,3 +482,70 @@ def test_y_uniform_state_stays_y_uniform_bitwise():
     oracle.run(f, 0.6, oracle.alpha_from_c2(0.16), 50)
     for i in range(9):
         assert all(np.array_equal(f[i][0], f[i][y]) for y in range(1, ny))
+
+
+# --- spatially varying alpha (a c^2 field; the outlook of Section 5) -----------
+
+def test_alpha_field_uniform_equals_scalar_bitwise():
+    """A field holding one value everywhere is the scalar-alpha run of Eq. 5,
+    bit for bit."""
+    nx, ny, tau, alpha = 40, 13, 0.75, oracle.alpha_from_c2(0.15)
+    rho, ux, uy = workloads.fourier_modes(nx, ny, amp=1e-2, seed=8)
+    f = oracle.init(rho, ux, uy)
+    g = f.copy()
+    oracle.run(f, tau, alpha, 30)
+    oracle.run(g, tau, np.full((ny, nx), alpha), 30)
+    assert np.array_equal(f, g)
+
+
+def test_alpha_field_force_is_local():
+    """With alpha varying over the grid the force of Eq. 5 at a site uses that
+    site's alpha: one step adds no mass and adds momentum alpha(x, y) grad(rho)
+    with the central difference of Section 4.  rho = 1 + A sin(kx) makes the
+    gradient A sin(k) cos(kx) exactly; alpha depends on both x and y, so a
+    transposed field, a neighbour's alpha or a flipped sign fails."""
+    nx, ny, A, tau = 32, 7, 1e-3, 0.8
+    k = 2 * np.pi / nx
+    x = np.arange(nx)[None, :]
+    y = np.arange(ny)[:, None]
+    alpha = -0.2 + 0.15 * np.cos(2 * np.pi * x / nx + 0.3) + 0.1 * np.sin(2 * np.pi * y / ny)
+    rho, ux, uy = workloads.sine_wave(nx, ny, A)
+    f0 = oracle.init(rho, ux, uy)
+    fa, fz = f0.copy(), f0.copy()
+    oracle.run(fa, tau, alpha, 1)
+    oracle.run(fz, tau, 0.0, 1)
+    d = fa - fz
+    F = np.stack([np.roll(d[i], (-oracle.EY[i], -oracle.EX[i]), axis=(0, 1))
+                  for i in range(9)])
+    np.testing.assert_allclose(F.sum(axis=0), 0.0, atol=1e-18)
+    gx = A * np.sin(k) * np.cos(k * x)
+    np.testing.assert_allclose(np.tensordot(oracle.EX, F, 1), alpha * gx, rtol=1e-9, atol=1e-18)
+    np.testing.assert_allclose(np.tensordot(oracle.EY, F, 1), 0.0, atol=1e-18)
+
+
+def test_alpha_field_pulse_travel_time():
+    """Eq. 8 holds locally: a density pulse crossing a smooth step from
+    c^2 = 0.1 to 0.4 reaches a probe at the ray travel time, the sum of
+    1 / c(x) over the cells it crosses, within 2 %.  The pulse starts off
+    centre so that its left-running half, which wraps around the periodic
+    channel, arrives much later."""
+    nx, ny, tau = 2048, 3, 0.55
+    x = np.arange(nx, dtype=float)
+    c2x = 0.1 + 0.3 * 0.5 * (1 + np.tanh((x - 1024) / 30.0))
+    x0, x1 = 700, 1400
+    rho = np.broadcast_to(1 + 1e-4 * np.exp(-0.5 * ((x - x0) / 6.0) ** 2), (ny, nx)).copy()
+    z = np.zeros((ny, nx))
+    t_ray = float(np.sum(1.0 / np.sqrt(c2x[x0:x1])))
+    alpha = np.broadcast_to(1.0 / 3.0 - c2x, (ny, nx)).copy()
+    f = oracle.init(rho, z, z.copy())
+    t = int(0.9 * t_ray)
+    oracle.run(f, tau, alpha, t)
+    ts, vals = [], []
+    while t < 1.1 * t_ray:
+        r, _, _ = oracle.moments(f)
+        ts.append(t)
+        vals.append(r[:, x1].mean() - 1.0)
+        oracle.run(f, tau, alpha, 2)
+        t += 2
+    t_peak = ts[int(np.argmax(vals))]
+    assert abs(t_peak / t_ray - 1) < 0.02, (t_peak, t_ray)
