@@ -182,14 +182,27 @@ def serve_comparison(args, stream=None):
     return out
 
 
-def cpu_baseline(seconds: float = 12.0):
-    """The FP64 oracle as it stands, on the host cores, on one 2048^2 grid of
-    the sweep: runs whole steps until `seconds` have passed."""
+def sweep_fields(r):
+    return workloads.acoustic_shear(r.nx, r.ny, r.amp)
+
+
+def fourier_fields(r):
+    return workloads.fourier_modes(r.nx, r.ny, amp=r.amp, seed=3)
+
+
+FOURIER8192 = ("8192x8192 periodic D2Q9, tau=0.6, c2=0.15, rho = 1 + 8 seeded plane waves "
+               "(integer wave numbers in [-4,4]^2, seed 3) scaled to max |rho - 1| = 1e-3, u = 0")
+
+
+def cpu_baseline(seconds: float = 12.0, r=None, make_fields=sweep_fields):
+    """The FP64 oracle as it stands, on the host cores, on one grid of the
+    workload (the first 2048^2 grid of the sweep by default): runs whole
+    steps until `seconds` have passed."""
     from oracle import oracle
     cores = os.cpu_count() or 1
     used = oracle.set_threads(cores)
-    r = workloads.sweep_2048()[0]
-    f = oracle.init(*workloads.acoustic_shear(r.nx, r.ny, r.amp))
+    r = r if r is not None else workloads.sweep_2048()[0]
+    f = oracle.init(*make_fields(r))
     alpha = oracle.alpha_from_c2(r.c2)
     oracle.run(f, r.tau, alpha, 1)  # warm-up
     steps, t0 = 0, time.perf_counter()
@@ -199,7 +212,8 @@ def cpu_baseline(seconds: float = 12.0):
     dt = time.perf_counter() - t0
     return {"value": r.nx * r.ny * steps / dt / 1e6, "unit": "MLUPS", "cores": used,
             "kind": "oracle",
-            "sample": f"{steps} FP64 steps of one 2048x2048 grid of the sweep ({dt:.1f} s)"}
+            "sample": f"{steps} FP64 steps of one {r.nx}x{r.ny} grid of the workload "
+                      f"({dt:.1f} s)"}
 
 
 def run_reference(args):
@@ -246,7 +260,12 @@ def run_native(args):
         raise SystemExit("bench.py: no CUDA device (the native path has no CPU fallback)")
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
-    runs = workloads.sweep_2048()[:args.grids]
+    if args.workload == "fourier8192":
+        runs = [workloads.Run(8192, 8192, 0.6, 0.15, 1e-3)]
+        make_fields, workload_desc = fourier_fields, FOURIER8192
+    else:
+        runs = workloads.sweep_2048()[:args.grids]
+        make_fields, workload_desc = sweep_fields, WORKLOAD
     storage = args.storage
     if args.drive is not None:
         args.path = "single"  # batches refuse driven grids
@@ -258,7 +277,7 @@ def run_native(args):
                 g.set_c2_field(workloads.c2_lens(r.nx, r.ny, r.c2))
             if args.drive is not None:
                 g.set_drive(args.drive, 500.0)
-            g.init(*workloads.acoustic_shear(r.nx, r.ny, r.amp))
+            g.init(*make_fields(r))
             if args.config:
                 g.set_config(*args.config)
             if args.rounding != "nearest":
@@ -342,6 +361,7 @@ def run_native(args):
     # 4-byte 1.5 alpha of every site with a c2 field, plus the drive's 27 ny
     # boundary stores.
     lu_bytes = BYTES_PER_LU[storage] + (4 if args.c2_field else 0)
+    state_mb = runs[0].nx * runs[0].ny * BYTES_PER_LU[storage] / 2 / 1e6  # one buffer
     per_step_bytes = lu_bytes * (sites if batch is not None else runs[0].nx * runs[0].ny)
     b1 = lu_bytes * runs[0].nx * runs[0].ny  # one grid-step of the single-grid kernel
     if args.drive is not None and batch is None:
@@ -352,7 +372,9 @@ def run_native(args):
     alg_bytes = per_step_bytes * (spl if batch is not None else 1)
     peak, peak_kind = measured_peak()
     traffic = None
-    if os.path.exists(PROFILE_TRAFFIC) and batch is not None:
+    # The recorded traffic is that of the nine-grid sweep.
+    if (os.path.exists(PROFILE_TRAFFIC) and batch is not None
+            and args.workload == "sweep2048" and len(runs) == 9):
         tj = json.load(open(PROFILE_TRAFFIC))
         entry = tj.get("storage", {}).get(storage)
         if (entry and tj.get("source_hash") == kernel_source_hash()
@@ -413,7 +435,7 @@ def run_native(args):
         args.e2e_jobs = 0
     e2e_runs = runs if args.e2e_jobs else []
     host_in = [[torch.from_numpy(a).pin_memory()
-                for a in workloads.acoustic_shear(r.nx, r.ny, r.amp)] for r in e2e_runs]
+                for a in make_fields(r)] for r in e2e_runs]
     host_out = [[torch.empty((r.ny, r.nx), dtype=torch.float64).pin_memory() for _ in range(3)]
                 for r in e2e_runs]
 
@@ -480,13 +502,14 @@ def run_native(args):
         "vs_baseline": None,
         "dtype": "f32" if storage == "f32" else f"{storage} storage ({args.rounding} rounding), f32 math",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grids": len(runs), "nx": runs[0].nx,
+        "config": {"workload": workload_desc, "grids": len(runs), "nx": runs[0].nx,
                    "ny": runs[0].ny, "storage": storage, "tile": {"vec": cfg[0],
                    "rows": cfg[1], "warps": cfg[2],
                    "pipeline_stages": stages if pipelined else 0},
-                   "l2": "inputs larger than L2 (2 x 151 MB per grid, 129 MB L2), no flush",
-                   "path": (f"persistent launches of {spl} steps over the 9 grids (batch API, "
-                            "grid barrier between steps)"
+                   "l2": (f"inputs larger than L2 (2 x {state_mb:.0f} MB per grid, 129 MB L2), "
+                          "no flush"),
+                   "path": (f"persistent launches of {spl} steps over the {len(runs)} grid(s) "
+                            "(batch API, grid barrier between steps)"
                             if batch is not None else "one step-kernel launch per grid and step"),
                    "steps_per_launch": spl,
                    "c2_field": ("acoustic lens, c2 x (1 + 0.5 gaussian), 1.5 alpha per site in FP32"
@@ -521,7 +544,7 @@ def run_native(args):
         "batch_one_step_per_launch": one_step,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, runs[0], make_fields)
     if not args.no_serve:
         line["serve"] = serve_comparison(args, stream)
     if batch is not None:
@@ -641,7 +664,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--storage", default="f32", choices=list(BYTES_PER_LU) + ["mixed"])
-    ap.add_argument("--workload", default="sweep2048", choices=["sweep2048", "batch", "serve"])
+    ap.add_argument("--workload", default="sweep2048",
+                    choices=["sweep2048", "fourier8192", "batch", "serve"])
     ap.add_argument("--rounding", default="nearest", choices=["nearest", "stochastic"],
                     help="rounding of 16-bit stores")
     ap.add_argument("--batch-count", type=int, default=512)
