@@ -291,6 +291,10 @@ def run_native(args):
     batch = lbm.Batch(grids) if args.path == "batch" else None
     if batch is not None and args.walk16:
         batch.set_walk16(args.walk16)
+    if batch is not None and args.batch_rows:
+        batch.set_config(args.batch_rows, 0)
+    if batch is not None and args.tune:
+        batch.tune()
 
     # Launch plan: on the batch path every launch is one persistent
     # cooperative kernel running `spl` steps of all grids (grid barrier between
@@ -512,6 +516,7 @@ def run_native(args):
                             "(batch API, grid barrier between steps)"
                             if batch is not None else "one step-kernel launch per grid and step"),
                    "steps_per_launch": spl,
+                   "batch_config": batch.get_config() if batch is not None else None,
                    "c2_field": ("acoustic lens, c2 x (1 + 0.5 gaussian), 1.5 alpha per site in FP32"
                                 if args.c2_field else None),
                    "drive": ({"amplitude": args.drive, "period": 500.0}
