@@ -79,7 +79,11 @@ typedef struct lbm_batch *lbm_batch_t;
 /* Creates a periodic nx x ny grid (Section 2-3).
  *   nx, ny      >= 1, nx * ny <= 2^31 - 1
  *   tau         relaxation time, > 0.5 (Section 4: the model turns unstable as
- *               tau -> 0.5)
+ *               tau -> 0.5).  With a large sound speed the force lowers the
+ *               margin for modes that vary in both x and y: at c_e = 0.9 to
+ *               1.0 the linearised update has growing 2-D modes below
+ *               tau = 0.52 to 0.53, while plane waves stay stable down to
+ *               0.501 (no warning is returned for this)
  *   c2          squared sound speed c_e^2 > 0 (Eq. 8); alpha = 1/3 - c2
  *   storage     LBM_F32, LBM_F16D or LBM_BF16D
  *   cuda_stream a cudaStream_t (NULL: legacy default stream)

@@ -549,3 +549,41 @@ def test_alpha_field_pulse_travel_time():
         t += 2
     t_peak = ts[int(np.argmax(vals))]
     assert abs(t_peak / t_ray - 1) < 0.02, (t_peak, t_ray)
+
+
+def test_onset_near_tau_half_plane_waves_and_transverse_modes():
+    """Section 4 (ν against τ down to 0.501 at α = −0.6): as τ → 1/2 the force
+    does not move the onset of instability for plane waves.  Every k_y = 0
+    mode of the linearised Eq. 5 is neutral or damped at τ = 0.501, 0.51,
+    0.52 for α = 0 and −0.6.  On a channel 4 rows high, transverse modes at
+    α = −0.6 do grow (3 % per step at τ = 0.501, none at 0.52).  The paper's
+    plane-wave runs stay stable because a y-uniform state stays y-uniform
+    exactly.  An oracle run seeded with the fastest transverse mode grows as
+    M(k)^t predicts."""
+    ks = 2 * np.pi * np.arange(128) / 128
+    for tau in (0.501, 0.51, 0.52):
+        for alpha in (0.0, -0.6):
+            g = max(linear.spectral_radius(kx, 0.0, tau, alpha) for kx in ks)
+            assert g <= 1 + 1e-12, (tau, alpha, g)
+    nx, ny = 64, 4
+
+    def channel_growth(tau):
+        return {(mx, my): linear.spectral_radius(2 * np.pi * mx / nx, 2 * np.pi * my / ny,
+                                                 tau, -0.6)
+                for mx in range(nx) for my in range(ny)}
+
+    assert max(channel_growth(0.52).values()) <= 1 + 1e-12
+    (mx, my), g = max(channel_growth(0.501).items(), key=lambda kv: kv[1])
+    assert my != 0 and g > 1.03
+    kx, ky = 2 * np.pi * mx / nx, 2 * np.pi * my / ny
+    x = np.arange(nx)[None, :]
+    y = np.arange(ny)[:, None]
+    z0, steps = 1e-9 * np.exp(0.4j), 200
+    rho = 1 + np.real(z0 * np.exp(1j * (kx * x + ky * y)))
+    f = oracle.init(rho, np.zeros_like(rho), np.zeros_like(rho))
+    oracle.run(f, 0.501, -0.6, steps)
+    r, _, _ = oracle.moments(f)
+    z = 2 * np.mean((r - 1) * np.exp(-1j * (kx * x + ky * y)))
+    pred = linear_mode_prediction(z0, kx, ky, 0.501, -0.6, steps)
+    assert abs(pred) > 100 * abs(z0)
+    assert abs(z - pred) < 1e-4 * abs(pred)
