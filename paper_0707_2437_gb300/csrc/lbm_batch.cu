@@ -238,10 +238,9 @@ extern "C" int lbm_batch_create(const lbm_t *grids, int n, lbm_batch_t *out) {
             delete b;
             return bfail(LBM_EINVAL, "lbm_batch_create: grids on different devices");
         }
-    cudaError_t e = cudaSuccess;
-    cudaDeviceProp prop;
-    e = cudaGetDeviceProperties(&prop, b->device);
-    if (e == cudaSuccess) b->sms = prop.multiProcessorCount;
+    // One attribute (a full cudaGetDeviceProperties is slow, and servers
+    // re-create batches often).
+    cudaError_t e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_grids, sizeof(GridDesc) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_limit, sizeof(long long) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_parity, sizeof(int) * n);
