@@ -114,8 +114,15 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
+        return self.summarize(out.strip().splitlines())
+
+    @staticmethod
+    def summarize(lines):
+        """Median and minimum SM clock, maximum clock, median power and the
+        throttle reasons seen, from `--format=csv,noheader,nounits` lines of
+        the query Q; None when no line parses."""
         sms, maxes, watts, reasons = [], [], [], set()
-        for line in out.strip().splitlines():
+        for line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
