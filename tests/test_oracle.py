@@ -91,6 +91,28 @@ def test_force_moments_closed_form():
     np.testing.assert_allclose(np.tensordot(oracle.EY, F, 1), 0.0, atol=1e-18)
 
 
+def test_force_moments_forward_difference_closed_form():
+    """The forward difference the paper tried first (Section 4) puts momentum
+    alpha (rho(x+1) - rho(x)) = alpha A (sin k(x+1) - sin kx) at each site and
+    adds no mass; with rho varying in x only there is no y-momentum."""
+    nx, ny, A, tau, alpha = 32, 4, 1e-3, 0.8, 0.25
+    k = 2 * np.pi / nx
+    rho, ux, uy = workloads.sine_wave(nx, ny, A)
+    f0 = oracle.init(rho, ux, uy)
+    fa, fz = f0.copy(), f0.copy()
+    oracle.run(fa, tau, alpha, 1, grad="forward")
+    oracle.run(fz, tau, 0.0, 1, grad="forward")
+    d = fa - fz
+    F = np.stack([np.roll(d[i], (-oracle.EY[i], -oracle.EX[i]), axis=(0, 1))
+                  for i in range(9)])
+    x = np.arange(nx)
+    np.testing.assert_allclose(F.sum(axis=0), 0.0, atol=1e-18)
+    gx = A * (np.sin(k * (x + 1)) - np.sin(k * x))
+    np.testing.assert_allclose(np.tensordot(oracle.EX, F, 1),
+                               np.broadcast_to(alpha * gx, (ny, nx)), rtol=1e-9, atol=1e-18)
+    np.testing.assert_allclose(np.tensordot(oracle.EY, F, 1), 0.0, atol=1e-18)
+
+
 # --- invariants --------------------------------------------------------------
 
 @pytest.mark.parametrize("c2", [1 / 3, 0.2, 0.05, 0.9])
