@@ -45,16 +45,21 @@ def moments(f):
 
 
 def step(f, tau, alpha):
+    """One step of Eq. 5.  ``alpha`` is a Fraction, or rows of Fractions: a
+    per-site alpha (the spatially varying sound speed of Section 5), used in
+    the force at the site where the collision happens."""
     ny, nx = len(f), len(f[0])
     rho, ux, uy = moments(f)
+    per_site = isinstance(alpha, list)
     post = [[None] * nx for _ in range(ny)]
     for y in range(ny):
         for x in range(nx):
             gx = (rho[y][(x + 1) % nx] - rho[y][(x - 1) % nx]) / 2
             gy = (rho[(y + 1) % ny][x] - rho[(y - 1) % ny][x]) / 2
             eq = feq(rho[y][x], ux[y][x], uy[y][x])
+            a = alpha[y][x] if per_site else alpha
             post[y][x] = [f[y][x][i] - (f[y][x][i] - eq[i]) / tau
-                          + 3 * WQ[i] * alpha * (gx * E[i][0] + gy * E[i][1])
+                          + 3 * WQ[i] * a * (gx * E[i][0] + gy * E[i][1])
                           for i in range(9)]
     return [[[post[(y - E[i][1]) % ny][(x - E[i][0]) % nx][i] for i in range(9)]
              for x in range(nx)] for y in range(ny)]

@@ -157,6 +157,23 @@ def test_exact_rational_brute_force():
         np.testing.assert_allclose(v, np.array(uy_ex, float), atol=1e-15)
 
 
+def test_exact_rational_brute_force_alpha_field():
+    """With a per-site alpha (a c^2 field) the oracle equals the exact rational
+    evaluation of Eq. 5 with each site's own alpha, to FP64 rounding."""
+    rng = np.random.default_rng(5)
+    for nx, ny, steps, tau in [(3, 3, 3, Q(4, 5)), (4, 3, 2, Q(7, 10))]:
+        rq = [[1 + Q(int(rng.integers(-80, 80)), 1000) for _ in range(nx)] for _ in range(ny)]
+        uxq = [[Q(int(rng.integers(-30, 30)), 1000) for _ in range(nx)] for _ in range(ny)]
+        uyq = [[Q(int(rng.integers(-30, 30)), 1000) for _ in range(nx)] for _ in range(ny)]
+        aq = [[Q(1, 3) - Q(int(rng.integers(5, 60)), 100) for _ in range(nx)] for _ in range(ny)]
+        fq = exact.run(exact.init(rq, uxq, uyq), tau, aq, steps)
+        f = oracle.init(np.array(rq, float), np.array(uxq, float), np.array(uyq, float))
+        oracle.run(f, float(tau), np.array([[float(a) for a in row] for row in aq]), steps)
+        fx = np.array([[[float(fq[y][x][i]) for x in range(nx)] for y in range(ny)]
+                       for i in range(9)])
+        np.testing.assert_allclose(f, fx, rtol=0, atol=4e-16)
+
+
 def test_translation_invariance_bitwise():
     """The periodic update commutes with shifts of the grid (bitwise: every
     site does the same FP64 arithmetic)."""
