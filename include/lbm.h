@@ -361,11 +361,14 @@ int lbm_batch_set_timeout_us(lbm_batch_t b, long long us);
  * Scratch: a fixed 24.1 KiB array in the library's device memory (one partial
  * triple for each of at most 1024 reduction blocks, plus the result), held on
  * every GPU that loads the library until the process exits.  The first call on
- * a device looks up that array's device address (once per device, with that
- * device current); make that first call before any stream capture.  All calls
- * share the array and leave their values in it; each call writes every slot it
- * reads, so nothing needs clearing, but calls that overlap on the GPU race and
- * can return wrong totals.  Waits for the stream.  Returns LBM_OK,
+ * a device also does a one-time set-up: it looks up that array's device
+ * address (cudaGetSymbolAddress, with that device current) and keeps it for
+ * later calls; make that first call on each device before any stream capture
+ * begins.  All calls share the array and leave their values in it; each call
+ * writes every slot it reads, so nothing needs clearing, but calls that
+ * overlap on the GPU race and can return wrong totals.  Every call is
+ * synchronous: it queues the reduction on cuda_stream, copies the three totals
+ * to out3 and waits for that stream before it returns.  Returns LBM_OK,
  * LBM_EINVAL, LBM_ECUDA or LBM_ENONFINITE. */
 int lbm_sums_noalloc(const void *f, int nx, int ny, size_t plane_stride,
                      int storage, double rho0, void *cuda_stream, double *out3);

@@ -81,8 +81,10 @@ Err launch_drive_x(int storage, void *f, int nx, int ny, size_t P, double rho0, 
                    double period, const uint32_t *tdev, uint32_t toff, cudaStream_t st);
 Err launch_moments(int storage, const void *f, int nx, int ny, size_t P, double rho0, double *rho,
                    double *ux, double *uy, cudaStream_t st);
-// FP64 reductions: `partials` holds at least reduce_partials_needed() doubles
-// per output; `out` (device) receives the result values.
+// FP64 reductions: `partials` holds reduce_blocks(nx, ny) entries of the
+// output's width (at most kReduceBlocksMax); `out` (device) receives the
+// result values.
+constexpr int kReduceBlocksMax = 1024;
 int reduce_blocks(int nx, int ny);
 Err launch_sums(int storage, const void *f, int nx, int ny, size_t P, double *partials,
                 double *out3, cudaStream_t st);

@@ -467,7 +467,7 @@ __global__ void k_moments(const void *f, int nx, int ny, size_t P, double rho0, 
 // fixed tree; a second one-block kernel sums the block partials in order.
 
 constexpr int RT = 256;
-constexpr int RB_MAX = 1024;
+constexpr int RB_MAX = kReduceBlocksMax;
 
 int reduce_blocks(int nx, int ny) {
     long long n = (long long)nx * ny;

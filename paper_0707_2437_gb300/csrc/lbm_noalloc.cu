@@ -27,7 +27,10 @@ using namespace vss;
 
 namespace {
 
-constexpr int kMaxBlocks = 1024;                // reduction blocks (reduce_blocks caps at this)
+// One partial triple per reduction block: reduce_blocks never returns more
+// than kReduceBlocksMax, so the scratch follows that cap.
+constexpr int kMaxBlocks = kReduceBlocksMax;
+static_assert(kMaxBlocks >= 1, "the reduction needs at least one block");
 constexpr int kSlots = 3 * kMaxBlocks + 8;      // partial triples, then the result
 static __device__ __align__(256) double g_noalloc_scratch[kSlots];
 
@@ -84,7 +87,7 @@ extern "C" int lbm_sums_noalloc(const void *f, int nx, int ny, size_t plane_stri
         return LBM_EINVAL;
     }
     int nb = reduce_blocks(nx, ny);
-    if (nb > kMaxBlocks) {
+    if (nb > kMaxBlocks) {  // defensive: reduce_blocks caps at kReduceBlocksMax
         set_error("lbm_sums_noalloc: grid needs more reduction blocks than the scratch holds");
         return LBM_EINVAL;
     }

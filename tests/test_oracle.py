@@ -133,6 +133,121 @@ def test_conservation_mass_momentum(c2):
         assert np.all(np.abs(s[1:] - s0[1:]) <= 1e-13 * s0[0])
 
 
+# --- Eq. 3 summed over the grid: the totals oracle.sums reports ---------------
+
+def _paper_links():
+    """Link vectors as printed in Section 2: e_i = (cos, sin)[pi (i-1)/2] for
+    i = 1..4 and sqrt(2) (cos, sin)[pi (i - 9/2)/2] for i = 5..8, e_0 = 0."""
+    e = [(0, 0)]
+    for i in range(1, 5):
+        a = np.pi * (i - 1) / 2
+        e.append((round(np.cos(a)), round(np.sin(a))))
+    for i in range(5, 9):
+        a = np.pi * (i - 4.5) / 2
+        e.append((round(np.sqrt(2) * np.cos(a)), round(np.sqrt(2) * np.sin(a))))
+    return e
+
+
+def _check_sums_pins(sums):
+    """Pins of a grid-totals function `sums(f) -> [mass, momentum_x,
+    momentum_y]` (Eq. 3: rho = sum_i f_i, rho u = sum_i f_i e_i, summed over
+    the sites); raises AssertionError where it disagrees.
+
+    (a) One direction at a time: a state with only plane i filled has mass
+        S = sum f_i and momentum e_i S, with e_i the printed link vector
+        (Section 2).  Distinct S per grid so that no two slips cancel.
+    (b) Exact-rational brute force: on small grids after steps of Eq. 5 the
+        totals equal the sum over sites of the exact rho and rho u of
+        `exact.moments` (its own link table, written separately).
+    (c) Equilibrium of known fields: rho = 1 + A sin(2 pi x / nx), uniform u
+        gives mass N and momentum N u exactly (the sine sums to zero over a
+        period, and the equilibrium's moments are rho and rho u)."""
+    links = _paper_links()
+    rng = np.random.default_rng(21)
+    nx, ny = 7, 5
+    for i, (ex, ey) in enumerate(links):
+        f = np.zeros((9, ny, nx))
+        f[i] = rng.uniform(0.1, 1.0, (ny, nx))
+        S = f[i].sum()
+        np.testing.assert_allclose(sums(f), [S, ex * S, ey * S], rtol=1e-14, atol=0,
+                                   err_msg=f"direction {i}")
+    # All nine planes at once with unequal random values.
+    f = rng.uniform(-1.0, 1.0, (9, ny, nx))
+    want = np.array([sum(f[i].sum() for i in range(9)),
+                     sum(links[i][0] * f[i].sum() for i in range(9)),
+                     sum(links[i][1] * f[i].sum() for i in range(9))])
+    np.testing.assert_allclose(sums(f), want, rtol=0, atol=1e-13)
+
+    for nx, ny, steps, tau, c2 in [(3, 3, 2, Q(4, 5), Q(1, 5)), (4, 3, 2, Q(3, 5), Q(1, 20))]:
+        rq = [[1 + Q(int(rng.integers(-80, 80)), 1000) for _ in range(nx)] for _ in range(ny)]
+        uxq = [[Q(int(rng.integers(-30, 30)), 1000) for _ in range(nx)] for _ in range(ny)]
+        uyq = [[Q(int(rng.integers(-30, 30)), 1000) for _ in range(nx)] for _ in range(ny)]
+        fq = exact.run(exact.init(rq, uxq, uyq), tau, Q(1, 3) - c2, steps)
+        r_ex, ux_ex, uy_ex = exact.moments(fq)
+        tot = [sum(r_ex[y][x] for y in range(ny) for x in range(nx)),
+               sum(r_ex[y][x] * ux_ex[y][x] for y in range(ny) for x in range(nx)),
+               sum(r_ex[y][x] * uy_ex[y][x] for y in range(ny) for x in range(nx))]
+        fx = np.array([[[float(fq[y][x][i]) for x in range(nx)] for y in range(ny)]
+                       for i in range(9)])
+        np.testing.assert_allclose(sums(fx), [float(t) for t in tot], rtol=0, atol=4e-15)
+
+    nx, ny, A, U, V = 16, 6, 1e-2, 3e-3, -7e-3
+    rho = np.broadcast_to(1 + A * np.sin(2 * np.pi * np.arange(nx) / nx), (ny, nx)).copy()
+    fx = np.array([[[float(v) for v in exact.feq(Q(rho[y, x]), Q(U), Q(V))] for x in range(nx)]
+                   for y in range(ny)]).transpose(2, 0, 1).copy()
+    N = nx * ny
+    np.testing.assert_allclose(sums(fx), [N, N * U, N * V], rtol=1e-13, atol=0)
+
+
+def test_sums_pinned_to_links_and_exact_moments():
+    """oracle.sums (the FP64 reference of lbm_sums) against the paper's link
+    vectors, the exact-rational moments and the equilibrium of known fields."""
+    _check_sums_pins(oracle.sums)
+
+
+# Slips planted in a private copy of oracle_sums (textual edits of the C
+# source, compiled into a temporary library): each must fail the pins above.
+_SUMS_MUTATIONS = {
+    "momentum_x uses e_y": ("px += f[i * n + s] * EX[i];", "px += f[i * n + s] * EY[i];"),
+    "momentum_y uses e_x": ("py += f[i * n + s] * EY[i];", "py += f[i * n + s] * EX[i];"),
+    "momentum_x sign flipped": ("px += f[i * n + s] * EX[i];", "px -= f[i * n + s] * EX[i];"),
+    "momentum_y sign flipped": ("py += f[i * n + s] * EY[i];", "py -= f[i * n + s] * EY[i];"),
+    "outputs x and y swapped": ("out3[1] = px;\n    out3[2] = py;",
+                                "out3[1] = py;\n    out3[2] = px;"),
+    "last direction dropped": ("for (int i = 0; i < 9; i++) {\n            m += f",
+                               "for (int i = 0; i < 8; i++) {\n            m += f"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(_SUMS_MUTATIONS))
+def test_sums_pins_catch_planted_slips(name, tmp_path):
+    """Each plausible slip in oracle_sums, planted in a copy of the oracle on
+    the CPU, fails _check_sums_pins: the pins are strong enough to see it."""
+    import ctypes
+    import subprocess
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "lbm_oracle.c")).read()
+    old, new = _SUMS_MUTATIONS[name]
+    assert src.count(old) == 1, f"mutation site not found: {old!r}"
+    mutated = tmp_path / "mutant.c"
+    mutated.write_text(src.replace(old, new))
+    lib_path = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", str(mutated), "-o",
+                    str(lib_path), "-lm"], check=True)
+    lib = ctypes.CDLL(str(lib_path))
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.oracle_sums.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
+
+    def mutant_sums(f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        _, ny, nx = f.shape
+        out = np.zeros(3)
+        lib.oracle_sums(nx, ny, f.ctypes.data_as(dp), out.ctypes.data_as(dp))
+        return out
+
+    with pytest.raises(AssertionError):
+        _check_sums_pins(mutant_sums)
+
+
 def test_exact_rational_brute_force():
     """The oracle equals an exact rational evaluation of Eq. 5 (brute force on
     tiny grids, written with pull streaming) to FP64 rounding."""

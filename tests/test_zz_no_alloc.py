@@ -40,6 +40,32 @@ def test_sums_noalloc_matches_lbm_sums_twice(lbm):
         np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * nx * ny)
 
 
+def test_sums_noalloc_padded_planes_bf16_and_own_stream(lbm):
+    """The other inputs the header documents: BF16-delta storage, planes
+    padded apart (plane_stride > nx*ny, so plane i starts at i*plane_stride),
+    and a caller's non-default stream; again two calls in a row."""
+    import torch
+    pad = 37
+    stream = torch.cuda.Stream()
+    for nx, ny, storage, steps in [(160, 41, "bf16d", 30), (96, 50, "f32", 12)]:
+        rho, ux, uy = workloads.fourier_modes(nx, ny, amp=2e-2, seed=nx + 1)
+        uy = uy + 2e-3 * np.sin(2 * np.pi * np.arange(nx) / nx)[None, :]
+        with lbm.Grid(nx, ny, 0.75, 0.15, storage) as g:
+            g.init(rho, ux, uy)
+            g.step(steps)
+            want = g.sums()
+            raw, _ = g.get_state()
+        n = nx * ny
+        esize = 4 if storage == "f32" else 2
+        planes = torch.from_numpy(raw.view(np.uint8)).view(9, n * esize)
+        padded = torch.full((9, (n + pad) * esize), 0xFF, dtype=torch.uint8)
+        padded[:, :n * esize] = planes  # the gaps hold NaN patterns: never read
+        dev = padded.cuda()
+        torch.cuda.synchronize()
+        got = lbm.sums_noalloc(dev.data_ptr(), nx, ny, n + pad, storage, stream=stream)
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * n)
+
+
 def test_sums_noalloc_rejects_bad_sizes(lbm):
     lib = lbm.load()
     out = (np.zeros(3))
