@@ -223,6 +223,16 @@ def cpu_baseline(seconds: float = 12.0, r=None, make_fields=sweep_fields):
                       f"({dt:.1f} s)"}
 
 
+def sweep_config(storage: str, runs, workload_desc: str) -> dict:
+    """`config` of the default line: the workload alone (sizes, storage, the
+    L2 note), the same in the native and the reference arm."""
+    state_mb = runs[0].nx * runs[0].ny * BYTES_PER_LU[storage] / 2 / 1e6  # one buffer
+    return {"workload": workload_desc, "grids": len(runs), "nx": runs[0].nx, "ny": runs[0].ny,
+            "storage": storage,
+            "l2": (f"inputs larger than L2 (2 x {state_mb:.0f} MB per grid, 129 MB L2), "
+                   "no flush")}
+
+
 def run_reference(args):
     ws, rank, _ = dist_setup(args.gpus)
     if rank != 0:
@@ -247,7 +257,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": "one 2048x2048 grid-step per bench step"},
+        "config": sweep_config("f32", runs, WORKLOAD),
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": used, "kind": "oracle",
                          "sample": f"{args.steps} steps of one 2048x2048 grid, tau/c2 cycling "
                                    "through the 9 runs"},
@@ -323,6 +333,11 @@ def run_native(args):
             for g in grids:
                 g.step(n)
 
+    # Clock samples cover the warm-up, the timed region and about 1.2 s of the
+    # same launches right after it (the timed region alone can be shorter than
+    # nvidia-smi's 200 ms sample period).
+    clocks = ClockSampler(local)
+    clocks.start()
     for c in chunks(args.warmup):
         advance(c)
     torch.cuda.synchronize()
@@ -335,8 +350,6 @@ def run_native(args):
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(n_launch)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(local)
-    clocks.start()
     barrier(ws)
     torch.cuda.synchronize()
     t_start.record(stream)
@@ -357,7 +370,14 @@ def run_native(args):
     t_end.record(stream)
     torch.cuda.synchronize()
     barrier(ws)
+    t_pad = time.perf_counter()
+    while time.perf_counter() - t_pad < args.clock_pad_s:
+        advance(plan[0])
+        torch.cuda.synchronize()
     clk = clocks.stop()
+    if clk is not None:
+        clk["window"] = (f"warm-up, the timed region and {args.clock_pad_s:.1f} s of the same "
+                         "launches right after it")
     if batch is not None:
         batch.sync()
     elapsed_ms = t_start.elapsed_time(t_end)
@@ -372,7 +392,6 @@ def run_native(args):
     # 4-byte 1.5 alpha of every site with a c2 field, plus the drive's 27 ny
     # boundary stores.
     lu_bytes = BYTES_PER_LU[storage] + (4 if args.c2_field else 0)
-    state_mb = runs[0].nx * runs[0].ny * BYTES_PER_LU[storage] / 2 / 1e6  # one buffer
     per_step_bytes = lu_bytes * (sites if batch is not None else runs[0].nx * runs[0].ny)
     b1 = lu_bytes * runs[0].nx * runs[0].ny  # one grid-step of the single-grid kernel
     if args.drive is not None and batch is None:
@@ -382,17 +401,10 @@ def run_native(args):
     per_launch_s = statistics.mean(launch_ms) * 1e-3
     alg_bytes = per_step_bytes * (spl if batch is not None else 1)
     peak, peak_kind = measured_peak()
-    traffic = None
-    # The recorded traffic is that of the nine-grid sweep.
-    if (os.path.exists(PROFILE_TRAFFIC) and batch is not None
-            and args.workload == "sweep2048" and len(runs) == 9):
-        tj = json.load(open(PROFILE_TRAFFIC))
-        entry = tj.get("storage", {}).get(storage)
-        if (entry and tj.get("source_hash") == kernel_source_hash()
-                and tj.get("path") == args.path and args.rounding == "nearest"):
-            # Captured on one-step launches of the same kernel; a launch of
-            # `spl` steps moves `spl` times the bytes of one step.
-            traffic = entry["dram_bytes_per_step"] * spl
+    # The recorded traffic is that of the nine-grid sweep on the batch path.
+    traffic = (recorded_traffic(storage, args.rounding, spl)
+               if batch is not None and args.workload == "sweep2048" and len(runs) == 9
+               and not args.c2_field else None)
 
     # The same batch with one step per launch, for the launch overhead, and
     # the plain single-grid step kernel on the same grids (one launch per grid
@@ -500,6 +512,14 @@ def run_native(args):
         e2e_phases = {"init_ms": 1e3 * (tb - ta), "steps_ms": 1e3 * (tc - tb),
                       "moments_ms": 1e3 * (td - tc)}
 
+    job_bytes = len(runs) * 3 * n * 8  # rho, ux, uy in FP64, each way
+    config = sweep_config(storage, runs, workload_desc)
+    if args.c2_field:
+        config["c2_field"] = "acoustic lens, c2 x (1 + 0.5 gaussian), 1.5 alpha per site in FP32"
+    if args.drive is not None:
+        config["drive"] = {"amplitude": args.drive, "period": 500.0}
+    if args.rounding != "nearest":
+        config["rounding"] = args.rounding
     line = {
         "metric": METRIC,
         "value": value,
@@ -513,21 +533,15 @@ def run_native(args):
         "vs_baseline": None,
         "dtype": "f32" if storage == "f32" else f"{storage} storage ({args.rounding} rounding), f32 math",
         "data": "synthetic",
-        "config": {"workload": workload_desc, "grids": len(runs), "nx": runs[0].nx,
-                   "ny": runs[0].ny, "storage": storage, "tile": {"vec": cfg[0],
-                   "rows": cfg[1], "warps": cfg[2],
-                   "pipeline_stages": stages if pipelined else 0},
-                   "l2": (f"inputs larger than L2 (2 x {state_mb:.0f} MB per grid, 129 MB L2), "
-                          "no flush"),
+        "config": config,
+        "launch": {"tile": {"vec": cfg[0], "rows": cfg[1], "warps": cfg[2],
+                            "pipeline_stages": stages if pipelined else 0},
                    "path": (f"persistent launches of {spl} steps over the {len(runs)} grid(s) "
                             "(batch API, grid barrier between steps)"
                             if batch is not None else "one step-kernel launch per grid and step"),
                    "steps_per_launch": spl,
                    "batch_config": batch.get_config() if batch is not None else None,
-                   "c2_field": ("acoustic lens, c2 x (1 + 0.5 gaussian), 1.5 alpha per site in FP32"
-                                if args.c2_field else None),
-                   "drive": ({"amplitude": args.drive, "period": 500.0}
-                             if args.drive is not None else None),
+                   "batch_launch": batch.get_launch() if batch is not None else None,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
@@ -543,11 +557,14 @@ def run_native(args):
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "mean_launch_ms": per_launch_s * 1e3},
         "e2e": {"value": e2e_value, "unit": "MLUPS",
-                "h2d_bytes_per_step": len(runs) * 3 * n * 8,
-                "d2h_bytes_per_step": len(runs) * 3 * n * 8,
+                "h2d_bytes_per_step": job_bytes / args.e2e_steps,
+                "d2h_bytes_per_step": job_bytes / args.e2e_steps,
+                "h2d_bytes_per_job": job_bytes, "d2h_bytes_per_job": job_bytes,
+                "steps_per_job": args.e2e_steps,
                 "step": f"one job: lbm_init from pinned host fields, {args.e2e_steps} steps "
                         f"({'one batch launch' if batch is not None else 'lbm_step per grid'}), "
-                        f"lbm_moments to host, for all {len(runs)} grids",
+                        f"lbm_moments to host, for all {len(runs)} grids; the copies happen "
+                        "once per job, so the bytes per step are the job's over its steps",
                 "jobs": args.e2e_jobs, "phases_of_one_more_job": e2e_phases,
                 "clocks": e2e_clk},
         "gpu_launches": n_launch * (2 if args.drive is not None else 1),
@@ -555,37 +572,112 @@ def run_native(args):
         "single_grid_kernel": single,
         "batch_one_step_per_launch": one_step,
     }
-    if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, runs[0], make_fields)
-    if not args.no_serve:
-        line["serve"] = serve_comparison(args, stream)
     if batch is not None:
         batch.close()
     for g in grids:
         g.close()
+    del grids
+    single_mlups = single["mlups"] if single else None
+    if not args.no_legs and args.workload == "sweep2048" and not args.c2_field \
+            and args.drive is None and storage == "f32":
+        line["f16d_sweep"] = sweep_leg(args, "f16d", stream, single_mlups)
+        line["batch512"] = {st: batch512_leg(args, st, stream, single_mlups)
+                            for st in ("f32", "f16d")}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, runs[0], make_fields)
+    if not args.no_serve:
+        line["serve"] = serve_comparison(args, stream)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def run_batch_workload(args):
-    """512 uneven grids (64^2 .. 1024^2, aspect 2^U[-2,2]) stepped together:
-    `--steps K` time steps of every grid in ONE persistent launch (replayed
-    from a CUDA graph), after `--warmup` steps."""
+def recorded_traffic(storage: str, rounding: str, spl: int):
+    """DRAM bytes of one launch of `spl` steps of the nine-grid sweep on the
+    batch path, from the ncu record under profiles/, or None when the record
+    does not cover these kernel sources, this storage or this rounding."""
+    if not os.path.exists(PROFILE_TRAFFIC) or rounding != "nearest":
+        return None
+    tj = json.load(open(PROFILE_TRAFFIC))
+    entry = tj.get("storage", {}).get(storage)
+    if entry and tj.get("source_hash") == kernel_source_hash() and tj.get("path") == "batch":
+        # Captured on one-step launches of the same kernel; a launch of `spl`
+        # steps makes the same accesses `spl` times.
+        return entry["dram_bytes_per_step"] * spl
+    return None
+
+
+def sweep_leg(args, storage: str, stream, single_mlups):
+    """The nine 2048^2 grids of the sweep in a 16-bit storage on the batch
+    path, persistent launches of --steps-per-launch steps (CUDA events per
+    launch on the launching stream): MLUPS, the roofline at that storage's
+    algorithmic bytes, and the ratio over the plain FP32 single-grid kernel."""
     import torch
 
     from paper_0707_2437_gb300 import lbm
+    runs = workloads.sweep_2048()
+    spl = max(1, args.steps_per_launch)
+    launches = max(1, args.leg_steps // spl)
+    with torch.cuda.stream(stream):
+        grids = []
+        for r in runs:
+            g = lbm.Grid(r.nx, r.ny, r.tau, r.c2, storage, stream=stream.cuda_stream)
+            g.init(*sweep_fields(r))
+            grids.append(g)
+        b = lbm.Batch(grids)
+        for _ in range(3):
+            b.step(spl)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(launches)]
+        for e0, e1 in ev:
+            e0.record(stream)
+            b.step(spl)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        status = b.sync()
+        launch = b.get_launch()
+        bcfg = b.get_config()
+        b.close()
+        for g in grids:
+            g.close()
+    ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    sites = sum(r.nx * r.ny for r in runs)
+    mlups = sites * spl * launches / (sum(ms) * 1e-3) / 1e6
+    per_launch = BYTES_PER_LU[storage] * sites * spl
+    achieved = per_launch / (statistics.mean(ms) * 1e-3) / 1e9
+    peak, _ = measured_peak()
+    return {"workload": "the nine 2048^2 grids of the sweep", "storage": storage,
+            "rounding": "nearest", "steps": spl * launches, "steps_per_launch": spl,
+            "mlups": mlups,
+            "ratio_over_single_grid_kernel": mlups / single_mlups if single_mlups else None,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak,
+                         "traffic": recorded_traffic(storage, "nearest", spl),
+                         "bytes_per_update": BYTES_PER_LU[storage],
+                         "kernel": f"k_batch_one<{storage}, vec {8 if storage != 'f32' else 4}>",
+                         "algorithmic_bytes_per_launch": per_launch,
+                         "mean_launch_ms": statistics.mean(ms)},
+            "batch_config": bcfg, "batch_launch": launch, "batch_status": status}
 
-    ws, rank, local = dist_setup(args.gpus)
-    torch.cuda.set_device(local)
-    stream = torch.cuda.Stream()
-    runs = workloads.batch_grids(args.batch_count)
-    storages = ([args.storage] if args.storage != "mixed" else ["f32", "f16d"])
+
+def batch512_run(args, storage: str, rounding: str, steps: int, warmup: int, stream,
+                 count: int = 512):
+    """The 512 uneven grids (sites log-uniform 64^2 .. 1024^2, aspect
+    2^U[-2, 2], per-grid tau and c^2) in one batch; `storage` is one kind or
+    'mixed' (FP32 and FP16-delta in turn).  `steps` time steps of every grid
+    in one lbm_batch_step call (one persistent launch per kind group, from a
+    CUDA graph), timed with CUDA events on the batch's stream."""
+    import torch
+
+    from paper_0707_2437_gb300 import lbm
+    runs = workloads.batch_grids(count)
+    storages = [storage] if storage != "mixed" else ["f32", "f16d"]
     grids = []
     for k, r in enumerate(runs):
         st = storages[k % len(storages)]
         g = lbm.Grid(r.nx, r.ny, r.tau, r.c2, st, stream=stream.cuda_stream)
-        if args.rounding != "nearest" and st != "f32":
-            g.set_rounding(args.rounding)
+        if rounding != "nearest" and st != "f32":
+            g.set_rounding(rounding)
         g.init(*workloads.sine_wave(r.nx, r.ny, r.amp, r.mode))
         grids.append(g)
     b = lbm.Batch(grids)
@@ -595,48 +687,86 @@ def run_batch_workload(args):
         b.set_walk16(args.walk16)
     if args.tune:
         b.tune()
-    bcfg = b.get_config()
     sites = sum(r.nx * r.ny for r in runs)
     alg = sum(r.nx * r.ny * lbm.BYTES_PER_LU[g.storage] for r, g in zip(runs, grids))
-    b.step(args.warmup)
+    b.step(warmup)
     b.sync()
     t0e = torch.cuda.Event(enable_timing=True)
     t1e = torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(local)
-    clocks.start()
-    barrier(ws)
     torch.cuda.synchronize()
     t0e.record(stream)
-    b.step(args.steps)
+    b.step(steps)
     t1e.record(stream)
     torch.cuda.synchronize()
     status = b.sync()
+    ms = t0e.elapsed_time(t1e)
+    out = {"ms": ms, "sites": sites, "alg_bytes_per_step": alg, "status": status,
+           "batch_config": b.get_config(), "batch_launch": b.get_launch(),
+           "grids": len(runs), "steps": steps}
+    b.close()
+    for g in grids:
+        g.close()
+    return out
+
+
+def batch512_leg(args, storage: str, stream, single_mlups):
+    """The 512-grid batch in one storage: MLUPS, roofline and the ratio over
+    the plain FP32 single-grid kernel."""
+    r = batch512_run(args, storage, "nearest", args.leg_steps, 5, stream)
+    mlups = r["sites"] * r["steps"] / (r["ms"] * 1e-3) / 1e6
+    achieved = r["alg_bytes_per_step"] * r["steps"] / (r["ms"] * 1e-3) / 1e9
+    peak, _ = measured_peak()
+    return {"workload": "batch of 512 uneven grids, sites log-uniform 64^2..1024^2, "
+                        "aspect 2^U[-2,2]", "sites": r["sites"], "storage": storage,
+            "steps": r["steps"], "launch": "one lbm_batch_step call of all steps",
+            "mlups": mlups,
+            "ratio_over_single_grid_kernel": mlups / single_mlups if single_mlups else None,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "bytes_per_update": BYTES_PER_LU[storage],
+                         "algorithmic_bytes_per_step": r["alg_bytes_per_step"]},
+            "batch_config": r["batch_config"], "batch_launch": r["batch_launch"],
+            "batch_status": r["status"]}
+
+
+def run_batch_workload(args):
+    """512 uneven grids (64^2 .. 1024^2, aspect 2^U[-2,2]) stepped together:
+    `--steps K` time steps of every grid in ONE persistent launch per kind
+    group (replayed from a CUDA graph), after `--warmup` steps."""
+    import torch
+
+    ws, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    r = batch512_run(args, args.storage, args.rounding, args.steps, args.warmup, stream,
+                     args.batch_count)
     barrier(ws)
     clk = clocks.stop()
-    ms = max_over_ranks(ws, t0e.elapsed_time(t1e))
-    value = ws * sites * args.steps / (ms * 1e-3) / 1e6
-    achieved = alg * args.steps / (ms * 1e-3) / 1e9
-    peak, kind = measured_peak()
+    ms = max_over_ranks(ws, r["ms"])
+    value = ws * r["sites"] * args.steps / (ms * 1e-3) / 1e6
+    achieved = r["alg_bytes_per_step"] * args.steps / (ms * 1e-3) / 1e9
+    peak, _ = measured_peak()
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": f"{args.storage} storage, f32 math", "data": "synthetic",
-        "config": {"workload": f"batch of {len(runs)} uneven grids, sites log-uniform "
+        "config": {"workload": f"batch of {r['grids']} uneven grids, sites log-uniform "
                                "64^2..1024^2, aspect 2^U[-2,2]",
-                   "sites": sites, "storage": args.storage, "rounding": args.rounding,
-                   "batch_config": bcfg,
-                   "launch":
-                   "one persistent cooperative launch of all steps (CUDA graph)",
-                   "l2": f"working set {alg / 1e9:.1f} GB >> 129 MB L2, no flush"},
+                   "sites": r["sites"], "storage": args.storage, "rounding": args.rounding,
+                   "l2": f"working set {r['alg_bytes_per_step'] / 1e9:.1f} GB >> 129 MB L2, "
+                         "no flush"},
+        "launch": {"batch_config": r["batch_config"], "batch_launch": r["batch_launch"],
+                   "path": "one lbm_batch_step call of all steps: one persistent cooperative "
+                           "launch per kind group"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_batch",
-                     "algorithmic_bytes_per_step": alg},
-        "gpu_launches": 1, "clocks": clk, "batch_status": status,
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_batch_one / k_batch",
+                     "algorithmic_bytes_per_step": r["alg_bytes_per_step"]},
+        "gpu_launches": r["batch_config"]["groups"], "clocks": clk, "batch_status": r["status"],
     }
-    b.close()
-    for g in grids:
-        g.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -718,6 +848,13 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1000)
     ap.add_argument("--e2e-jobs", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the FP16-delta sweep and 512-grid batch legs of the default run")
+    ap.add_argument("--leg-steps", type=int, default=200,
+                    help="time steps timed in each extra leg")
+    ap.add_argument("--clock-pad-s", type=float, default=1.2,
+                    help="seconds of the same launches run after the timed region while "
+                         "the clocks are sampled")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -287,7 +287,7 @@ int lbm_batch_destroy(lbm_batch_t b);
 
 /* Advances grid g of the batch by min(n, limits[g]) steps (limits may be NULL:
  * n steps each), one persistent launch per kind group, replayed from a CUDA
- * graph.  Asynchronous.  A barrier wait that exceeds its time limit makes the
+ * graph (see lbm_batch_set_launch).  Asynchronous.  A barrier wait that exceeds its time limit makes the
  * kernel stop and the next synchronising batch call return LBM_ETIMEOUT.
  * If a grid's c2 field or rounding mode changed since the batch was built,
  * the work-list is rebuilt first (the call then waits for the stream).
@@ -336,6 +336,26 @@ int lbm_batch_get_groups(lbm_batch_t b, int *groups);
 #define LBM_WALK16_V4_PF2 3
 int lbm_batch_set_walk16(lbm_batch_t b, int walk);
 int lbm_batch_get_walk16(lbm_batch_t b, int *walk);
+
+/* How lbm_batch_step issues its persistent launches:
+ *   LBM_LAUNCH_AUTO    the default: the launches of a call (one per kind group,
+ *                      with their parameter copies) are captured once per step
+ *                      count into a CUDA graph and replayed; if the capture
+ *                      fails, the batch switches to direct launches for good
+ *                      and reports it below
+ *   LBM_LAUNCH_GRAPH   always replay the graph; a failed capture is an error
+ *                      (LBM_ECUDA from lbm_batch_step)
+ *   LBM_LAUNCH_DIRECT  cooperative launches issued one by one, no graph
+ * Results are bitwise the same in every mode.  lbm_batch_set_launch waits for
+ * the batch's stream.  lbm_batch_get_launch gives the mode, how the last step
+ * call ran (*last: LBM_LAUNCH_GRAPH or LBM_LAUNCH_DIRECT; 0 before the first
+ * call) and whether an AUTO capture failed (*capture_failed: 1).  Any output
+ * pointer may be NULL. */
+#define LBM_LAUNCH_AUTO 0
+#define LBM_LAUNCH_GRAPH 1
+#define LBM_LAUNCH_DIRECT 2
+int lbm_batch_set_launch(lbm_batch_t b, int mode);
+int lbm_batch_get_launch(lbm_batch_t b, int *mode, int *last, int *capture_failed);
 
 /* Barrier wait limit of the batch kernel in microseconds (default 1e6). */
 int lbm_batch_set_timeout_us(lbm_batch_t b, long long us);

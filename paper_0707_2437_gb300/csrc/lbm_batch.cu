@@ -65,7 +65,14 @@ struct lbm_batch {
     // graph cache (one step count)
     cudaGraphExec_t graph = nullptr;
     long long graph_n = -1;
-    bool use_graph = true;
+    // Launch mode (lbm_batch_set_launch): LBM_LAUNCH_AUTO tries a graph and
+    // falls back to direct launches if capture fails, LBM_LAUNCH_GRAPH
+    // requires the graph, LBM_LAUNCH_DIRECT never captures.  `capture_failed`
+    // records an AUTO fallback; `last_launch` is how the last step call ran
+    // (0 before the first one).
+    int launch_mode = LBM_LAUNCH_AUTO;
+    bool capture_failed = false;
+    int last_launch = 0;
 };
 
 static int bfail(int code, const std::string &m) {
@@ -339,7 +346,10 @@ static int run_batch(lbm_batch *b, long long n, const long long *limits, bool ad
         ++nxs;
     }
     cudaError_t e = cudaSuccess;
-    if (b->use_graph) {
+    const bool want_graph = b->launch_mode == LBM_LAUNCH_GRAPH ||
+                            (b->launch_mode == LBM_LAUNCH_AUTO && !b->capture_failed);
+    bool graphed = false;
+    if (want_graph) {
         if (b->graph_n != n) {
             drop_graph(b);
             cudaStream_t cs;
@@ -355,18 +365,24 @@ static int run_batch(lbm_batch *b, long long n, const long long *limits, bool ad
             if (g) cudaGraphDestroy(g);
             cudaStreamDestroy(cs);
             if (e != cudaSuccess) {
-                // Cooperative launches that cannot be captured run directly.
                 cudaGetLastError();
-                b->use_graph = false;
                 drop_graph(b);
+                if (b->launch_mode == LBM_LAUNCH_GRAPH)
+                    return bcuda(e, "lbm_batch_step: capturing the persistent launch in a CUDA graph");
+                // AUTO: recorded (lbm_batch_get_launch) and never retried.
+                b->capture_failed = true;
             } else {
                 b->graph_n = n;
             }
         }
-        if (b->use_graph) e = cudaGraphLaunch(b->graph, b->stream);
+        if (b->graph) {
+            e = cudaGraphLaunch(b->graph, b->stream);
+            graphed = true;
+        }
     }
-    if (!b->use_graph) e = enqueue(b, n, b->stream);
+    if (!graphed) e = enqueue(b, n, b->stream);
     if (e != cudaSuccess) return bcuda(e, "lbm_batch_step launch");
+    b->last_launch = graphed ? LBM_LAUNCH_GRAPH : LBM_LAUNCH_DIRECT;
     BCK(cudaEventRecord(b->copied, b->stream));
     if (nxs) {
         // Later work on those streams (lbm_moments, lbm_destroy, a step)
@@ -522,6 +538,24 @@ extern "C" int lbm_batch_tune(lbm_batch_t b) {
     }
     rc = lbm_batch_set_walk16(b, best_walk);
     return rc != LBM_OK ? rc : lbm_batch_set_config(b, best_rows, 0);
+}
+
+extern "C" int lbm_batch_set_launch(lbm_batch_t b, int mode) {
+    if (!b || mode < LBM_LAUNCH_AUTO || mode > LBM_LAUNCH_DIRECT)
+        return bfail(LBM_EINVAL, "lbm_batch_set_launch: unknown mode");
+    BCK(cudaStreamSynchronize(b->stream));
+    b->launch_mode = mode;
+    b->capture_failed = false;
+    drop_graph(b);
+    return LBM_OK;
+}
+
+extern "C" int lbm_batch_get_launch(lbm_batch_t b, int *mode, int *last, int *capture_failed) {
+    if (!b) return bfail(LBM_EINVAL, "lbm_batch_get_launch: NULL batch");
+    if (mode) *mode = b->launch_mode;
+    if (last) *last = b->last_launch;
+    if (capture_failed) *capture_failed = b->capture_failed ? 1 : 0;
+    return LBM_OK;
 }
 
 extern "C" int lbm_batch_get_config(lbm_batch_t b, int *rows, int *blocks_per_sm,

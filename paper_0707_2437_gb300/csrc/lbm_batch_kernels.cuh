@@ -128,7 +128,7 @@ template <int S, int V, bool PF = false, int RND = 0, int VA = 0>
 __device__ __noinline__ void do_tile(const GridDesc &g, int par, const Tile &t, uint32_t step) {
     Walker<S, V, LD_CG, RND, VA> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P, t.x0);
     if constexpr (VA) w.a15f = g.a15f;
-    if constexpr (RND) w.rstep = step;
+    if constexpr (RND) w.set_step(step);
     if constexpr (PF)
         w.run_prefetch(t.y0, t.y1, t.dir, g.c);
     else
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(32 * kBatchWarps, PD == 2 ? 3 : 4)
             const Coef c = g.c;
             Walker<S, V, LD_CG, RND, VA> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P, t.x0);
             if constexpr (VA) w.a15f = g.a15f;
-            if constexpr (RND) w.rstep = t0[t.grid] + (uint32_t)k;
+            if constexpr (RND) w.set_step(t0[t.grid] + (uint32_t)k);
             if constexpr (S != ST_F32 && V == 8)
                 w.run_async(t.y0, t.y1, t.dir, c, &rowbuf[threadIdx.x >> 5][0]);
             else if constexpr (PD == 2)

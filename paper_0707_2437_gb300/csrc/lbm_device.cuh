@@ -244,7 +244,7 @@ __device__ __forceinline__ uint32_t pack1(float v) {
 // a stored value that changes by less than half a unit in the last place per
 // step never changes at all, which freezes slow processes such as the viscous
 // decay of long shear waves.  Stochastic rounding rounds up with probability
-// equal to the discarded fraction (resolved to 1/256 here), so the expected
+// equal to the discarded fraction (as many random bits as dropped bits), so the expected
 // stored value equals the FP32 result.  The random bits are a counter-based
 // hash of (site, step): deterministic, and independent of the tile
 // configuration and of batching, so results stay bitwise reproducible.
@@ -267,7 +267,11 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
 // are deterministic and independent of tile shape, sites per lane and
 // batching (with 2, 4 or 8 sites per lane nx is even, so the two sites of a
 // packed word are always such a pair; a 1-site lane takes its half).  The
-// pair hash is the full mix; the nine direction words use a lighter one.
+// pair hash is the full mix.  A direction's word is that hash times an odd
+// constant of its own (a bijection of the 32-bit words, different for every
+// direction), with the high half folded into the low one so that the low
+// bits, which FP16 uses, depend on every bit of the hash: three instructions
+// per word.
 __device__ __forceinline__ uint32_t sr_step_key(uint32_t step) {
     return mix32(step * 0x9e3779b9u + 0x632be5abu);
 }
@@ -275,11 +279,8 @@ __device__ __forceinline__ uint32_t sr_pair_base(uint32_t site, uint32_t key) {
     return mix32((site >> 1) ^ key);
 }
 __device__ __forceinline__ uint32_t sr_word(uint32_t base, int i) {
-    uint32_t x = base + (uint32_t)(i + 1) * 0x85ebca6bu;
-    x ^= x >> 16;
-    x *= 0x7feb352du;
-    x ^= x >> 15;
-    return x;
+    const uint32_t x = base * (0x9e3779b9u + 2u * (uint32_t)i * 0x6a09e667u);
+    return x ^ (x >> 16);
 }
 
 // FP32 -> 16-bit with round up probability equal to the discarded fraction,
@@ -434,7 +435,8 @@ struct Walker {
     static constexpr int NW = Pack<S, V>::NW;
     using T = typename StoreT<S>::T;
     static_assert(RND == 0 || S != ST_F32, "stochastic rounding applies to 16-bit storage");
-    uint32_t rstep = 0;  // step number that seeds stochastic rounding
+    uint32_t rkey = 0;  // sr_step_key of the step number (stochastic rounding)
+    __device__ __forceinline__ void set_step(uint32_t step) { rkey = sr_step_key(step); }
     // Spatially varying sound speed (VA = 1): 1.5 alpha per site, [ny][nx].
     const float *__restrict__ a15f = nullptr;
 
@@ -542,7 +544,7 @@ struct Walker {
             }
         } else {
             const uint32_t site = (uint32_t)r * (uint32_t)nx + (uint32_t)(xs + v0);
-            const uint32_t base = sr_pair_base(site, sr_step_key(rstep));
+            const uint32_t base = sr_pair_base(site, rkey);
             if constexpr (SP == 2) {
                 // site is even: the word's two sites are the pair (site, site + 1)
 #pragma unroll

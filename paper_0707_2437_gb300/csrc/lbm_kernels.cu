@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256, 2)
     if constexpr (VA) w.a15f = a15f;
     // Stochastic rounding is seeded by the step being computed: a device
     // counter (set before each graph replay) plus this launch's offset.
-    if constexpr (RND) w.rstep = (tdev ? *tdev : 0u) + toff;
+    if constexpr (RND) w.set_step((tdev ? *tdev : 0u) + toff);
     // Neighbouring segments walk in opposite directions so that the two rows
     // they share are read by both at about the same time.
     if constexpr (PF)

@@ -88,6 +88,9 @@ def load() -> ctypes.CDLL:
             "lbm_batch_get_config": ([vp, ctypes.POINTER(i), ctypes.POINTER(i),
                                       ctypes.POINTER(i)], i),
             "lbm_batch_set_timeout_us": ([vp, ll], i),
+            "lbm_batch_set_launch": ([vp, i], i),
+            "lbm_batch_get_launch": ([vp, ctypes.POINTER(i), ctypes.POINTER(i),
+                                      ctypes.POINTER(i)], i),
             "lbm_sums_noalloc": ([vp, i, i, sz, i, d, vp, dp], i),
             "lbm_strerror": ([i], ctypes.c_char_p),
             "lbm_last_error": ([], ctypes.c_char_p),
@@ -334,6 +337,8 @@ class Grid:
 
 WALK16 = {"auto": 0, "v8": 1, "v4": 2, "v4pf2": 3}
 WALK16_NAMES = {v: k for k, v in WALK16.items()}
+LAUNCH = {"auto": 0, "graph": 1, "direct": 2}
+LAUNCH_NAMES = {v: k for k, v in LAUNCH.items()}
 
 
 class Batch:
@@ -395,3 +400,18 @@ class Batch:
 
     def set_timeout_us(self, us: int):
         _check(self.lib.lbm_batch_set_timeout_us(self.b, int(us)), "lbm_batch_set_timeout_us")
+
+    def set_launch(self, mode: str):
+        """'auto' (graph replay, direct launches if capture fails), 'graph'
+        (capture failure is an error) or 'direct'."""
+        _check(self.lib.lbm_batch_set_launch(self.b, LAUNCH[mode]), "lbm_batch_set_launch")
+
+    def get_launch(self):
+        """{'mode', 'last' ('graph', 'direct' or None before the first step
+        call), 'capture_failed'}."""
+        m, last, cf = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self.lib.lbm_batch_get_launch(self.b, ctypes.byref(m), ctypes.byref(last),
+                                             ctypes.byref(cf)), "lbm_batch_get_launch")
+        return {"mode": LAUNCH_NAMES[m.value],
+                "last": {0: None, 1: "graph", 2: "direct"}[last.value],
+                "capture_failed": bool(cf.value)}

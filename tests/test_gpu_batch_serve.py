@@ -230,3 +230,51 @@ def test_set_stream_keeps_order(lbm):
         got = g.moments()
     for x, y in zip(got, ref):
         assert np.array_equal(x, y)
+
+
+def test_batch_replays_from_cuda_graph(lbm):
+    """The default launch mode replays the batch's persistent launches from a
+    CUDA graph on this GPU (no capture failure), and the graph, forced-graph
+    and direct modes give bitwise the same states."""
+    specs = [(512, 256, 0.8, 0.2, "f32"), (256, 96, 0.6, 0.1, "f16d"), (37, 29, 0.7, 0.3, "f32")]
+
+    def run(mode):
+        grids = []
+        for nx, ny, tau, c2, st in specs:
+            g = lbm.Grid(nx, ny, tau, c2, st)
+            g.init(*workloads.fourier_modes(nx, ny, amp=1e-3, seed=nx))
+            grids.append(g)
+        b = lbm.Batch(grids)
+        assert b.get_launch() == {"mode": "auto", "last": None, "capture_failed": False}
+        if mode != "auto":
+            b.set_launch(mode)
+        b.step(20)
+        b.step(20)
+        assert b.sync() == 0
+        info = b.get_launch()
+        states = [g.get_state()[0] for g in grids]
+        b.close()
+        for g in grids:
+            g.close()
+        return info, states
+
+    auto, s_auto = run("auto")
+    assert auto == {"mode": "auto", "last": "graph", "capture_failed": False}
+    forced, s_graph = run("graph")
+    assert forced["last"] == "graph"
+    direct, s_direct = run("direct")
+    assert direct == {"mode": "direct", "last": "direct", "capture_failed": False}
+    for a, b_, c in zip(s_auto, s_graph, s_direct):
+        assert np.array_equal(a, b_) and np.array_equal(a, c)
+
+
+def test_batch_launch_mode_argument_checks(lbm):
+    g = lbm.Grid(64, 64, 0.8, 0.2)
+    g.init(*workloads.sine_wave(64, 64))
+    b = lbm.Batch([g])
+    for bad in (-1, 3):
+        assert b.lib.lbm_batch_set_launch(b.b, bad) == lbm.LBM_EINVAL
+    with pytest.raises(KeyError):
+        b.set_launch("eager")
+    b.close()
+    g.close()
