@@ -58,18 +58,40 @@ __host__ __device__ constexpr int EYi(int i) {
     return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
 }
 
-// Weights of Section 2 rounded to FP32.
-#define VSS_W0 (4.0f / 9.0f)
-#define VSS_W1 (1.0f / 9.0f)
-#define VSS_W5 (1.0f / 36.0f)
+// Weights of Section 2 in FP32, chosen so that the collision conserves the
+// density and momentum deviations exactly in its linear part: W1 = fl(1/9),
+// W5 = 1/36 on the 2^-27 grid, and W0 = 1 - 4 W1 - 4 W5 (which is 4 W1), so
+// that W0 + 4 W1 + 4 W5 = 1 exactly; each is within 1e-7 of the printed
+// weight.  (Rounded one by one they sum to 1 + 7.5e-9; together with
+// 1 - 1/tau rounded apart from 1/tau, every step then scaled the density and
+// momentum deviations by 1 + O(1e-7), 0.3 % over 40,000 steps.)
+#define VSS_W0 0x1.c71c72p-2f
+#define VSS_W1 0x1.c71c72p-4f
+#define VSS_W5 0x1.c71c7p-6f
+// T = 2 (W1 + 2 W5) = sum_i W_i e_ix^2 (1/3 - 5e-9), exact in double: the
+// momentum a collision adds is T times the antisymmetric part it puts on
+// each link pair.
+#define VSS_T_D 0x1.555555p-2
+// 1 / (2 T): 1.5 alpha scaled so that the force adds momentum alpha grad(rho)
+// with these weights (the 1/2 of the central difference included).
+#define VSS_A15_SCALE_D 0x1.8000006000002p+0
+
+// The per-site force constant alpha / (2 T) in FP32 from alpha in FP64, the
+// same rounding for a grid's uniform alpha (host) and a c2 field (device), so
+// that a uniform field reproduces the uniform run bitwise.
+__host__ __device__ inline float a15_of_alpha(double alpha) {
+    return (float)(alpha * VSS_A15_SCALE_D);
+}
 
 // Per-grid constants of the collision.
 struct Coef {
     float om;    // 1/tau
-    float om1;   // 1 - 1/tau
-    float w3;    // 3/tau
+    float om1;   // 1 - 1/tau; om + om1 == 1 exactly in FP32
+    float w3;    // 3/tau as (1/tau)/T, split into a rounded value ...
+    float w3lo;  // ... and its remainder, so that T (w3 + w3lo) = 1/tau to ~2^-48
     float w45;   // 4.5/tau
-    float a15;   // 1.5 alpha  (3 alpha times the 1/2 of the central difference)
+    float a15;   // alpha / (2 T), about 1.5 alpha (3 alpha times the 1/2 of the
+                 // central difference)
     float rho0;  // reference density of the stored deviations
 };
 
@@ -400,8 +422,8 @@ __device__ __forceinline__ SiteQ site_quantities(float h1, float h2, float h3, f
     float ju = __fmaf_rn(q.jx, q.ux, __fmul_rn(q.jy, q.uy));
     q.wB = __fmul_rn(c.om, __fmaf_rn(-1.5f, ju, dr));
     // Central differences of Section 4: grad = (d(+1) - d(-1))/2; the 1/2 is in a15.
-    q.Ax = __fmaf_rn(c.w3, q.jx, __fmul_rn(a15, __fsub_rn(dxp, dxm)));
-    q.Ay = __fmaf_rn(c.w3, q.jy, __fmul_rn(a15, __fsub_rn(dyp, dym)));
+    q.Ax = __fmaf_rn(c.w3, q.jx, __fmaf_rn(c.w3lo, q.jx, __fmul_rn(a15, __fsub_rn(dxp, dxm))));
+    q.Ay = __fmaf_rn(c.w3, q.jy, __fmaf_rn(c.w3lo, q.jy, __fmul_rn(a15, __fsub_rn(dyp, dym))));
     return q;
 }
 

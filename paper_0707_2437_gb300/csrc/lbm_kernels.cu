@@ -6,15 +6,28 @@
 
 namespace vss {
 
+// The FP32 constants are chosen so that the linear part of the collision
+// conserves the density and momentum deviations exactly (with the weights of
+// lbm_device.cuh): om + om1 == 1 in FP32 (the one of them in [0.5, 2] is
+// rounded, the other is 1 minus it, which is exact there), and the momentum
+// coefficient (1/tau)/T is carried as a rounded value plus its remainder.
 Coef make_coef(double tau, double c2, double rho0) {
     Coef c;
-    double om = 1.0 / tau;
-    double alpha = 1.0 / 3.0 - c2;  // Section 3, Eq. 8 with c_1^2 = 1/3
-    c.om = (float)om;
-    c.om1 = (float)(1.0 - om);
-    c.w3 = (float)(3.0 * om);
-    c.w45 = (float)(4.5 * om);
-    c.a15 = (float)(1.5 * alpha);
+    float om = (float)(1.0 / tau);
+    float om1;
+    if (om >= 0.5f) {
+        om1 = 1.0f - om;  // exact: om in [0.5, 2) for tau in (0.5, 2]
+    } else {
+        om1 = (float)(1.0 - 1.0 / tau);  // in (0.5, 1)
+        om = 1.0f - om1;                  // exact
+    }
+    c.om = om;
+    c.om1 = om1;
+    const double w3 = (double)om / VSS_T_D;
+    c.w3 = (float)w3;
+    c.w3lo = (float)(w3 - (double)c.w3);
+    c.w45 = (float)(4.5 * (double)om);
+    c.a15 = a15_of_alpha(1.0 / 3.0 - c2);  // Section 3, Eq. 8 with c_1^2 = 1/3
     c.rho0 = (float)rho0;
     return c;
 }
@@ -294,7 +307,7 @@ __global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
 __global__ void k_a15_from_c2(const double *c2, float *a15, long long n) {
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n;
          s += (long long)gridDim.x * blockDim.x)
-        a15[s] = (float)(1.5 * (1.0 / 3.0 - c2[s]));
+        a15[s] = a15_of_alpha(1.0 / 3.0 - c2[s]);
 }
 
 Err launch_a15_from_c2(const double *c2, float *a15, long long n, cudaStream_t st) {

@@ -113,7 +113,10 @@ def test_damping_run_alpha_minus_065_matches_oracle(lbm):
           f"rate GPU {rate_gpu:.6e}, oracle {rate_ora:.6e}")
     assert err <= tol
     assert np.abs(a_gpu - a_ora).max() <= tol
-    assert abs(rate_gpu / rate_ora - 1) < 1e-3
+    # Each window mean is within tol of the oracle's, so the log ratio of the
+    # two windows, and with it rate * span, is within 2 tol / (smaller mean).
+    a_min = min(a_ora[1:17].mean(), a_ora[18:].mean())
+    assert abs(rate_gpu - rate_ora) * span <= 2 * tol / a_min
 
 
 @pytest.mark.parametrize("run", [7, 8])
