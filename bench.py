@@ -158,11 +158,13 @@ def serve_comparison(args, stream=None):
                                steps_hi=args.serve_steps_hi)
     overlap = not args.serve_no_overlap
 
-    def server():
-        return serve.Server(quantum=args.serve_quantum, overlap=overlap)
+    def server(schedule="lockstep"):
+        return serve.Server(quantum=args.serve_quantum, overlap=overlap, schedule=schedule,
+                            flow_updates=args.serve_flow_updates)
 
     warm = serve.scaled_trace(8, 1000.0, seed=99, hi=256, steps_hi=2000)
     server().run(warm, realtime=False)
+    server("flow").run(warm, realtime=False)
     srv = server().run(trace, realtime=True).summary()
     out = {"trace": f"{args.serve_count} requests, Poisson {args.serve_rate}/s, sites "
                     f"log-uniform 128^2..2048^2, steps U{{1000..{args.serve_steps_hi}}}, "
@@ -181,6 +183,13 @@ def serve_comparison(args, stream=None):
     trace07 = serve.scaled_trace(args.serve_count, rate07, steps_hi=args.serve_steps_hi)
     srv07 = server().run(trace07, realtime=True).summary()
     out["at_0.7_capacity"] = {"rate_hz": rate07, "continuous_batching": srv07}
+    if not args.serve_no_flow:
+        # The same two traces with the flow schedule (each grid advances on
+        # its own; launches share a budget of lattice updates equally).
+        out["continuous_batching_flow"] = server("flow").run(trace, realtime=True).summary()
+        out["at_0.7_capacity"]["continuous_batching_flow"] = server("flow").run(
+            trace07, realtime=True).summary()
+        out["flow_updates_per_launch"] = args.serve_flow_updates
     if not (args.serve_no_fifo07 or args.serve_skip_fifo):
         fifo07 = serve.serve_fifo(trace07, realtime=True).summary()
         out["at_0.7_capacity"]["fifo_f32"] = fifo07
@@ -306,6 +315,8 @@ def run_native(args):
     stages, pipelined = grids[0].get_pipeline()
     sites = sum(r.nx * r.ny for r in runs)
     batch = lbm.Batch(grids) if args.path == "batch" else None
+    if batch is not None and args.schedule != "lockstep":
+        batch.set_schedule(args.schedule)
     if batch is not None and args.walk16:
         batch.set_walk16(args.walk16)
     if batch is not None and args.batch_rows:
@@ -540,6 +551,7 @@ def run_native(args):
                             "(batch API, grid barrier between steps)"
                             if batch is not None else "one step-kernel launch per grid and step"),
                    "steps_per_launch": spl,
+                   "schedule": args.schedule if batch is not None else None,
                    "batch_config": batch.get_config() if batch is not None else None,
                    "batch_launch": batch.get_launch() if batch is not None else None,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
@@ -681,6 +693,8 @@ def batch512_run(args, storage: str, rounding: str, steps: int, warmup: int, str
         g.init(*workloads.sine_wave(r.nx, r.ny, r.amp, r.mode))
         grids.append(g)
     b = lbm.Batch(grids)
+    if args.schedule != "lockstep":
+        b.set_schedule(args.schedule)
     if args.batch_rows:
         b.set_config(args.batch_rows, 0)
     if args.walk16:
@@ -757,6 +771,7 @@ def run_batch_workload(args):
         "config": {"workload": f"batch of {r['grids']} uneven grids, sites log-uniform "
                                "64^2..1024^2, aspect 2^U[-2,2]",
                    "sites": r["sites"], "storage": args.storage, "rounding": args.rounding,
+                   "schedule": args.schedule,
                    "l2": f"working set {r['alg_bytes_per_step'] / 1e9:.1f} GB >> 129 MB L2, "
                          "no flush"},
         "launch": {"batch_config": r["batch_config"], "batch_launch": r["batch_launch"],
@@ -793,6 +808,7 @@ def run_serve_workload(args):
                                f"sites log-uniform 128^2..2048^2, steps U{{1000..{args.serve_steps_hi}}}",
                    "quantum_steps": args.serve_quantum},
         "served": srv, "fifo_f32": fifo, "at_0.7_capacity": cmp_["at_0.7_capacity"],
+        "served_flow": cmp_.get("continuous_batching_flow"),
         "clocks": clk,
     }
     if rank == 0:
@@ -827,6 +843,12 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-steps-hi", type=int, default=5000)
     ap.add_argument("--serve-quantum", type=int, default=256)
+    ap.add_argument("--schedule", default="lockstep", choices=["lockstep", "flow"],
+                    help="batch schedule on the batch paths (flow: no barrier across grids)")
+    ap.add_argument("--serve-no-flow", action="store_true",
+                    help="skip the flow-schedule server in the serving comparison")
+    ap.add_argument("--serve-flow-updates", type=float, default=2e9,
+                    help="lattice updates per launch shared by the flow-schedule server")
     ap.add_argument("--serve-no-overlap", action="store_true",
                     help="admit requests between quanta instead of during them")
     ap.add_argument("--serve-skip-fifo", action="store_true",

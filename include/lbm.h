@@ -337,6 +337,28 @@ int lbm_batch_get_groups(lbm_batch_t b, int *groups);
 int lbm_batch_set_walk16(lbm_batch_t b, int walk);
 int lbm_batch_get_walk16(lbm_batch_t b, int *walk);
 
+/* Schedule of lbm_batch_step:
+ *   LBM_SCHEDULE_LOCKSTEP  the default: one persistent launch per kind group
+ *                          runs every time step of all its grids, with a
+ *                          grid-wide barrier between steps
+ *   LBM_SCHEDULE_FLOW      one launch over all grids with no barrier: each
+ *                          grid advances on its own, a tile's step starting
+ *                          as soon as the tiles it reads from have finished
+ *                          the previous step (per-tile progress counters,
+ *                          bounded waits).  Warps share the GPU round-robin
+ *                          between grids, so a small grid takes many steps
+ *                          while a large one takes few: each grid's
+ *                          time-to-result follows its own size instead of the
+ *                          whole batch's.  Every call still runs until each
+ *                          grid has taken min(n, limits[g]) steps; n at most
+ *                          2^31 - 1.
+ * Every grid reaches bitwise the same state in both schedules.  Waits for the
+ * batch's stream; LBM_EINVAL for other values. */
+#define LBM_SCHEDULE_LOCKSTEP 0
+#define LBM_SCHEDULE_FLOW 1
+int lbm_batch_set_schedule(lbm_batch_t b, int schedule);
+int lbm_batch_get_schedule(lbm_batch_t b, int *schedule);
+
 /* How lbm_batch_step issues its persistent launches:
  *   LBM_LAUNCH_AUTO    the default: the launches of a call (one per kind group,
  *                      with their parameter copies) are captured once per step

@@ -73,6 +73,15 @@ struct lbm_batch {
     int launch_mode = LBM_LAUNCH_AUTO;
     bool capture_failed = false;
     int last_launch = 0;
+    // Schedule (lbm_batch_set_schedule): lockstep kind groups, or one flow
+    // launch over all grids with per-tile progress (control words per grid,
+    // completed steps per tile, and the count of grids with work this call).
+    int schedule = LBM_SCHEDULE_LOCKSTEP;
+    unsigned long long *d_ctl = nullptr;
+    int *d_prog = nullptr;
+    size_t prog_cap = 0;
+    int *d_nwork = nullptr;
+    int *h_nwork = nullptr;
 };
 
 static int bfail(int code, const std::string &m) {
@@ -110,6 +119,26 @@ static int batch_vec(const lbm_batch *b, const lbm_grid *g) {
     return g->nx % 4 == 0 ? 4 : 1;
 }
 
+// Copies the grid table and the tile list to the device.
+static int upload_worklist(lbm_batch *b, const std::vector<GridDesc> &gd,
+                           const std::vector<Tile> &ordered) {
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    b->d_tiles = nullptr;
+    BCK(cudaMalloc(&b->d_tiles, sizeof(Tile) * std::max<size_t>(1, ordered.size())));
+    BCK(cudaMemcpy(b->d_grids, gd.data(), sizeof(GridDesc) * gd.size(), cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(b->d_tiles, ordered.data(), sizeof(Tile) * ordered.size(),
+                   cudaMemcpyHostToDevice));
+    b->ntiles = (int)ordered.size();
+    b->built_a15f.clear();
+    b->built_rounding.clear();
+    for (const lbm_grid *g : b->grids) {
+        b->built_a15f.push_back(g->a15f);
+        b->built_rounding.push_back(g->rounding);
+    }
+    drop_graph(b);
+    return LBM_OK;
+}
+
 // (Re)builds the device grid table and the tile work-list.
 static int build_worklist(lbm_batch *b) {
     std::vector<GridDesc> gd(b->grids.size());
@@ -128,12 +157,46 @@ static int build_worklist(lbm_batch *b) {
         d.pad = 0;
         d.c = g->coef;
         int w = 32 * v;
+        d.tile0 = (int)tiles.size();
+        d.nstrips = (g->nx + w - 1) / w;
+        d.nsegs = (g->ny + b->rows - 1) / b->rows;
+        d.ntile = d.nstrips * d.nsegs;
+        // A step reads two rows and two columns beyond its tile: the next
+        // segment or strip over suffices unless one of them is a single row
+        // or column wide (the last one of a grid can be).
+        const int last_rows = g->ny - (d.nsegs - 1) * b->rows;
+        const int last_cols = g->nx - (d.nstrips - 1) * w;
+        d.dseg = (b->rows >= 2 && last_rows >= 2) ? 1 : 2;
+        d.dstrip = last_cols >= 2 ? 1 : 2;
         // Neighbouring segments walk in opposite directions, so the rows they
         // share are read by both at about the same time (from L2 the second time).
         for (int y0 = 0, seg = 0; y0 < g->ny; y0 += b->rows, ++seg)
             for (int x0 = 0; x0 < g->nx; x0 += w)
                 tiles.push_back(Tile{(int)k, x0, y0, std::min(g->ny, y0 + b->rows),
                                      (seg & 1) ? -1 : 1});
+    }
+    if (b->schedule == LBM_SCHEDULE_FLOW) {
+        // One launch over every grid, tiles grid by grid in their order.
+        b->groups.clear();
+        lbm_batch::Group gr;
+        gr.begin = 0;
+        gr.count = (int)tiles.size();
+        gr.kernel = nullptr;
+        BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gr.max_blocks_per_sm,
+                                                          (const void *)k_flow,
+                                                          32 * kBatchWarps, 0));
+        if (gr.max_blocks_per_sm < 1) return bfail(LBM_ECUDA, "flow kernel cannot be resident");
+        b->groups.push_back(gr);
+        if (tiles.size() > b->prog_cap) {
+            cudaFree(b->d_prog);
+            b->d_prog = nullptr;
+            BCK(cudaMalloc(&b->d_prog, sizeof(int) * tiles.size()));
+            b->prog_cap = tiles.size();
+        }
+        if (!b->d_ctl)
+            BCK(cudaMalloc(&b->d_ctl, sizeof(unsigned long long) * kFlowCtlWords *
+                                          b->grids.size()));
+        return upload_worklist(b, gd, tiles);
     }
     // Kind groups.  A kind with a specialised kernel runs in its own launch
     // when its grids move at least kOwnLaunchBytes per step (about 10 us of
@@ -188,21 +251,7 @@ static int build_worklist(lbm_batch *b) {
         int rc = add_group(rest);
         if (rc != LBM_OK) return rc;
     }
-    if (b->d_tiles) cudaFree(b->d_tiles);
-    b->d_tiles = nullptr;
-    BCK(cudaMalloc(&b->d_tiles, sizeof(Tile) * std::max<size_t>(1, ordered.size())));
-    BCK(cudaMemcpy(b->d_grids, gd.data(), sizeof(GridDesc) * gd.size(), cudaMemcpyHostToDevice));
-    BCK(cudaMemcpy(b->d_tiles, ordered.data(), sizeof(Tile) * ordered.size(),
-                   cudaMemcpyHostToDevice));
-    b->ntiles = (int)ordered.size();
-    b->built_a15f.clear();
-    b->built_rounding.clear();
-    for (const lbm_grid *g : b->grids) {
-        b->built_a15f.push_back(g->a15f);
-        b->built_rounding.push_back(g->rounding);
-    }
-    drop_graph(b);
-    return LBM_OK;
+    return upload_worklist(b, gd, ordered);
 }
 
 extern "C" int lbm_batch_destroy(lbm_batch_t b) {
@@ -216,6 +265,10 @@ extern "C" int lbm_batch_destroy(lbm_batch_t b) {
     cudaFree(b->d_t0);
     cudaFree(b->d_bar);
     cudaFree(b->d_status);
+    cudaFree(b->d_ctl);
+    cudaFree(b->d_prog);
+    cudaFree(b->d_nwork);
+    if (b->h_nwork) cudaFreeHost(b->h_nwork);
     if (b->h_limit) cudaFreeHost(b->h_limit);
     if (b->h_parity) cudaFreeHost(b->h_parity);
     if (b->h_t0) cudaFreeHost(b->h_t0);
@@ -258,6 +311,8 @@ extern "C" int lbm_batch_create(const lbm_t *grids, int n, lbm_batch_t *out) {
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_parity, sizeof(int) * n);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_t0, sizeof(uint32_t) * n);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_nwork, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_nwork, sizeof(int));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
@@ -300,6 +355,19 @@ static cudaError_t enqueue(lbm_batch *b, long long n, cudaStream_t st) {
     unsigned *bar = b->d_bar;
     int *status = b->d_status;
     unsigned long long to = b->timeout_ns;
+    if (b->schedule == LBM_SCHEDULE_FLOW) {
+        e = cudaMemcpyAsync(b->d_nwork, b->h_nwork, sizeof(int), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(b->d_ctl, 0,
+                                sizeof(unsigned long long) * kFlowCtlWords * ng, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_prog, 0, sizeof(int) * b->ntiles, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned) * kBarWords, st);
+        if (e != cudaSuccess) return e;
+        k_flow<<<grid_blocks(b, b->groups[0]), 32 * kBatchWarps, 0, st>>>(
+            grids, ng, b->d_tiles, lim, par, t0, b->d_ctl, b->d_prog, bar, b->d_nwork, status,
+            to);
+        return cudaGetLastError();
+    }
     // The groups hold disjoint grids: each launch advances its grids by all n
     // steps.  Barrier words and tile counters start at zero for every launch.
     for (const lbm_batch::Group &gr : b->groups) {
@@ -321,12 +389,15 @@ static int run_batch(lbm_batch *b, long long n, const long long *limits, bool ad
     int ng = (int)b->grids.size();
     // The previous call's copies must have read the pinned arrays first.
     BCK(cudaEventSynchronize(b->copied));
+    int nwork = 0;
     for (int k = 0; k < ng; ++k) {
         long long lim = limits ? std::max(0LL, std::min(n, limits[k])) : n;
         b->h_limit[k] = lim;
         b->h_parity[k] = b->grids[k]->cur;
         b->h_t0[k] = (uint32_t)b->grids[k]->t;
+        nwork += lim > 0;
     }
+    *b->h_nwork = nwork;
     // Work already queued on the members' own streams (an lbm_init, a step
     // call) runs before the batch's launches.
     int nxs = 0;
@@ -402,6 +473,8 @@ static int run_batch(lbm_batch *b, long long n, const long long *limits, bool ad
 
 extern "C" int lbm_batch_step(lbm_batch_t b, long long n, const long long *limits) {
     if (!b || n < 0) return bfail(LBM_EINVAL, "lbm_batch_step: bad argument");
+    if (b->schedule == LBM_SCHEDULE_FLOW && n > 0x7fffffffLL)
+        return bfail(LBM_EINVAL, "lbm_batch_step: flow schedule takes at most 2^31 - 1 steps a call");
     if (n == 0) return LBM_OK;
     bool stale = false;
     for (size_t k = 0; k < b->grids.size(); ++k) {
@@ -540,6 +613,21 @@ extern "C" int lbm_batch_tune(lbm_batch_t b) {
     return rc != LBM_OK ? rc : lbm_batch_set_config(b, best_rows, 0);
 }
 
+extern "C" int lbm_batch_set_schedule(lbm_batch_t b, int schedule) {
+    if (!b || schedule < LBM_SCHEDULE_LOCKSTEP || schedule > LBM_SCHEDULE_FLOW)
+        return bfail(LBM_EINVAL, "lbm_batch_set_schedule: unknown schedule");
+    BCK(cudaStreamSynchronize(b->stream));
+    if (schedule == b->schedule) return LBM_OK;
+    b->schedule = schedule;
+    return build_worklist(b);
+}
+
+extern "C" int lbm_batch_get_schedule(lbm_batch_t b, int *schedule) {
+    if (!b || !schedule) return bfail(LBM_EINVAL, "lbm_batch_get_schedule: bad argument");
+    *schedule = b->schedule;
+    return LBM_OK;
+}
+
 extern "C" int lbm_batch_set_launch(lbm_batch_t b, int mode) {
     if (!b || mode < LBM_LAUNCH_AUTO || mode > LBM_LAUNCH_DIRECT)
         return bfail(LBM_EINVAL, "lbm_batch_set_launch: unknown mode");
@@ -567,7 +655,7 @@ extern "C" int lbm_batch_get_config(lbm_batch_t b, int *rows, int *blocks_per_sm
     if (specialised) {
         *specialised = 1;
         for (const auto &gr : b->groups)
-            if (gr.kernel == (BatchKernel)k_batch) *specialised = 0;
+            if (gr.kernel == (BatchKernel)k_batch || gr.kernel == nullptr) *specialised = 0;
     }
     return LBM_OK;
 }

@@ -33,6 +33,11 @@ struct GridDesc {
     int kind;  // kind_code(storage, vec, stochastic rounding)
     int pad;
     Coef c;
+    // Tiles of the grid in the work-list (flow schedule): the first one, how
+    // many per step (segment-major: t = segment * nstrips + strip), and how
+    // many segments / strips on each side a tile's step reads from (1, or 2
+    // when a neighbouring segment or strip can be a single row or column).
+    int tile0, ntile, nstrips, nsegs, dseg, dstrip;
 };
 
 struct Tile {
@@ -135,6 +140,75 @@ __device__ __noinline__ void do_tile(const GridDesc &g, int par, const Tile &t, 
         w.run(t.y0, t.y1, t.dir, g.c);
 }
 
+// One tile of any kind (the walks out of line: one kernel for every mix).
+__device__ __forceinline__ void any_tile(const GridDesc &g, int par, const Tile &t,
+                                         uint32_t step) {
+    switch (g.kind) {
+        case kind_code(ST_F32, 4, 0):
+            do_tile<ST_F32, 4>(g, par, t, step);
+            break;
+        case kind_code(ST_F32, 1, 0):
+            do_tile<ST_F32, 1>(g, par, t, step);
+            break;
+        case kind_code(ST_F16, 8, 0):
+            do_tile<ST_F16, 8>(g, par, t, step);
+            break;
+        case kind_code(ST_F16, 4, 0):
+            do_tile<ST_F16, 4, true>(g, par, t, step);
+            break;
+        case kind_code(ST_F16, 1, 0):
+            do_tile<ST_F16, 1>(g, par, t, step);
+            break;
+        case kind_code(ST_BF16, 8, 0):
+            do_tile<ST_BF16, 8>(g, par, t, step);
+            break;
+        case kind_code(ST_BF16, 4, 0):
+            do_tile<ST_BF16, 4, true>(g, par, t, step);
+            break;
+        case kind_code(ST_BF16, 1, 0):
+            do_tile<ST_BF16, 1>(g, par, t, step);
+            break;
+        case kind_code(ST_F16, 8, 1):
+            do_tile<ST_F16, 8, false, 1>(g, par, t, step);
+            break;
+        case kind_code(ST_F16, 4, 1):
+            do_tile<ST_F16, 4, true, 1>(g, par, t, step);
+            break;
+        case kind_code(ST_F16, 1, 1):
+            do_tile<ST_F16, 1, false, 1>(g, par, t, step);
+            break;
+        case kind_code(ST_BF16, 8, 1):
+            do_tile<ST_BF16, 8, false, 1>(g, par, t, step);
+            break;
+        case kind_code(ST_BF16, 4, 1):
+            do_tile<ST_BF16, 4, true, 1>(g, par, t, step);
+            break;
+        case kind_code(ST_BF16, 1, 1):
+            do_tile<ST_BF16, 1, false, 1>(g, par, t, step);
+            break;
+        case kind_code(ST_F32, 4, 0, 1):
+            do_tile<ST_F32, 4, false, 0, 1>(g, par, t, step);
+            break;
+        case kind_code(ST_F32, 1, 0, 1):
+            do_tile<ST_F32, 1, false, 0, 1>(g, par, t, step);
+            break;
+        case kind_code(ST_F16, 4, 0, 1):
+            do_tile<ST_F16, 4, true, 0, 1>(g, par, t, step);
+            break;
+        case kind_code(ST_F16, 1, 0, 1):
+            do_tile<ST_F16, 1, false, 0, 1>(g, par, t, step);
+            break;
+        case kind_code(ST_BF16, 4, 0, 1):
+            do_tile<ST_BF16, 4, true, 0, 1>(g, par, t, step);
+            break;
+        case kind_code(ST_BF16, 1, 0, 1):
+            do_tile<ST_BF16, 1, false, 0, 1>(g, par, t, step);
+            break;
+        default:
+            break;
+    }
+}
+
 __global__ void __launch_bounds__(32 * kBatchWarps, 3)
     k_batch(const GridDesc *__restrict__ grids, const Tile *__restrict__ tiles, int ntiles,
             const long long *__restrict__ limit, const int *__restrict__ parity0,
@@ -149,72 +223,156 @@ __global__ void __launch_bounds__(32 * kBatchWarps, 3)
             const GridDesc &g = grids[t.grid];
             const int par = (parity0[t.grid] + (int)(k & 1)) & 1;
             const uint32_t step = t0[t.grid] + (uint32_t)k;
-            switch (g.kind) {
-                case kind_code(ST_F32, 4, 0):
-                    do_tile<ST_F32, 4>(g, par, t, step);
-                    break;
-                case kind_code(ST_F32, 1, 0):
-                    do_tile<ST_F32, 1>(g, par, t, step);
-                    break;
-                case kind_code(ST_F16, 8, 0):
-                    do_tile<ST_F16, 8>(g, par, t, step);
-                    break;
-                case kind_code(ST_F16, 4, 0):
-                    do_tile<ST_F16, 4, true>(g, par, t, step);
-                    break;
-                case kind_code(ST_F16, 1, 0):
-                    do_tile<ST_F16, 1>(g, par, t, step);
-                    break;
-                case kind_code(ST_BF16, 8, 0):
-                    do_tile<ST_BF16, 8>(g, par, t, step);
-                    break;
-                case kind_code(ST_BF16, 4, 0):
-                    do_tile<ST_BF16, 4, true>(g, par, t, step);
-                    break;
-                case kind_code(ST_BF16, 1, 0):
-                    do_tile<ST_BF16, 1>(g, par, t, step);
-                    break;
-                case kind_code(ST_F16, 8, 1):
-                    do_tile<ST_F16, 8, false, 1>(g, par, t, step);
-                    break;
-                case kind_code(ST_F16, 4, 1):
-                    do_tile<ST_F16, 4, true, 1>(g, par, t, step);
-                    break;
-                case kind_code(ST_F16, 1, 1):
-                    do_tile<ST_F16, 1, false, 1>(g, par, t, step);
-                    break;
-                case kind_code(ST_BF16, 8, 1):
-                    do_tile<ST_BF16, 8, false, 1>(g, par, t, step);
-                    break;
-                case kind_code(ST_BF16, 4, 1):
-                    do_tile<ST_BF16, 4, true, 1>(g, par, t, step);
-                    break;
-                case kind_code(ST_BF16, 1, 1):
-                    do_tile<ST_BF16, 1, false, 1>(g, par, t, step);
-                    break;
-                case kind_code(ST_F32, 4, 0, 1):
-                    do_tile<ST_F32, 4, false, 0, 1>(g, par, t, step);
-                    break;
-                case kind_code(ST_F32, 1, 0, 1):
-                    do_tile<ST_F32, 1, false, 0, 1>(g, par, t, step);
-                    break;
-                case kind_code(ST_F16, 4, 0, 1):
-                    do_tile<ST_F16, 4, true, 0, 1>(g, par, t, step);
-                    break;
-                case kind_code(ST_F16, 1, 0, 1):
-                    do_tile<ST_F16, 1, false, 0, 1>(g, par, t, step);
-                    break;
-                case kind_code(ST_BF16, 4, 0, 1):
-                    do_tile<ST_BF16, 4, true, 0, 1>(g, par, t, step);
-                    break;
-                case kind_code(ST_BF16, 1, 0, 1):
-                    do_tile<ST_BF16, 1, false, 0, 1>(g, par, t, step);
-                    break;
-                default:
-                    break;
-            }
+            any_tile(g, par, t, step);
         }
         if (k + 1 < nsteps && !grid_barrier(bar, status, timeout_ns)) return;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Flow schedule: every grid advances its own steps, with no barrier across
+// the batch.  Each grid hands out tickets m = k * ntile + t (step k, tile t)
+// from its own counter, in step order.  A warp holding (k, t) waits until
+// every tile its step reads from or overwrites (the tiles within dseg
+// segments and dstrip strips, wrapped, itself included) has completed step
+// k - 1, runs the tile, and publishes k + 1 completed steps for it.  All
+// tickets a wait depends on are earlier tickets of the same grid, already
+// taken by warps that are running and never wait on later ones, so the
+// kernel needs no co-residency guarantee and cannot deadlock.
+//
+// Warps pick grids round-robin, so every grid gets about the same number of
+// tiles per unit time: small grids take many steps while large ones take
+// few, instead of every grid waiting for the whole batch at every step.  A
+// grid's tickets may run at most kFlowWindow steps ahead of its completed
+// tiles, so that the warps a short grid's step chain would hold waiting go to
+// other grids.
+//
+// Control words (zeroed before each launch): per grid, tickets taken and
+// tiles completed (64-bit, each on its own 128-byte line); globally the
+// round-robin counter and the number of grids whose last ticket is taken.
+// Every wait is bounded by the same wall-clock limit as the barrier.
+constexpr int kFlowWindow = 2;
+constexpr int kFlowCtlWords = 32;  // unsigned long long words per grid: [0] taken, [16] done
+constexpr int kFlowRR = 0;         // words of `glob`
+constexpr int kFlowExh = 32;
+
+__device__ __forceinline__ int wrap_idx(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+// Waits until the tiles step k of tile (seg, strip) depends on have
+// completed k steps.  False if the wait ran out or another warp reported one.
+__device__ __forceinline__ bool flow_wait(const GridDesc &g, const int *prog, int seg, int strip,
+                                          int k, int *status, unsigned long long timeout_ns) {
+    if (k == 0) return true;
+    const int lane = threadIdx.x & 31;
+    const int ns = 2 * g.dseg + 1, nt = 2 * g.dstrip + 1;
+    int idx = -1;
+    if (lane < ns * nt) {
+        const int sq = wrap_idx(seg + lane / nt - g.dseg, g.nsegs);
+        const int st = wrap_idx(strip + lane % nt - g.dstrip, g.nstrips);
+        idx = g.tile0 + sq * g.nstrips + st;
+    }
+    unsigned long long t0 = 0;
+    unsigned ns_sleep = 32;
+    for (unsigned it = 0;; ++it) {
+        const bool ok = idx < 0 || *(volatile const int *)(prog + idx) >= k;
+        if (__all_sync(FULL, ok)) break;
+        if (it == 0) t0 = global_ns();
+        if ((it & 7u) == 7u) {
+            int bad = 0;
+            if (lane == 0) {
+                if (*(volatile int *)status != 0) {
+                    bad = 1;
+                } else if (global_ns() - t0 > timeout_ns) {
+                    atomicCAS(status, 0, LBM_ETIMEOUT);
+                    bad = 1;
+                }
+            }
+            if (__shfl_sync(FULL, bad, 0)) return false;
+        }
+        __nanosleep(ns_sleep);
+        if (ns_sleep < 512u) ns_sleep *= 2u;
+    }
+    __threadfence();  // the flags are read before the tiles' data
+    return true;
+}
+
+__global__ void __launch_bounds__(32 * kBatchWarps, 3)
+    k_flow(const GridDesc *__restrict__ grids, int ngrids, const Tile *__restrict__ tiles,
+           const long long *__restrict__ limit, const int *__restrict__ parity0,
+           const uint32_t *__restrict__ t0, unsigned long long *ctl, int *prog, unsigned *glob,
+           const int *__restrict__ nwork_p, int *status, unsigned long long timeout_ns) {
+    const int lane = threadIdx.x & 31;
+    const int nwork = *nwork_p;  // grids with steps to take in this launch
+    unsigned long long idle_since = 0;
+    for (;;) {
+        // Lane 0 takes a ticket from the next grid round-robin that has
+        // tickets left and room in its window; -1: none right now; -2: done.
+        int gsel = -1;
+        unsigned long long m = 0;
+        if (lane == 0) {
+            if (*(volatile int *)status != 0) {
+                gsel = -2;
+            } else {
+                const unsigned start = atomicAdd(glob + kFlowRR, 1u);
+                for (int j = 0; j < ngrids && gsel == -1; ++j) {
+                    const int cand = (int)((start + (unsigned)j) % (unsigned)ngrids);
+                    const GridDesc &G = grids[cand];
+                    const unsigned long long total =
+                        (unsigned long long)limit[cand] * (unsigned long long)G.ntile;
+                    volatile unsigned long long *c = ctl + (size_t)cand * kFlowCtlWords;
+                    const unsigned long long taken = c[0];
+                    if (taken >= total) continue;
+                    if (taken - c[16] >= (unsigned long long)kFlowWindow * G.ntile) continue;
+                    const unsigned long long mm =
+                        atomicAdd(ctl + (size_t)cand * kFlowCtlWords, 1ULL);
+                    if (mm >= total) continue;
+                    if (mm + 1 == total) atomicAdd(glob + kFlowExh, 1u);
+                    gsel = cand;
+                    m = mm;
+                }
+                if (gsel == -1 && *(volatile unsigned *)(glob + kFlowExh) >= (unsigned)nwork)
+                    gsel = -2;
+            }
+        }
+        gsel = __shfl_sync(FULL, gsel, 0);
+        if (gsel == -2) return;
+        if (gsel == -1) {
+            // Every grid with tickets left is at the end of its window: wait
+            // for tiles to complete (bounded, in case progress has stopped).
+            int bad = 0;
+            if (lane == 0) {
+                const unsigned long long now = global_ns();
+                if (idle_since == 0) {
+                    idle_since = now;
+                } else if (now - idle_since > timeout_ns) {
+                    atomicCAS(status, 0, LBM_ETIMEOUT);
+                    bad = 1;
+                }
+            }
+            if (__shfl_sync(FULL, bad, 0)) return;
+            __nanosleep(256);
+            continue;
+        }
+        idle_since = 0;
+        m = __shfl_sync(FULL, m, 0);
+        const GridDesc &g = grids[gsel];
+        const int k = (int)(m / (unsigned long long)g.ntile);
+        const int ti = (int)(m % (unsigned long long)g.ntile);
+        const int seg = ti / g.nstrips, strip = ti % g.nstrips;
+        if (!flow_wait(g, prog, seg, strip, k, status, timeout_ns)) return;
+        const Tile t = tiles[g.tile0 + ti];
+        const int par = (parity0[gsel] + k) & 1;
+        any_tile(g, par, t, t0[gsel] + (uint32_t)k);
+        // Publish: the tile's stores before its completed-step count.
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) {
+            *(volatile int *)(prog + g.tile0 + ti) = k + 1;
+            atomicAdd(ctl + (size_t)gsel * kFlowCtlWords + 16, 1ULL);
+        }
     }
 }
 
@@ -262,6 +420,7 @@ __global__ void __launch_bounds__(32 * kBatchWarps, PD == 2 ? 3 : 4)
 
 using BatchKernel = void (*)(const GridDesc *, const Tile *, int, const long long *, const int *,
                              const uint32_t *, long long, unsigned *, int *, unsigned long long);
+
 
 // The kernel for a set of kinds: a specialised one when every grid has the
 // same kind, else the general k_batch.  `walk16` picks the prefetch depth of

@@ -637,13 +637,19 @@ struct Walker {
                                       h[s][6], h[s][7], h[s][8]);
         }
         // Halo drho: lanes 0..8 hold the left halo's nine values, 16..24 the
-        // right halo's; gather them in direction order and sum as above.
+        // right halo's.  The sums of delta_rho are formed across lanes in the
+        // same order: lanes 1, 3, 5, 7 add their right neighbour (h1+h2,
+        // h3+h4, h5+h6, h7+h8), lanes 1 and 5 then add the pair two lanes on
+        // ((h1+h2)+(h3+h4), (h5+h6)+(h7+h8)), and lane 0 (16) combines them
+        // with h0 as delta_rho does.
         {
+            const float v = elem_to_f<S>(g);
+            const float t = __fadd_rn(v, __shfl_down_sync(FULL, v, 1));
+            const float u = __fadd_rn(t, __shfl_down_sync(FULL, t, 2));
             const int base = lane & 16;
-            float hh[9];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) hh[i] = elem_to_f<S>(__shfl_sync(FULL, g, base + i));
-            float dh = delta_rho(hh[0], hh[1], hh[2], hh[3], hh[4], hh[5], hh[6], hh[7], hh[8]);
+            const float sa = __shfl_sync(FULL, u, base + 1);
+            const float sd = __shfl_sync(FULL, u, base + 5);
+            const float dh = __fmaf_rn(VSS_W0, v, __fmaf_rn(VSS_W1, sa, __fmul_rn(VSS_W5, sd)));
             dl = __shfl_sync(FULL, dh, 0);
             dr = __shfl_sync(FULL, dh, 16);
         }

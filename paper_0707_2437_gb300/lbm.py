@@ -89,6 +89,8 @@ def load() -> ctypes.CDLL:
                                       ctypes.POINTER(i)], i),
             "lbm_batch_set_timeout_us": ([vp, ll], i),
             "lbm_batch_set_launch": ([vp, i], i),
+            "lbm_batch_set_schedule": ([vp, i], i),
+            "lbm_batch_get_schedule": ([vp, ctypes.POINTER(i)], i),
             "lbm_batch_get_launch": ([vp, ctypes.POINTER(i), ctypes.POINTER(i),
                                       ctypes.POINTER(i)], i),
             "lbm_sums_noalloc": ([vp, i, i, sz, i, d, vp, dp], i),
@@ -338,6 +340,8 @@ class Grid:
 WALK16 = {"auto": 0, "v8": 1, "v4": 2, "v4pf2": 3}
 WALK16_NAMES = {v: k for k, v in WALK16.items()}
 LAUNCH = {"auto": 0, "graph": 1, "direct": 2}
+SCHEDULE = {"lockstep": 0, "flow": 1}
+SCHEDULE_NAMES = {v: k for k, v in SCHEDULE.items()}
 LAUNCH_NAMES = {v: k for k, v in LAUNCH.items()}
 
 
@@ -400,6 +404,17 @@ class Batch:
 
     def set_timeout_us(self, us: int):
         _check(self.lib.lbm_batch_set_timeout_us(self.b, int(us)), "lbm_batch_set_timeout_us")
+
+    def set_schedule(self, schedule: str):
+        """'lockstep' (the default: a grid-wide barrier between time steps) or
+        'flow' (each grid advances on its own, per-tile progress)."""
+        _check(self.lib.lbm_batch_set_schedule(self.b, SCHEDULE[schedule]),
+               "lbm_batch_set_schedule")
+
+    def get_schedule(self) -> str:
+        v = ctypes.c_int()
+        _check(self.lib.lbm_batch_get_schedule(self.b, ctypes.byref(v)), "lbm_batch_get_schedule")
+        return SCHEDULE_NAMES[v.value]
 
     def set_launch(self, mode: str):
         """'auto' (graph replay, direct launches if capture fails), 'graph'

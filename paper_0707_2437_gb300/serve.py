@@ -15,6 +15,13 @@ memory frees up, and their work overlaps on the device.
 ``serve_fifo`` is the plain baseline: one grid at a time, in arrival order,
 with the single-grid FP32 kernel.
 
+Two schedules (``Server(schedule=...)``).  ``lockstep``: each launch advances
+every resident grid by up to `quantum` steps together, a barrier across the
+batch between steps, so a small grid waits as many batch-wide steps as a large
+one.  ``flow``: each launch shares a budget of lattice updates equally between
+the grids (a small grid gets many steps, a large one few) and runs them with
+the batch's flow schedule, where each grid advances on its own.
+
 All stepping runs in the CUDA library; this module only schedules.
 """
 from __future__ import annotations
@@ -90,14 +97,35 @@ class Server:
 
     def __init__(self, quantum: int = 256, reserve_bytes: int = 4 << 30,
                  max_slots: int = 512, keep_fields: bool = False, stream=None,
-                 overlap: bool = True):
+                 overlap: bool = True, schedule: str = "lockstep",
+                 flow_updates: float = 2e9, flow_max_steps: int = 4096):
         self.quantum = quantum
         self.reserve = reserve_bytes
         self.max_slots = max_slots
         self.keep_fields = keep_fields
         self.stream = stream
         self.overlap = overlap
+        if schedule not in ("lockstep", "flow"):
+            raise ValueError(f"unknown schedule {schedule!r}")
+        self.schedule = schedule
+        self.flow_updates = flow_updates
+        self.flow_max_steps = flow_max_steps
         lbm.load()
+
+    def _limits(self, active):
+        """Steps each resident grid takes in the next launch.  Lockstep:
+        every grid up to `quantum` steps (all advance together).  Flow: the
+        launch's budget of `flow_updates` lattice updates is shared equally
+        between the grids, so a grid takes steps in inverse proportion to its
+        size (at least one, at most `flow_max_steps`, at most what it has
+        left); the flow schedule runs them without a barrier across grids."""
+        if self.schedule == "lockstep":
+            q = min(self.quantum, max(a[2] for a in active))
+            return q, [min(q, a[2]) for a in active]
+        share = self.flow_updates / len(active)
+        lim = [int(min(a[2], self.flow_max_steps,
+                       max(1, share // (a[0].nx * a[0].ny)))) for a in active]
+        return max(lim), lim
 
     def _need(self, req) -> int:
         # distributions + the staging of three FP64 fields during lbm_init
@@ -160,10 +188,11 @@ class Server:
                     if batch is not None:
                         batch.close()
                     batch = lbm.Batch([a[1] for a in active])
+                    if self.schedule == "flow":
+                        batch.set_schedule("flow")
                     members = [id(a[1]) for a in active]
                 stats.max_active = max(stats.max_active, len(active))
-                q = min(self.quantum, max(a[2] for a in active))
-                limits = [min(q, a[2]) for a in active]
+                q, limits = self._limits(active)
                 batch.step(q, limits)
                 ph["batch"] += time.perf_counter() - tb
             if self.overlap:

@@ -110,6 +110,8 @@ def test_every_handle_call_rejects_null_before_device_work():
         lambda: lib.lbm_batch_get_walk16(None, ctypes.byref(i)),
         lambda: lib.lbm_batch_set_timeout_us(None, 1000),
         lambda: lib.lbm_batch_set_launch(None, 0),
+        lambda: lib.lbm_batch_set_schedule(None, 0),
+        lambda: lib.lbm_batch_get_schedule(None, ctypes.byref(i)),
         lambda: lib.lbm_batch_get_launch(None, ctypes.byref(i), ctypes.byref(i),
                                          ctypes.byref(i)),
     ]

@@ -278,3 +278,109 @@ def test_batch_launch_mode_argument_checks(lbm):
         b.set_launch("eager")
     b.close()
     g.close()
+
+
+def _solo_states(lbm, specs, limits, fields_of, rounding=None):
+    out = []
+    for (nx, ny, tau, c2, st), lim in zip(specs, limits):
+        with lbm.Grid(nx, ny, tau, c2, st) as g:
+            if rounding and st != "f32":
+                g.set_rounding(rounding)
+            g.init(*fields_of(nx, ny))
+            g.step(lim)
+            out.append(g.get_state()[0])
+    return out
+
+
+@pytest.mark.parametrize("rows", [16, 5, 1])
+def test_flow_schedule_equals_solo_runs(lbm, rows):
+    """The flow schedule (no barrier across the batch; each tile waits only
+    for the tiles it reads from) gives every grid bitwise the state it reaches
+    alone: mixed storages and walks, per-grid step limits, odd widths (1-site
+    lanes), single-row tail segments (rows 5 with ny = 41, and rows 1) and
+    grids down to 1 x 1, over two calls."""
+    specs = [(2048, 512, 0.8, 0.2, "f32"), (1024, 256, 0.6, 0.1, "f16d"),
+             (37, 41, 0.7, 0.3, "f32"), (256, 40, 1.1, 0.3, "bf16d"),
+             (96, 130, 0.55, 0.05, "f16d"), (8, 8, 0.9, 0.4, "f32"), (1, 1, 0.9, 0.2, "f32"),
+             (3, 5, 0.7, 0.15, "f16d"), (520, 16, 0.7, 0.25, "f32")]
+    limits = [30, 80, 200, 45, 120, 200, 7, 150, 1]
+
+    def fields(nx, ny):
+        return workloads.fourier_modes(nx, ny, amp=1e-3, seed=nx * 7 + ny)
+
+    solo = _solo_states(lbm, specs, limits, fields)
+    grids = []
+    for nx, ny, tau, c2, st in specs:
+        g = lbm.Grid(nx, ny, tau, c2, st)
+        g.init(*fields(nx, ny))
+        grids.append(g)
+    b = lbm.Batch(grids)
+    b.set_config(rows, 0)
+    b.set_schedule("flow")
+    assert b.get_schedule() == "flow"
+    b.step(120, limits)
+    b.step(80, [max(0, x - 120) for x in limits])
+    assert b.sync() == 0
+    for g, s, lim in zip(grids, solo, limits):
+        assert g.t == lim
+        assert np.array_equal(g.get_state()[0], s)
+    b.close()
+    for g in grids:
+        g.close()
+
+
+def test_flow_schedule_stochastic_rounding_and_graph(lbm):
+    """Stochastic rounding seeds by each grid's own step counter, so the flow
+    schedule reproduces solo runs bitwise with it too; repeated calls with
+    the same step count replay the captured graph."""
+    specs = [(512, 128, 0.7, 0.2, "f16d"), (264, 40, 0.9, 0.1, "bf16d"), (40, 24, 0.6, 0.3, "f32")]
+    limits = [64, 40, 64]
+
+    def fields(nx, ny):
+        return workloads.fourier_modes(nx, ny, amp=1e-2, seed=nx + 3)
+
+    solo = _solo_states(lbm, specs, limits, fields, rounding="stochastic")
+    grids = []
+    for nx, ny, tau, c2, st in specs:
+        g = lbm.Grid(nx, ny, tau, c2, st)
+        if st != "f32":
+            g.set_rounding("stochastic")
+        g.init(*fields(nx, ny))
+        grids.append(g)
+    b = lbm.Batch(grids)
+    b.set_schedule("flow")
+    for _ in range(4):
+        b.step(16, [16, 10, 16])
+    assert b.get_launch()["last"] == "graph"
+    assert b.sync() == 0
+    for g, s, lim in zip(grids, solo, limits):
+        assert g.t == lim
+        assert np.array_equal(g.get_state()[0], s)
+    b.close()
+    for g in grids:
+        g.close()
+
+
+def test_flow_schedule_timeout_reports_status(lbm):
+    """A 1-microsecond wait limit runs out in the flow schedule too (a tile
+    waiting for its neighbours): the kernel ends, the host reads
+    LBM_ETIMEOUT, and a later call with the normal limit succeeds."""
+    grids = [lbm.Grid(1024, 1024, 0.8, 0.2) for _ in range(2)]
+    for g in grids:
+        g.init(*workloads.sine_wave(1024, 1024))
+    b = lbm.Batch(grids)
+    b.set_schedule("flow")
+    b.set_timeout_us(1)
+    b.step(20)
+    with pytest.raises(lbm.LbmError) as ei:
+        b.sync()
+    assert ei.value.status == lbm.LBM_ETIMEOUT
+    b.set_timeout_us(1_000_000)
+    for g in grids:
+        g.init(*workloads.sine_wave(1024, 1024))
+    b.step(5)
+    assert b.sync() == 0
+    assert all(g.t == 5 for g in grids)
+    b.close()
+    for g in grids:
+        g.close()

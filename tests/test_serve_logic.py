@@ -17,6 +17,7 @@ class _FakeDevice:
         self.created = []
         self.in_flight = None    # the batch whose quantum is queued, until sync
         self.streams = 0
+        self.steps = []          # (schedule, [(sites, steps)]) of every step call
 
     # the subset of the lbm module the server uses
     def load(self):
@@ -73,12 +74,18 @@ def _fake_lbm(dev):
             self.stream = self.grids[0].stream
             assert all(g.stream is self.stream for g in self.grids)
 
+        def set_schedule(self, schedule):
+            assert schedule in ("lockstep", "flow")
+            self.schedule = schedule
+
         def step(self, n, limits=None):
             assert dev.in_flight is None
             limits = limits or [n] * len(self.grids)
             for g, lim in zip(self.grids, limits):
                 assert 0 <= lim <= n
                 g.t += lim
+            dev.steps.append((getattr(self, "schedule", "lockstep"),
+                              [(g.nx * g.ny, lim) for g, lim in zip(self.grids, limits)]))
             dev.in_flight = self
 
         def sync(self):
@@ -184,3 +191,35 @@ def test_admission_overlaps_the_running_quantum(monkeypatch, overlap):
         assert all(g.stream is not None for g in dev.created)
     for q, g in zip(reqs, dev.created):
         assert g.steps_at_close == q.steps
+
+
+def test_flow_schedule_shares_updates_equally(monkeypatch):
+    """With the flow schedule every launch gives each resident grid about the
+    same number of lattice updates (steps in inverse proportion to its size,
+    at least one, at most its remaining steps and the per-launch cap), and
+    every request still runs exactly its steps."""
+    dev = _FakeDevice(total=1 << 40)
+    monkeypatch.setattr(serve, "lbm", _fake_lbm(dev))
+    reqs = _requests(n=16)
+    budget = 4e6
+    srv = serve.Server(reserve_bytes=0, schedule="flow", flow_updates=budget, flow_max_steps=900)
+    stats = srv.run(reqs, realtime=False)
+    assert len(stats.results) == len(reqs) and dev.live == 0
+    for q, g in zip(reqs, dev.created):
+        assert g.steps_at_close == q.steps
+    assert dev.steps and all(sch == "flow" for sch, _ in dev.steps)
+    for _, calls in dev.steps:
+        share = budget / len(calls)
+        for sites, lim in calls:
+            assert 1 <= lim <= 900
+            # at most the share, unless a single step already exceeds it
+            assert lim * sites <= max(share, sites)
+    # small grids took more steps per launch than large ones in a shared launch
+    _, first = dev.steps[0]
+    by_size = sorted(first)
+    assert by_size[0][1] >= by_size[-1][1]
+
+
+def test_unknown_schedule_is_refused():
+    with pytest.raises(ValueError):
+        serve.Server(schedule="eager")
