@@ -158,9 +158,9 @@ def serve_comparison(args, stream=None):
                                steps_hi=args.serve_steps_hi)
     overlap = not args.serve_no_overlap
 
-    def server(schedule="lockstep"):
+    def server(schedule="lockstep", policy="fair"):
         return serve.Server(quantum=args.serve_quantum, overlap=overlap, schedule=schedule,
-                            flow_updates=args.serve_flow_updates)
+                            flow_updates=args.serve_flow_updates, policy=policy)
 
     warm = serve.scaled_trace(8, 1000.0, seed=99, hi=256, steps_hi=2000)
     server().run(warm, realtime=False)
@@ -183,6 +183,11 @@ def serve_comparison(args, stream=None):
     trace07 = serve.scaled_trace(args.serve_count, rate07, steps_hi=args.serve_steps_hi)
     srv07 = server().run(trace07, realtime=True).summary()
     out["at_0.7_capacity"] = {"rate_hz": rate07, "continuous_batching": srv07}
+    if not args.serve_no_srpt:
+        # The same two traces, the grids with the least remaining work first.
+        out["continuous_batching_srpt"] = server(policy="srpt").run(trace, realtime=True).summary()
+        out["at_0.7_capacity"]["continuous_batching_srpt"] = server(policy="srpt").run(
+            trace07, realtime=True).summary()
     if not args.serve_no_flow:
         # The same two traces with the flow schedule (each grid advances on
         # its own; launches share a budget of lattice updates equally).
@@ -809,6 +814,7 @@ def run_serve_workload(args):
                    "quantum_steps": args.serve_quantum},
         "served": srv, "fifo_f32": fifo, "at_0.7_capacity": cmp_["at_0.7_capacity"],
         "served_flow": cmp_.get("continuous_batching_flow"),
+        "served_srpt": cmp_.get("continuous_batching_srpt"),
         "clocks": clk,
     }
     if rank == 0:
@@ -845,6 +851,8 @@ def main():
     ap.add_argument("--serve-quantum", type=int, default=256)
     ap.add_argument("--schedule", default="lockstep", choices=["lockstep", "flow"],
                     help="batch schedule on the batch paths (flow: no barrier across grids)")
+    ap.add_argument("--serve-no-srpt", action="store_true",
+                    help="skip the least-remaining-work-first server in the serving comparison")
     ap.add_argument("--serve-no-flow", action="store_true",
                     help="skip the flow-schedule server in the serving comparison")
     ap.add_argument("--serve-flow-updates", type=float, default=2e9,

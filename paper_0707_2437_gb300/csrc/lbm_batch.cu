@@ -36,6 +36,7 @@ struct lbm_batch {
     struct Group {
         int begin = 0, count = 0;
         BatchKernel kernel = nullptr;
+        FlowKernel fkernel = nullptr;  // flow schedule
         int max_blocks_per_sm = 1;
     };
     std::vector<Group> groups;
@@ -157,22 +158,29 @@ static int build_worklist(lbm_batch *b) {
         d.pad = 0;
         d.c = g->coef;
         int w = 32 * v;
+        // Flow schedule: a grid's step takes as long as its slowest tile's
+        // walk, so grids below kFlowShortSites sites use tiles of a quarter
+        // of the height (more tiles, each walk a quarter as long).
+        const int rows = (b->schedule == LBM_SCHEDULE_FLOW &&
+                          (long long)g->nx * g->ny < kFlowShortSites)
+                             ? std::max(1, b->rows / 4)
+                             : b->rows;
         d.tile0 = (int)tiles.size();
         d.nstrips = (g->nx + w - 1) / w;
-        d.nsegs = (g->ny + b->rows - 1) / b->rows;
+        d.nsegs = (g->ny + rows - 1) / rows;
         d.ntile = d.nstrips * d.nsegs;
         // A step reads two rows and two columns beyond its tile: the next
         // segment or strip over suffices unless one of them is a single row
         // or column wide (the last one of a grid can be).
-        const int last_rows = g->ny - (d.nsegs - 1) * b->rows;
+        const int last_rows = g->ny - (d.nsegs - 1) * rows;
         const int last_cols = g->nx - (d.nstrips - 1) * w;
-        d.dseg = (b->rows >= 2 && last_rows >= 2) ? 1 : 2;
+        d.dseg = (rows >= 2 && last_rows >= 2) ? 1 : 2;
         d.dstrip = last_cols >= 2 ? 1 : 2;
         // Neighbouring segments walk in opposite directions, so the rows they
         // share are read by both at about the same time (from L2 the second time).
-        for (int y0 = 0, seg = 0; y0 < g->ny; y0 += b->rows, ++seg)
+        for (int y0 = 0, seg = 0; y0 < g->ny; y0 += rows, ++seg)
             for (int x0 = 0; x0 < g->nx; x0 += w)
-                tiles.push_back(Tile{(int)k, x0, y0, std::min(g->ny, y0 + b->rows),
+                tiles.push_back(Tile{(int)k, x0, y0, std::min(g->ny, y0 + rows),
                                      (seg & 1) ? -1 : 1});
     }
     if (b->schedule == LBM_SCHEDULE_FLOW) {
@@ -182,8 +190,11 @@ static int build_worklist(lbm_batch *b) {
         gr.begin = 0;
         gr.count = (int)tiles.size();
         gr.kernel = nullptr;
+        std::vector<int> kinds;
+        for (const GridDesc &d : gd) kinds.push_back(d.kind);
+        gr.fkernel = flow_kernel_for(kinds, b->walk16);
         BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gr.max_blocks_per_sm,
-                                                          (const void *)k_flow,
+                                                          (const void *)gr.fkernel,
                                                           32 * kBatchWarps, 0));
         if (gr.max_blocks_per_sm < 1) return bfail(LBM_ECUDA, "flow kernel cannot be resident");
         b->groups.push_back(gr);
@@ -363,7 +374,7 @@ static cudaError_t enqueue(lbm_batch *b, long long n, cudaStream_t st) {
         if (e == cudaSuccess) e = cudaMemsetAsync(b->d_prog, 0, sizeof(int) * b->ntiles, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned) * kBarWords, st);
         if (e != cudaSuccess) return e;
-        k_flow<<<grid_blocks(b, b->groups[0]), 32 * kBatchWarps, 0, st>>>(
+        b->groups[0].fkernel<<<grid_blocks(b, b->groups[0]), 32 * kBatchWarps, 0, st>>>(
             grids, ng, b->d_tiles, lim, par, t0, b->d_ctl, b->d_prog, bar, b->d_nwork, status,
             to);
         return cudaGetLastError();
@@ -655,7 +666,8 @@ extern "C" int lbm_batch_get_config(lbm_batch_t b, int *rows, int *blocks_per_sm
     if (specialised) {
         *specialised = 1;
         for (const auto &gr : b->groups)
-            if (gr.kernel == (BatchKernel)k_batch || gr.kernel == nullptr) *specialised = 0;
+            if (gr.kernel == (BatchKernel)k_batch || gr.fkernel == (FlowKernel)k_flow)
+                *specialised = 0;
     }
     return LBM_OK;
 }

@@ -252,6 +252,7 @@ __global__ void __launch_bounds__(32 * kBatchWarps, 3)
 // round-robin counter and the number of grids whose last ticket is taken.
 // Every wait is bounded by the same wall-clock limit as the barrier.
 constexpr int kFlowWindow = 2;
+constexpr long long kFlowShortSites = 1LL << 21;  // below this, flow tiles are a quarter as tall
 constexpr int kFlowCtlWords = 32;  // unsigned long long words per grid: [0] taken, [16] done
 constexpr int kFlowRR = 0;         // words of `glob`
 constexpr int kFlowExh = 32;
@@ -299,11 +300,16 @@ __device__ __forceinline__ bool flow_wait(const GridDesc &g, const int *prog, in
     return true;
 }
 
-__global__ void __launch_bounds__(32 * kBatchWarps, 3)
-    k_flow(const GridDesc *__restrict__ grids, int ngrids, const Tile *__restrict__ tiles,
-           const long long *__restrict__ limit, const int *__restrict__ parity0,
-           const uint32_t *__restrict__ t0, unsigned long long *ctl, int *prog, unsigned *glob,
-           const int *__restrict__ nwork_p, int *status, unsigned long long timeout_ns) {
+// The flow loop of one warp; run_tile(g, par, tile, step) runs a tile.
+template <class RunTile>
+__device__ __forceinline__ void flow_loop(const GridDesc *__restrict__ grids, int ngrids,
+                                          const Tile *__restrict__ tiles,
+                                          const long long *__restrict__ limit,
+                                          const int *__restrict__ parity0,
+                                          const uint32_t *__restrict__ t0,
+                                          unsigned long long *ctl, int *prog, unsigned *glob,
+                                          const int *__restrict__ nwork_p, int *status,
+                                          unsigned long long timeout_ns, RunTile run_tile) {
     const int lane = threadIdx.x & 31;
     const int nwork = *nwork_p;  // grids with steps to take in this launch
     unsigned long long idle_since = 0;
@@ -364,8 +370,7 @@ __global__ void __launch_bounds__(32 * kBatchWarps, 3)
         const int seg = ti / g.nstrips, strip = ti % g.nstrips;
         if (!flow_wait(g, prog, seg, strip, k, status, timeout_ns)) return;
         const Tile t = tiles[g.tile0 + ti];
-        const int par = (parity0[gsel] + k) & 1;
-        any_tile(g, par, t, t0[gsel] + (uint32_t)k);
+        run_tile(g, (parity0[gsel] + k) & 1, t, t0[gsel] + (uint32_t)k);
         // Publish: the tile's stores before its completed-step count.
         __threadfence();
         __syncwarp();
@@ -374,6 +379,82 @@ __global__ void __launch_bounds__(32 * kBatchWarps, 3)
             atomicAdd(ctl + (size_t)gsel * kFlowCtlWords + 16, 1ULL);
         }
     }
+}
+
+// Flow kernel for any mix of walks (out of line, as in k_batch).
+__global__ void __launch_bounds__(32 * kBatchWarps, 3)
+    k_flow(const GridDesc *__restrict__ grids, int ngrids, const Tile *__restrict__ tiles,
+           const long long *__restrict__ limit, const int *__restrict__ parity0,
+           const uint32_t *__restrict__ t0, unsigned long long *ctl, int *prog, unsigned *glob,
+           const int *__restrict__ nwork_p, int *status, unsigned long long timeout_ns) {
+    flow_loop(grids, ngrids, tiles, limit, parity0, t0, ctl, prog, glob, nwork_p, status,
+              timeout_ns, [](const GridDesc &g, int par, const Tile &t, uint32_t step) {
+                  any_tile(g, par, t, step);
+              });
+}
+
+// Flow kernel for a batch of one walk, inlined (the register budget and the
+// row buffers of k_batch_one).
+template <int S, int V, int PD, int RND, int VA = 0>
+__global__ void __launch_bounds__(32 * kBatchWarps, 3)
+    k_flow_one(const GridDesc *__restrict__ grids, int ngrids, const Tile *__restrict__ tiles,
+               const long long *__restrict__ limit, const int *__restrict__ parity0,
+               const uint32_t *__restrict__ t0, unsigned long long *ctl, int *prog,
+               unsigned *glob, const int *__restrict__ nwork_p, int *status,
+               unsigned long long timeout_ns) {
+    __shared__ uint4 rowbuf[(S != ST_F32 && V == 8) ? kBatchWarps : 1][2 * 9 * 32];
+    (void)rowbuf;
+    flow_loop(grids, ngrids, tiles, limit, parity0, t0, ctl, prog, glob, nwork_p, status,
+              timeout_ns, [&](const GridDesc &g, int par, const Tile &t, uint32_t step) {
+                  Walker<S, V, LD_CG, RND, VA> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P,
+                                                 t.x0);
+                  if constexpr (VA) w.a15f = g.a15f;
+                  if constexpr (RND) w.set_step(step);
+                  const Coef c = g.c;
+                  if constexpr (S != ST_F32 && V == 8)
+                      w.run_async(t.y0, t.y1, t.dir, c, &rowbuf[threadIdx.x >> 5][0]);
+                  else if constexpr (PD == 2)
+                      w.run_prefetch2(t.y0, t.y1, t.dir, c);
+                  else if constexpr (PD == 1)
+                      w.run_prefetch(t.y0, t.y1, t.dir, c);
+                  else
+                      w.run(t.y0, t.y1, t.dir, c);
+              });
+}
+
+using FlowKernel = void (*)(const GridDesc *, int, const Tile *, const long long *, const int *,
+                            const uint32_t *, unsigned long long *, int *, unsigned *,
+                            const int *, int *, unsigned long long);
+
+// The flow kernel for a batch's kinds: specialised when all grids share one
+// walk, else the general k_flow.
+FlowKernel flow_kernel_for(const std::vector<int> &kinds, int walk16) {
+    bool same = true;
+    for (int k : kinds) same = same && k == kinds[0];
+    if (!kinds.empty() && same) {
+        const bool two = walk16 == LBM_WALK16_V4_PF2;
+        switch (kinds[0]) {
+            case kind_code(ST_F32, 4, 0):
+                return k_flow_one<ST_F32, 4, 0, 0>;
+            case kind_code(ST_F16, 8, 0):
+                return k_flow_one<ST_F16, 8, 0, 0>;
+            case kind_code(ST_BF16, 8, 0):
+                return k_flow_one<ST_BF16, 8, 0, 0>;
+            case kind_code(ST_F16, 8, 1):
+                return k_flow_one<ST_F16, 8, 0, 1>;
+            case kind_code(ST_BF16, 8, 1):
+                return k_flow_one<ST_BF16, 8, 0, 1>;
+            case kind_code(ST_F16, 4, 0):
+                return two ? k_flow_one<ST_F16, 4, 2, 0> : k_flow_one<ST_F16, 4, 1, 0>;
+            case kind_code(ST_BF16, 4, 0):
+                return two ? k_flow_one<ST_BF16, 4, 2, 0> : k_flow_one<ST_BF16, 4, 1, 0>;
+            case kind_code(ST_F32, 4, 0, 1):
+                return k_flow_one<ST_F32, 4, 0, 0, 1>;
+            default:
+                break;
+        }
+    }
+    return k_flow;
 }
 
 // Specialised persistent kernel for a batch whose grids all use one walk

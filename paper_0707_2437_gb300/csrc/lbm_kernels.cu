@@ -71,7 +71,7 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned 
 // Fused step: one warp per (strip, row segment) tile.
 
 template <int S, int V, bool PF, int RND = 0, int VA = 0>
-__global__ void __launch_bounds__(256, (VA && S == ST_F32 && V == 4) ? 1 : 2)
+__global__ void __launch_bounds__(256, 2)
     k_step(const void *__restrict__ fin, void *__restrict__ fout, int nx, int ny, size_t P,
            int nstrips, long long ntiles, int rows, Coef c, const uint32_t *tdev,
            uint32_t toff, const float *__restrict__ a15f) {

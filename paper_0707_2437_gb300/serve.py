@@ -22,6 +22,11 @@ one.  ``flow``: each launch shares a budget of lattice updates equally between
 the grids (a small grid gets many steps, a large one few) and runs them with
 the batch's flow schedule, where each grid advances on its own.
 
+Two policies (``Server(policy=...)``) pick the grids that step in a launch:
+``fair`` steps every resident grid; ``srpt`` steps the grids with the least
+remaining work first (shortest remaining processing time), adding grids until
+their sites keep the GPU's memory bandwidth busy, while the others wait.
+
 All stepping runs in the CUDA library; this module only schedules.
 """
 from __future__ import annotations
@@ -98,7 +103,8 @@ class Server:
     def __init__(self, quantum: int = 256, reserve_bytes: int = 4 << 30,
                  max_slots: int = 512, keep_fields: bool = False, stream=None,
                  overlap: bool = True, schedule: str = "lockstep",
-                 flow_updates: float = 2e9, flow_max_steps: int = 4096):
+                 flow_updates: float = 2e9, flow_max_steps: int = 1024,
+                 policy: str = "fair", srpt_sites: float = 4e6):
         self.quantum = quantum
         self.reserve = reserve_bytes
         self.max_slots = max_slots
@@ -110,7 +116,30 @@ class Server:
         self.schedule = schedule
         self.flow_updates = flow_updates
         self.flow_max_steps = flow_max_steps
+        if policy not in ("fair", "srpt"):
+            raise ValueError(f"unknown policy {policy!r}")
+        self.policy = policy
+        self.srpt_sites = srpt_sites
         lbm.load()
+
+    def _selected(self, active):
+        """Which resident grids step in the next launch.  'fair': all of
+        them.  'srpt': the grids with the least remaining work (steps left
+        times sites), smallest first, until their sites reach `srpt_sites`
+        (enough for a step to be bound by memory bandwidth rather than by the
+        walk of one tile); the rest wait with a step limit of 0."""
+        if self.policy == "fair":
+            return [True] * len(active)
+        order = sorted(range(len(active)), key=lambda j: active[j][2] * active[j][0].nx
+                       * active[j][0].ny)
+        sel = [False] * len(active)
+        sites = 0
+        for j in order:
+            sel[j] = True
+            sites += active[j][0].nx * active[j][0].ny
+            if sites >= self.srpt_sites:
+                break
+        return sel
 
     def _limits(self, active):
         """Steps each resident grid takes in the next launch.  Lockstep:
@@ -119,12 +148,14 @@ class Server:
         between the grids, so a grid takes steps in inverse proportion to its
         size (at least one, at most `flow_max_steps`, at most what it has
         left); the flow schedule runs them without a barrier across grids."""
+        sel = self._selected(active)
+        run = [a for a, s_ in zip(active, sel) if s_]
         if self.schedule == "lockstep":
-            q = min(self.quantum, max(a[2] for a in active))
-            return q, [min(q, a[2]) for a in active]
-        share = self.flow_updates / len(active)
-        lim = [int(min(a[2], self.flow_max_steps,
-                       max(1, share // (a[0].nx * a[0].ny)))) for a in active]
+            q = min(self.quantum, max(a[2] for a in run))
+            return q, [min(q, a[2]) if s_ else 0 for a, s_ in zip(active, sel)]
+        share = self.flow_updates / len(run)
+        lim = [int(min(a[2], self.flow_max_steps, max(1, share // (a[0].nx * a[0].ny))))
+               if s_ else 0 for a, s_ in zip(active, sel)]
         return max(lim), lim
 
     def _need(self, req) -> int:

@@ -223,3 +223,31 @@ def test_flow_schedule_shares_updates_equally(monkeypatch):
 def test_unknown_schedule_is_refused():
     with pytest.raises(ValueError):
         serve.Server(schedule="eager")
+
+
+def test_srpt_policy_steps_the_least_remaining_work_first(monkeypatch):
+    """The srpt policy steps, in each launch, the grids with the least
+    remaining work until their sites reach the threshold (at least one grid);
+    the others take no steps.  Every request still completes its steps."""
+    dev = _FakeDevice(total=1 << 40)
+    monkeypatch.setattr(serve, "lbm", _fake_lbm(dev))
+    reqs = _requests(n=16)
+    thresh = 3 * 128 * 128
+    srv = serve.Server(quantum=128, reserve_bytes=0, policy="srpt", srpt_sites=thresh)
+    stats = srv.run(reqs, realtime=False)
+    assert len(stats.results) == len(reqs) and dev.live == 0
+    for q, g in zip(reqs, dev.created):
+        assert g.steps_at_close == q.steps
+    paused_seen = False
+    for _, calls in dev.steps:
+        stepping = [s for s, lim in calls if lim > 0]
+        assert stepping
+        # the stepping grids, minus the last one added, stay below the threshold
+        assert sum(stepping) - max(stepping) < thresh or len(stepping) == 1
+        paused_seen = paused_seen or any(lim == 0 for _, lim in calls)
+    assert paused_seen
+
+
+def test_unknown_policy_is_refused():
+    with pytest.raises(ValueError):
+        serve.Server(policy="lifo")
