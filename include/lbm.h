@@ -180,7 +180,9 @@ int lbm_set_drive(lbm_t h, int on, double amplitude, double period);
  * values are checked); the force at site x uses alpha(x) = 1/3 - c2(x) in
  * Eq. 5.  NULL returns to the grid's uniform c2.  The field costs one more
  * 4-byte read per site and step.  While a field is set the walks use at most
- * 4 sites per lane, no bulk-copy pipeline and nearest rounding; the grid can
+ * 4 sites per lane, no bulk-copy pipeline and nearest rounding (an FP32 grid
+ * configured for 4 sites per lane steps with 2 sites per lane and one row of
+ * loads prefetched: as fast, and within the register budget); the grid can
  * join a batch and long lbm_step calls still run one persistent launch. */
 int lbm_set_c2_field(lbm_t h, const double *c2, int on_device);
 

@@ -144,6 +144,23 @@ static int upload_worklist(lbm_batch *b, const std::vector<GridDesc> &gd,
 static int build_worklist(lbm_batch *b) {
     std::vector<GridDesc> gd(b->grids.size());
     std::vector<Tile> tiles;
+    // Flow schedule: the kernel for the grids' kinds and the warps it keeps
+    // resident, which set each grid's tile height below.
+    FlowKernel fk = nullptr;
+    int flow_bps = 1;
+    long long flow_warps = 0;
+    if (b->schedule == LBM_SCHEDULE_FLOW) {
+        std::vector<int> kinds;
+        for (const lbm_grid *g : b->grids)
+            kinds.push_back(kind_code(g->storage, batch_vec(b, g), g->rounding ? 1 : 0,
+                                      g->a15f ? 1 : 0));
+        fk = flow_kernel_for(kinds, b->walk16);
+        BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&flow_bps, (const void *)fk,
+                                                          32 * kBatchWarps, 0));
+        if (flow_bps < 1) return bfail(LBM_ECUDA, "flow kernel cannot be resident");
+        const int per = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, flow_bps) : flow_bps;
+        flow_warps = (long long)per * b->sms * kBatchWarps;
+    }
     for (size_t k = 0; k < b->grids.size(); ++k) {
         lbm_grid *g = b->grids[k];
         GridDesc &d = gd[k];
@@ -158,13 +175,16 @@ static int build_worklist(lbm_batch *b) {
         d.pad = 0;
         d.c = g->coef;
         int w = 32 * v;
-        // Flow schedule: a grid's step takes as long as its slowest tile's
-        // walk, so grids below kFlowShortSites sites use tiles of a quarter
-        // of the height (more tiles, each walk a quarter as long).
-        const int rows = (b->schedule == LBM_SCHEDULE_FLOW &&
-                          (long long)g->nx * g->ny < kFlowShortSites)
-                             ? std::max(1, b->rows / 4)
-                             : b->rows;
+        // Flow schedule: a grid's step takes at least one tile walk, so a grid
+        // with fewer tiles than its share of the resident warps (the warps
+        // split evenly between the grids) uses tiles a quarter as tall: four
+        // times the tiles, each walk a quarter as long.
+        int rows = b->rows;
+        if (b->schedule == LBM_SCHEDULE_FLOW) {
+            const long long tiles_tall =
+                (long long)((g->nx + w - 1) / w) * ((g->ny + b->rows - 1) / b->rows);
+            if (tiles_tall * (long long)b->grids.size() < flow_warps) rows = std::max(1, b->rows / 4);
+        }
         d.tile0 = (int)tiles.size();
         d.nstrips = (g->nx + w - 1) / w;
         d.nsegs = (g->ny + rows - 1) / rows;
@@ -190,13 +210,8 @@ static int build_worklist(lbm_batch *b) {
         gr.begin = 0;
         gr.count = (int)tiles.size();
         gr.kernel = nullptr;
-        std::vector<int> kinds;
-        for (const GridDesc &d : gd) kinds.push_back(d.kind);
-        gr.fkernel = flow_kernel_for(kinds, b->walk16);
-        BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gr.max_blocks_per_sm,
-                                                          (const void *)gr.fkernel,
-                                                          32 * kBatchWarps, 0));
-        if (gr.max_blocks_per_sm < 1) return bfail(LBM_ECUDA, "flow kernel cannot be resident");
+        gr.fkernel = fk;
+        gr.max_blocks_per_sm = flow_bps;
         b->groups.push_back(gr);
         if (tiles.size() > b->prog_cap) {
             cudaFree(b->d_prog);

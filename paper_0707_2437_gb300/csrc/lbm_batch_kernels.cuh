@@ -252,7 +252,6 @@ __global__ void __launch_bounds__(32 * kBatchWarps, 3)
 // round-robin counter and the number of grids whose last ticket is taken.
 // Every wait is bounded by the same wall-clock limit as the barrier.
 constexpr int kFlowWindow = 2;
-constexpr long long kFlowShortSites = 1LL << 21;  // below this, flow tiles are a quarter as tall
 constexpr int kFlowCtlWords = 32;  // unsigned long long words per grid: [0] taken, [16] done
 constexpr int kFlowRR = 0;         // words of `glob`
 constexpr int kFlowExh = 32;
@@ -422,6 +421,32 @@ __global__ void __launch_bounds__(32 * kBatchWarps, 3)
               });
 }
 
+// Flow kernel for the serving mix: FP32 grids (4 sites per lane) and 16-bit
+// grids of storage S2 and rounding RND2 (8 sites per lane), both walks inlined.
+template <int S2, int RND2>
+__global__ void __launch_bounds__(32 * kBatchWarps, 3)
+    k_flow_two(const GridDesc *__restrict__ grids, int ngrids, const Tile *__restrict__ tiles,
+               const long long *__restrict__ limit, const int *__restrict__ parity0,
+               const uint32_t *__restrict__ t0, unsigned long long *ctl, int *prog,
+               unsigned *glob, const int *__restrict__ nwork_p, int *status,
+               unsigned long long timeout_ns) {
+    __shared__ uint4 rowbuf[kBatchWarps][2 * 9 * 32];
+    flow_loop(grids, ngrids, tiles, limit, parity0, t0, ctl, prog, glob, nwork_p, status,
+              timeout_ns, [&](const GridDesc &g, int par, const Tile &t, uint32_t step) {
+                  const Coef c = g.c;
+                  if (g.kind == kind_code(ST_F32, 4, 0)) {
+                      Walker<ST_F32, 4, LD_CG> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P,
+                                                 t.x0);
+                      w.run(t.y0, t.y1, t.dir, c);
+                  } else {
+                      Walker<S2, 8, LD_CG, RND2> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P,
+                                                   t.x0);
+                      if constexpr (RND2) w.set_step(step);
+                      w.run_async(t.y0, t.y1, t.dir, c, &rowbuf[threadIdx.x >> 5][0]);
+                  }
+              });
+}
+
 using FlowKernel = void (*)(const GridDesc *, int, const Tile *, const long long *, const int *,
                             const uint32_t *, unsigned long long *, int *, unsigned *,
                             const int *, int *, unsigned long long);
@@ -450,6 +475,28 @@ FlowKernel flow_kernel_for(const std::vector<int> &kinds, int walk16) {
                 return two ? k_flow_one<ST_BF16, 4, 2, 0> : k_flow_one<ST_BF16, 4, 1, 0>;
             case kind_code(ST_F32, 4, 0, 1):
                 return k_flow_one<ST_F32, 4, 0, 0, 1>;
+            default:
+                break;
+        }
+    }
+    // FP32 (4 sites per lane) with one 16-bit kind of 8 sites per lane.
+    int other = -1;
+    bool pair = !kinds.empty();
+    for (int k : kinds) {
+        if (k == kind_code(ST_F32, 4, 0)) continue;
+        if (other == -1) other = k;
+        pair = pair && k == other;
+    }
+    if (pair && other != -1) {
+        switch (other) {
+            case kind_code(ST_F16, 8, 0):
+                return k_flow_two<ST_F16, 0>;
+            case kind_code(ST_BF16, 8, 0):
+                return k_flow_two<ST_BF16, 0>;
+            case kind_code(ST_F16, 8, 1):
+                return k_flow_two<ST_F16, 1>;
+            case kind_code(ST_BF16, 8, 1):
+                return k_flow_two<ST_BF16, 1>;
             default:
                 break;
         }

@@ -158,6 +158,8 @@ static Err launch_step_t(const TileCfg &cfg, const void *fin, void *fout, int nx
                                       P, g.nstrips, g.ntiles, cfg.rows, c, tdev, toff, a15f);
                 else
                     return cudaErrorInvalidValue;
+            } else if constexpr (S == ST_F32 && V == 4) {
+                return cudaErrorInvalidValue;  // launch_step_s runs the 2-site walk instead
             } else {
                 return launch_pdl(k_step<S, V, false, 0, 1>, nb, nt, 0, st, fin, fout, nx, ny, P,
                                   g.nstrips, g.ntiles, cfg.rows, c, tdev, toff, a15f);
@@ -238,6 +240,15 @@ static Err launch_step_s(const TileCfg &cfg, const void *fin, void *fout, int nx
                          const Coef &c, int *status, int rnd, const uint32_t *tdev,
                          uint32_t toff, const float *a15f, cudaStream_t st) {
     if (a15f && (rnd || cfg.vec == 8)) return cudaErrorInvalidValue;
+    if (S == ST_F32 && a15f && cfg.vec == 4) {
+        // FP32 with a c2 field: the 4-site walk needs more than 128 registers
+        // with the field's four alphas (it spilled 60 bytes); the 2-site walk
+        // with one row of loads prefetched runs at the same speed within 120.
+        TileCfg c2 = cfg;
+        c2.vec = 2;
+        c2.stages = 1;
+        return launch_step_t<S, 2, 0>(c2, fin, fout, nx, ny, P, c, tdev, toff, a15f, st);
+    }
     if (rnd) {
         // Stochastic rounding: register walks with vec 1, 2 or 4.
         if constexpr (S == ST_F32) {

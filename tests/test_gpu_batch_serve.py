@@ -21,11 +21,16 @@ def _trace():
             for k, (nx, ny, st, steps) in enumerate(specs)]
 
 
-@pytest.mark.parametrize("overlap", [True, False])
-def test_served_results_equal_solo_runs(lbm, overlap):
+@pytest.mark.parametrize("overlap,schedule,policy", [(True, "lockstep", "fair"),
+                                                     (False, "lockstep", "fair"),
+                                                     (True, "lockstep", "srpt"),
+                                                     (True, "flow", "fair"),
+                                                     (True, "flow", "srpt")])
+def test_served_results_equal_solo_runs(lbm, overlap, schedule, policy):
     reqs = _trace()
     srv = serve.Server(quantum=48, max_slots=3, keep_fields=True, reserve_bytes=0,
-                       overlap=overlap)
+                       overlap=overlap, schedule=schedule, policy=policy,
+                       flow_updates=2e5, flow_max_steps=64, srpt_sites=8000)
     stats = srv.run(reqs, realtime=False)
     assert len(stats.results) == len(reqs)
     assert stats.max_active == 3
@@ -381,6 +386,36 @@ def test_flow_schedule_timeout_reports_status(lbm):
     b.step(5)
     assert b.sync() == 0
     assert all(g.t == 5 for g in grids)
+    b.close()
+    for g in grids:
+        g.close()
+
+
+def test_flow_schedule_serving_mix_two_walks(lbm):
+    """The serving mix (FP32 and FP16-delta grids, nx multiples of 8) runs
+    the flow kernel with both walks inlined; every grid equals its solo run
+    bitwise, including grids small enough for short tiles."""
+    specs = [(2048, 256, 0.8, 0.2, "f32"), (512, 512, 0.6, 0.1, "f16d"),
+             (128, 128, 0.7, 0.3, "f32"), (136, 72, 0.9, 0.25, "f16d"), (64, 8, 0.55, 0.05, "f16d")]
+    limits = [20, 60, 300, 250, 90]
+
+    def fields(nx, ny):
+        return workloads.fourier_modes(nx, ny, amp=1e-3, seed=nx + ny)
+
+    solo = _solo_states(lbm, specs, limits, fields)
+    grids = []
+    for nx, ny, tau, c2, st in specs:
+        g = lbm.Grid(nx, ny, tau, c2, st)
+        g.init(*fields(nx, ny))
+        grids.append(g)
+    b = lbm.Batch(grids)
+    b.set_schedule("flow")
+    assert b.get_config()["specialised"]
+    b.step(300, limits)
+    assert b.sync() == 0
+    for g, s_, lim in zip(grids, solo, limits):
+        assert g.t == lim
+        assert np.array_equal(g.get_state()[0], s_)
     b.close()
     for g in grids:
         g.close()
