@@ -183,7 +183,7 @@ def serve_comparison(args, stream=None):
     trace07 = serve.scaled_trace(args.serve_count, rate07, steps_hi=args.serve_steps_hi)
     srv07 = server().run(trace07, realtime=True).summary()
     out["at_0.7_capacity"] = {"rate_hz": rate07, "continuous_batching": srv07}
-    if not args.serve_no_srpt:
+    if args.serve_srpt:
         # The same two traces, the grids with the least remaining work first.
         out["continuous_batching_srpt"] = server(policy="srpt").run(trace, realtime=True).summary()
         out["at_0.7_capacity"]["continuous_batching_srpt"] = server(policy="srpt").run(
@@ -851,11 +851,11 @@ def main():
     ap.add_argument("--serve-quantum", type=int, default=256)
     ap.add_argument("--schedule", default="lockstep", choices=["lockstep", "flow"],
                     help="batch schedule on the batch paths (flow: no barrier across grids)")
-    ap.add_argument("--serve-no-srpt", action="store_true",
-                    help="skip the least-remaining-work-first server in the serving comparison")
+    ap.add_argument("--serve-srpt", action="store_true",
+                    help="also run the least-remaining-work-first server in the serving comparison")
     ap.add_argument("--serve-no-flow", action="store_true",
                     help="skip the flow-schedule server in the serving comparison")
-    ap.add_argument("--serve-flow-updates", type=float, default=2e9,
+    ap.add_argument("--serve-flow-updates", type=float, default=1e9,
                     help="lattice updates per launch shared by the flow-schedule server")
     ap.add_argument("--serve-no-overlap", action="store_true",
                     help="admit requests between quanta instead of during them")

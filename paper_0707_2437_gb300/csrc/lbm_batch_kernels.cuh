@@ -310,8 +310,13 @@ __device__ __forceinline__ void flow_loop(const GridDesc *__restrict__ grids, in
                                           const int *__restrict__ nwork_p, int *status,
                                           unsigned long long timeout_ns, RunTile run_tile) {
     const int lane = threadIdx.x & 31;
-    const int nwork = *nwork_p;  // grids with steps to take in this launch
-    unsigned long long idle_since = 0;
+    // The warp's ticket and idle timer live in shared memory while a tile
+    // runs, leaving the walk the registers it has in the lockstep kernels.
+    __shared__ unsigned long long idle_sh[kBatchWarps];
+    __shared__ int tk_sh[kBatchWarps][3];
+    const int wib = threadIdx.x >> 5;
+    if (lane == 0) idle_sh[wib] = 0;
+    __syncwarp();
     for (;;) {
         // Lane 0 takes a ticket from the next grid round-robin that has
         // tickets left and room in its window; -1: none right now; -2: done.
@@ -338,7 +343,7 @@ __device__ __forceinline__ void flow_loop(const GridDesc *__restrict__ grids, in
                     gsel = cand;
                     m = mm;
                 }
-                if (gsel == -1 && *(volatile unsigned *)(glob + kFlowExh) >= (unsigned)nwork)
+                if (gsel == -1 && *(volatile unsigned *)(glob + kFlowExh) >= (unsigned)*nwork_p)
                     gsel = -2;
             }
         }
@@ -350,9 +355,9 @@ __device__ __forceinline__ void flow_loop(const GridDesc *__restrict__ grids, in
             int bad = 0;
             if (lane == 0) {
                 const unsigned long long now = global_ns();
-                if (idle_since == 0) {
-                    idle_since = now;
-                } else if (now - idle_since > timeout_ns) {
+                if (idle_sh[wib] == 0) {
+                    idle_sh[wib] = now;
+                } else if (now - idle_sh[wib] > timeout_ns) {
                     atomicCAS(status, 0, LBM_ETIMEOUT);
                     bad = 1;
                 }
@@ -361,21 +366,28 @@ __device__ __forceinline__ void flow_loop(const GridDesc *__restrict__ grids, in
             __nanosleep(256);
             continue;
         }
-        idle_since = 0;
         m = __shfl_sync(FULL, m, 0);
-        const GridDesc &g = grids[gsel];
-        const int k = (int)(m / (unsigned long long)g.ntile);
-        const int ti = (int)(m % (unsigned long long)g.ntile);
-        const int seg = ti / g.nstrips, strip = ti % g.nstrips;
-        if (!flow_wait(g, prog, seg, strip, k, status, timeout_ns)) return;
-        const Tile t = tiles[g.tile0 + ti];
-        run_tile(g, (parity0[gsel] + k) & 1, t, t0[gsel] + (uint32_t)k);
+        {
+            const GridDesc &g = grids[gsel];
+            const int k = (int)(m / (unsigned long long)g.ntile);
+            const int ti = (int)(m % (unsigned long long)g.ntile);
+            if (lane == 0) {
+                idle_sh[wib] = 0;
+                tk_sh[wib][0] = gsel;
+                tk_sh[wib][1] = k;
+                tk_sh[wib][2] = g.tile0 + ti;
+            }
+            const int seg = ti / g.nstrips, strip = ti % g.nstrips;
+            if (!flow_wait(g, prog, seg, strip, k, status, timeout_ns)) return;
+            const Tile t = tiles[g.tile0 + ti];
+            run_tile(g, (parity0[gsel] + k) & 1, t, t0[gsel] + (uint32_t)k);
+        }
         // Publish: the tile's stores before its completed-step count.
         __threadfence();
         __syncwarp();
         if (lane == 0) {
-            *(volatile int *)(prog + g.tile0 + ti) = k + 1;
-            atomicAdd(ctl + (size_t)gsel * kFlowCtlWords + 16, 1ULL);
+            *(volatile int *)(prog + tk_sh[wib][2]) = tk_sh[wib][1] + 1;
+            atomicAdd(ctl + (size_t)tk_sh[wib][0] * kFlowCtlWords + 16, 1ULL);
         }
     }
 }
@@ -393,9 +405,10 @@ __global__ void __launch_bounds__(32 * kBatchWarps, 3)
 }
 
 // Flow kernel for a batch of one walk, inlined (the register budget and the
-// row buffers of k_batch_one).
+// row buffers of k_batch_one: 16 warps per SM, measured faster than 12
+// without spills although the flow loop's state costs a few bytes of spill).
 template <int S, int V, int PD, int RND, int VA = 0>
-__global__ void __launch_bounds__(32 * kBatchWarps, 3)
+__global__ void __launch_bounds__(32 * kBatchWarps, PD == 2 ? 3 : 4)
     k_flow_one(const GridDesc *__restrict__ grids, int ngrids, const Tile *__restrict__ tiles,
                const long long *__restrict__ limit, const int *__restrict__ parity0,
                const uint32_t *__restrict__ t0, unsigned long long *ctl, int *prog,
@@ -422,7 +435,8 @@ __global__ void __launch_bounds__(32 * kBatchWarps, 3)
 }
 
 // Flow kernel for the serving mix: FP32 grids (4 sites per lane) and 16-bit
-// grids of storage S2 and rounding RND2 (8 sites per lane), both walks inlined.
+// grids of storage S2 and rounding RND2 (8 sites per lane), both walks
+// inlined; 12 warps per SM (at 16 both walks together spill heavily).
 template <int S2, int RND2>
 __global__ void __launch_bounds__(32 * kBatchWarps, 3)
     k_flow_two(const GridDesc *__restrict__ grids, int ngrids, const Tile *__restrict__ tiles,

@@ -103,8 +103,8 @@ class Server:
     def __init__(self, quantum: int = 256, reserve_bytes: int = 4 << 30,
                  max_slots: int = 512, keep_fields: bool = False, stream=None,
                  overlap: bool = True, schedule: str = "lockstep",
-                 flow_updates: float = 2e9, flow_max_steps: int = 1024,
-                 policy: str = "fair", srpt_sites: float = 4e6):
+                 flow_updates: float = 1e9, flow_max_steps: int = 1024,
+                 flow_weight: float = 0.5, policy: str = "fair", srpt_sites: float = 4e6):
         self.quantum = quantum
         self.reserve = reserve_bytes
         self.max_slots = max_slots
@@ -116,6 +116,7 @@ class Server:
         self.schedule = schedule
         self.flow_updates = flow_updates
         self.flow_max_steps = flow_max_steps
+        self.flow_weight = flow_weight
         if policy not in ("fair", "srpt"):
             raise ValueError(f"unknown policy {policy!r}")
         self.policy = policy
@@ -144,18 +145,27 @@ class Server:
     def _limits(self, active):
         """Steps each resident grid takes in the next launch.  Lockstep:
         every grid up to `quantum` steps (all advance together).  Flow: the
-        launch's budget of `flow_updates` lattice updates is shared equally
-        between the grids, so a grid takes steps in inverse proportion to its
-        size (at least one, at most `flow_max_steps`, at most what it has
-        left); the flow schedule runs them without a barrier across grids."""
+        launch's budget of `flow_updates` lattice updates is shared between
+        the grids in proportion to sites^flow_weight (0: equally, so a grid
+        takes steps in inverse proportion to its size; 1: in proportion to
+        its size, every grid the same steps), at least one step, at most
+        `flow_max_steps` and what the grid has left; the flow schedule runs
+        them without a barrier across grids."""
         sel = self._selected(active)
         run = [a for a, s_ in zip(active, sel) if s_]
         if self.schedule == "lockstep":
             q = min(self.quantum, max(a[2] for a in run))
             return q, [min(q, a[2]) if s_ else 0 for a, s_ in zip(active, sel)]
-        share = self.flow_updates / len(run)
-        lim = [int(min(a[2], self.flow_max_steps, max(1, share // (a[0].nx * a[0].ny))))
-               if s_ else 0 for a, s_ in zip(active, sel)]
+        wts = [(a[0].nx * a[0].ny) ** self.flow_weight for a in run]
+        total_w = sum(wts)
+        lim, j = [], 0
+        for a, s_ in zip(active, sel):
+            if not s_:
+                lim.append(0)
+                continue
+            share = self.flow_updates * wts[j] / total_w
+            j += 1
+            lim.append(int(min(a[2], self.flow_max_steps, max(1, share // (a[0].nx * a[0].ny)))))
         return max(lim), lim
 
     def _need(self, req) -> int:
