@@ -202,7 +202,8 @@ def test_flow_schedule_shares_updates_equally(monkeypatch):
     monkeypatch.setattr(serve, "lbm", _fake_lbm(dev))
     reqs = _requests(n=16)
     budget = 4e6
-    srv = serve.Server(reserve_bytes=0, schedule="flow", flow_updates=budget, flow_max_steps=900)
+    srv = serve.Server(reserve_bytes=0, schedule="flow", flow_updates=budget, flow_max_steps=900,
+                       flow_weight=0.0)
     stats = srv.run(reqs, realtime=False)
     assert len(stats.results) == len(reqs) and dev.live == 0
     for q, g in zip(reqs, dev.created):
@@ -251,3 +252,25 @@ def test_srpt_policy_steps_the_least_remaining_work_first(monkeypatch):
 def test_unknown_policy_is_refused():
     with pytest.raises(ValueError):
         serve.Server(policy="lifo")
+
+
+def test_flow_shares_weighted_by_size(monkeypatch):
+    """With flow_weight w a grid's share of a launch's updates is in
+    proportion to sites^w: w = 1 gives every grid the same steps (up to what
+    it has left), w = 0.5 gives larger grids more updates but fewer steps."""
+    for w in (1.0, 0.5):
+        dev = _FakeDevice(total=1 << 40)
+        monkeypatch.setattr(serve, "lbm", _fake_lbm(dev))
+        reqs = _requests(n=12)
+        srv = serve.Server(reserve_bytes=0, schedule="flow", flow_updates=2e7,
+                           flow_max_steps=10 ** 6, flow_weight=w)
+        srv.run(reqs, realtime=False)
+        _, first = dev.steps[0]
+        wts = [s_ ** w for s_, _ in first]
+        for (sites, lim), wt in zip(first, wts):
+            share = 2e7 * wt / sum(wts)
+            assert lim <= max(1, share // sites)
+        by_size = sorted(first)
+        if w == 0.5:
+            assert by_size[0][1] >= by_size[-1][1]
+            assert by_size[0][0] * by_size[0][1] <= by_size[-1][0] * by_size[-1][1] * 1.01 + by_size[-1][0]
