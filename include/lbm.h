@@ -323,9 +323,7 @@ int lbm_batch_get_groups(lbm_batch_t b, int *groups);
 
 /* The walk of 16-bit grids in a batch (results are bitwise the same for all):
  *   LBM_WALK16_AUTO    the default: LBM_WALK16_V8, the faster on GB300 for
- *                      both roundings, except (lockstep schedule) for grids
- *                      whose width fills 128-column strips much better than
- *                      256-column ones, which take LBM_WALK16_V4
+ *                      both roundings
  *   LBM_WALK16_V8      8 sites per lane, 128-bit loads, when nx is a multiple
  *                      of 8 (else as LBM_WALK16_V4)
  *   LBM_WALK16_V4      4 sites per lane, 64-bit loads, one row of loads in

@@ -114,27 +114,9 @@ static void drop_graph(lbm_batch *b) {
 // when nx is a multiple of 4.  Any other nx: 1.  (Measured on GB300: 8 sites
 // per lane run 15 % faster than 4 with nearest rounding and 10 % faster with
 // stochastic rounding.)
-//
-// With LBM_WALK16_AUTO in the lockstep schedule a 16-bit grid takes the
-// 4-site walk instead when its strips use the lanes so much better that it
-// pays for that walk's cost per site: every lane of a warp executes the walk
-// whether or not its sites exist, so a grid 264 wide keeps 33 of 64 lanes
-// busy with 8 sites per lane and 66 of 96 with 4.  The 4-site walk costs
-// kWalk4Cost times the 8-site walk per site (measured: 136.8k against
-// 158.1k MLUPS on full strips).  The flow schedule keeps one walk per storage
-// (its kernels inline at most two walks).
-constexpr double kWalk4Cost = 1.156;
-
 static int batch_vec(const lbm_batch *b, const lbm_grid *g) {
     const bool eight = !g->a15f && (b->walk16 == LBM_WALK16_V8 || b->walk16 == LBM_WALK16_AUTO);
-    if (g->storage != ST_F32 && eight && g->nx % 8 == 0) {
-        if (b->walk16 == LBM_WALK16_AUTO && b->schedule == LBM_SCHEDULE_LOCKSTEP) {
-            const double use8 = (double)g->nx / (256.0 * ((g->nx + 255) / 256));
-            const double use4 = (double)g->nx / (128.0 * ((g->nx + 127) / 128));
-            if (use4 > kWalk4Cost * use8) return 4;
-        }
-        return 8;
-    }
+    if (g->storage != ST_F32 && eight && g->nx % 8 == 0) return 8;
     return g->nx % 4 == 0 ? 4 : 1;
 }
 
