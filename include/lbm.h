@@ -384,6 +384,49 @@ int lbm_batch_get_launch(lbm_batch_t b, int *mode, int *last, int *capture_faile
 /* Barrier wait limit of the batch kernel in microseconds (default 1e6). */
 int lbm_batch_set_timeout_us(lbm_batch_t b, long long us);
 
+/* ---- Slab decomposition in y (one grid over several GPUs) ---------------- */
+
+/* A slab of a grid split along y between ranks (one GPU each): rank r of N
+ * owns the global rows [r*ny_local, (r+1)*ny_local); the grid stays
+ * periodic in x and in y (rank 0's lower neighbour is rank N-1).  A step of
+ * Eq. 5 at a row reads the stored values up to two rows away (the pull, and
+ * the central gradient of the pulled density, Section 4), so the handle's
+ * buffers hold ny_local + 4 rows: ghost rows 0 and 1 (copies of the lower
+ * neighbour's two highest rows), the own rows 2 .. ny_local+1, and ghost rows
+ * ny_local+2 and ny_local+3 (copies of the upper neighbour's two lowest).
+ *   nx, tau, c2, storage, cuda_stream, out  as lbm_create
+ *   ny_local  own rows, >= 2
+ * The handle is an ordinary one otherwise: lbm_init, lbm_moments,
+ * lbm_get_state, lbm_set_c2_field and so on see the whole local buffer,
+ * [ny_local + 4][nx], ghost rows included.  lbm_step takes n = 1 only (the
+ * ghost rows must be refreshed between steps; LBM_EINVAL otherwise) and
+ * computes the own rows, with the batch kernel over their tiles; a slab can
+ * also join a batch.  Driven slabs are refused.  Returns as lbm_create. */
+int lbm_slab_create(int nx, int ny_local, double tau, double c2, int storage,
+                    void *cuda_stream, lbm_t *out);
+
+/* Bytes of one side's halo: 9 planes x 2 rows x nx elements of the storage
+ * type (0 for a handle that is not a slab). */
+size_t lbm_slab_halo_bytes(lbm_t h);
+
+/* Halo exchange, queued on the handle's stream (asynchronous):
+ *   lbm_slab_pack(h, dst, 0)    own rows 2, 3 (to send to the lower
+ *                               neighbour)          -> dst
+ *   lbm_slab_pack(h, dst, 1)    own rows ny_local, ny_local+1 (to send to
+ *                               the upper neighbour) -> dst
+ *   lbm_slab_unpack(h, src, 0)  src -> ghost rows 0, 1 (from the lower
+ *                               neighbour's side-1 pack)
+ *   lbm_slab_unpack(h, src, 1)  src -> ghost rows ny_local+2, +3 (from the
+ *                               upper neighbour's side-0 pack)
+ * dst/src are device buffers of lbm_slab_halo_bytes bytes, packed as
+ * [9][2][nx] of the current state (after the last lbm_step).  The transfer
+ * between ranks is the caller's; order it with the handle's stream.  A
+ * single slab exchanging with itself (side 0 into side 1 and back) is the
+ * periodic grid.  LBM_EINVAL for a bad side, NULL or a handle that is not a
+ * slab. */
+int lbm_slab_pack(lbm_t h, void *dst, int side);
+int lbm_slab_unpack(lbm_t h, const void *src, int side);
+
 /* ---- Grid totals without allocation ------------------------------------- */
 
 /* The paper has no counterpart to this call; it is a service for callers that

@@ -445,9 +445,14 @@ extern "C" int lbm_step(lbm_t h, long long n) {
         h->kernel_launches = n;
         return LBM_OK;
     }
+    if (h->slab && n != 1)
+        return fail(LBM_EINVAL, "lbm_step: a slab takes one step at a time (its ghost rows "
+                                "are refreshed between steps)");
     const bool large = (long long)h->nx * h->ny >= kLargeSites;
-    if (h->persistent && !h->drive &&
-        (n >= kPersistentMin || (large && n >= kPersistentMinLarge))) {
+    if (h->slab || (h->persistent && !h->drive &&
+                    (n >= kPersistentMin || (large && n >= kPersistentMinLarge)))) {
+        // Slabs always step here: the batch's tile list covers only their
+        // own rows.
         // One persistent launch of all n steps (dynamic tile scheduling,
         // barrier between steps), bitwise the same as n single launches.
         if (!h->self_batch) {
@@ -696,6 +701,7 @@ extern "C" int lbm_set_c2_field(lbm_t h, const double *c2, int on_device) {
 extern "C" int lbm_set_drive(lbm_t h, int on, double amplitude, double period) {
     if (!h) return fail(LBM_EINVAL, "lbm_set_drive: NULL handle");
     if (on) {
+        if (h->slab) return fail(LBM_EINVAL, "lbm_set_drive: a slab cannot be driven");
         if (h->nx < 4) return fail(LBM_EINVAL, "lbm_set_drive: needs nx >= 4");
         if (!(period > 0.0) || !isfinite(period))
             return fail(LBM_EINVAL, "lbm_set_drive: period must be finite and > 0");

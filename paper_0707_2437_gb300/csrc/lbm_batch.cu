@@ -182,25 +182,27 @@ static int build_worklist(lbm_batch *b) {
         int rows = b->rows;
         if (b->schedule == LBM_SCHEDULE_FLOW) {
             const long long tiles_tall =
-                (long long)((g->nx + w - 1) / w) * ((g->ny + b->rows - 1) / b->rows);
+                (long long)((g->nx + w - 1) / w) * ((g->ny - 2 * g->slab + b->rows - 1) / b->rows);
             if (tiles_tall * (long long)b->grids.size() < flow_warps) rows = std::max(1, b->rows / 4);
         }
+        // Rows computed: all of them, or a slab's own rows between its ghosts.
+        const int ylo = g->slab, yhi = g->ny - g->slab, nyc = yhi - ylo;
         d.tile0 = (int)tiles.size();
         d.nstrips = (g->nx + w - 1) / w;
-        d.nsegs = (g->ny + rows - 1) / rows;
+        d.nsegs = (nyc + rows - 1) / rows;
         d.ntile = d.nstrips * d.nsegs;
         // A step reads two rows and two columns beyond its tile: the next
         // segment or strip over suffices unless one of them is a single row
         // or column wide (the last one of a grid can be).
-        const int last_rows = g->ny - (d.nsegs - 1) * rows;
+        const int last_rows = nyc - (d.nsegs - 1) * rows;
         const int last_cols = g->nx - (d.nstrips - 1) * w;
         d.dseg = (rows >= 2 && last_rows >= 2) ? 1 : 2;
         d.dstrip = last_cols >= 2 ? 1 : 2;
         // Neighbouring segments walk in opposite directions, so the rows they
         // share are read by both at about the same time (from L2 the second time).
-        for (int y0 = 0, seg = 0; y0 < g->ny; y0 += rows, ++seg)
+        for (int y0 = ylo, seg = 0; y0 < yhi; y0 += rows, ++seg)
             for (int x0 = 0; x0 < g->nx; x0 += w)
-                tiles.push_back(Tile{(int)k, x0, y0, std::min(g->ny, y0 + rows),
+                tiles.push_back(Tile{(int)k, x0, y0, std::min(yhi, y0 + rows),
                                      (seg & 1) ? -1 : 1});
     }
     if (b->schedule == LBM_SCHEDULE_FLOW) {
@@ -234,7 +236,7 @@ static int build_worklist(lbm_batch *b) {
     std::vector<int> count(kKindCodes, 0);
     for (size_t k = 0; k < b->grids.size(); ++k) {
         const lbm_grid *g = b->grids[k];
-        bytes[gd[k].kind] += (double)g->nx * g->ny *
+        bytes[gd[k].kind] += (double)g->nx * (g->ny - 2 * g->slab) *
                              ((g->storage == ST_F32 ? 72.0 : 36.0) + (g->a15f ? 4.0 : 0.0));
     }
     for (const Tile &t : tiles) count[gd[t.grid].kind]++;

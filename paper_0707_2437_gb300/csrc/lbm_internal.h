@@ -111,6 +111,10 @@ struct lbm_grid {
     vss::TileCfg cfg{};
     int rounding = 0;             // 1: stochastic rounding of 16-bit stores
     float *a15f = nullptr;        // spatially varying alpha: 1.5 alpha per site
+    // Slab of a grid decomposed in y (lbm_slab_create): this many ghost rows
+    // at each end of the local buffer, which steps read but never compute
+    // (0 for an ordinary periodic grid).
+    int slab = 0;
     // Driven channel in x (lbm_set_drive): boundary columns after every step.
     bool drive = false;
     double drive_amp = 0, drive_period = 0;

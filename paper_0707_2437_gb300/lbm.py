@@ -94,6 +94,10 @@ def load() -> ctypes.CDLL:
             "lbm_batch_get_launch": ([vp, ctypes.POINTER(i), ctypes.POINTER(i),
                                       ctypes.POINTER(i)], i),
             "lbm_sums_noalloc": ([vp, i, i, sz, i, d, vp, dp], i),
+            "lbm_slab_create": ([i, i, d, d, i, vp, ctypes.POINTER(vp)], i),
+            "lbm_slab_halo_bytes": ([vp], sz),
+            "lbm_slab_pack": ([vp, vp, i], i),
+            "lbm_slab_unpack": ([vp, vp, i], i),
             "lbm_strerror": ([i], ctypes.c_char_p),
             "lbm_last_error": ([], ctypes.c_char_p),
         }
@@ -335,6 +339,45 @@ class Grid:
         ms, n = ctypes.c_double(), ctypes.c_longlong()
         _check(self.lib.lbm_kernel_ms(self.h, ctypes.byref(ms), ctypes.byref(n)), "lbm_kernel_ms")
         return ms.value, n.value
+
+
+class Slab(Grid):
+    """The slab of a grid split along y that one rank owns (lbm_slab_create):
+    `ny_local` own rows between two ghost rows on each side; the local buffer
+    (fields of init / moments) is [ny_local + 4][nx].  step() takes one step;
+    pack / unpack move the halo rows through device buffers."""
+
+    GHOST = 2
+
+    def __init__(self, nx: int, ny_local: int, tau: float, c2: float, storage: str = "f32",
+                 stream=None):
+        self.lib = load()
+        self.nx, self.ny, self.tau, self.c2 = nx, ny_local + 2 * self.GHOST, tau, c2
+        self.ny_local = ny_local
+        self.storage = storage
+        self.rho0 = 1.0
+        self._stream = stream
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(_stream_handle(stream))
+        self.status = _check(self.lib.lbm_slab_create(nx, ny_local, tau, c2, STORAGE[storage],
+                                                       st, ctypes.byref(h)), "lbm_slab_create")
+        self.h = h
+
+    @property
+    def halo_bytes(self) -> int:
+        return int(self.lib.lbm_slab_halo_bytes(self.h))
+
+    def pack(self, side: int, out):
+        """Own rows next to `side` (0: the two lowest, 1: the two highest) into
+        the device buffer `out` (a CUDA tensor of halo_bytes bytes)."""
+        _check(self.lib.lbm_slab_pack(self.h, ctypes.c_void_p(out.data_ptr()), side),
+               "lbm_slab_pack")
+
+    def unpack(self, side: int, src):
+        """The device buffer `src` into the ghost rows of `side` (0: below,
+        1: above)."""
+        _check(self.lib.lbm_slab_unpack(self.h, ctypes.c_void_p(src.data_ptr()), side),
+               "lbm_slab_unpack")
 
 
 WALK16 = {"auto": 0, "v8": 1, "v4": 2, "v4pf2": 3}

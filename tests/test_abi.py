@@ -111,6 +111,9 @@ def test_every_handle_call_rejects_null_before_device_work():
         lambda: lib.lbm_batch_set_timeout_us(None, 1000),
         lambda: lib.lbm_batch_set_launch(None, 0),
         lambda: lib.lbm_batch_set_schedule(None, 0),
+        lambda: lib.lbm_slab_pack(None, buf, 0),
+        lambda: lib.lbm_slab_unpack(None, buf, 0),
+        lambda: lib.lbm_slab_create(8, 8, 0.8, 0.2, 0, None, None),
         lambda: lib.lbm_batch_get_schedule(None, ctypes.byref(i)),
         lambda: lib.lbm_batch_get_launch(None, ctypes.byref(i), ctypes.byref(i),
                                          ctypes.byref(i)),
@@ -119,3 +122,4 @@ def test_every_handle_call_rejects_null_before_device_work():
         assert call() == -1, k
     assert lib.lbm_batch_destroy(None) == 0
     assert lib.lbm_state_bytes(None) == 0
+    assert lib.lbm_slab_halo_bytes(None) == 0
