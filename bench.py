@@ -791,6 +791,77 @@ def run_batch_workload(args):
         print(json.dumps(line), flush=True)
 
 
+def run_slab_workload(args):
+    """One grid split along y between the ranks (one GPU each): every step
+    is the local step of each rank's slab and the halo exchange (two rows of
+    all nine planes with each neighbour, NCCL point-to-point; with one rank,
+    the slab's own rows wrap around).  Strong scaling: the grid is fixed."""
+    import functools
+
+    import torch
+
+    from paper_0707_2437_gb300 import lbm, slab
+
+    ws, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    n = args.slab_n
+    if n % ws:
+        raise SystemExit(f"bench.py: the {n} rows do not split evenly over {ws} ranks")
+    ny_local = n // ws
+    tau, c2 = 0.6, 0.15
+    rho, ux, uy = workloads.fourier_modes(n, n, amp=1e-3, seed=3)
+    rows = [(rank * ny_local - 2 + k) % n for k in range(ny_local + 4)]
+    stream = torch.cuda.current_stream()
+    s = lbm.Slab(n, ny_local, tau, c2, args.storage, stream=stream)
+    s.init(rho[rows], ux[rows], uy[rows])
+    del rho, ux, uy
+    ds = slab.DeviceSlab(s)
+    runner = slab.SlabRunner(ds, functools.partial(slab.exchange, rank=rank, world=ws))
+    runner.run(args.warmup)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        ds.step()
+        runner.refresh()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ms = max_over_ranks(ws, e0.elapsed_time(e1))
+    value = n * n * args.steps / (ms * 1e-3) / 1e6
+    per_rank_bytes = BYTES_PER_LU[args.storage] * n * ny_local * args.steps
+    achieved = per_rank_bytes / (ms * 1e-3) / 1e9
+    peak, _ = measured_peak()
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None,
+        "dtype": "f32" if args.storage == "f32" else f"{args.storage} storage, f32 math",
+        "data": "synthetic",
+        "config": {"workload": f"one {n}x{n} periodic grid split in y over the ranks, tau={tau}, "
+                               f"c2={c2}, 8 seeded plane waves of amplitude 1e-3",
+                   "storage": args.storage, "rows_per_rank": ny_local,
+                   "l2": f"{2 * n * (ny_local + 4) * BYTES_PER_LU[args.storage] / 2 / 1e9:.1f} GB "
+                         "of state per rank, no flush"},
+        "launch": {"path": "lbm_step(1) per slab (the batch kernel over the own rows) and a "
+                           "halo exchange per step", "halo_bytes_per_side": s.halo_bytes,
+                   "parallelism": f"slabs x{ws}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "note": "per rank: the algorithmic bytes of its own rows over the step time "
+                             "including the exchange"},
+        "gpu_launches": args.steps, "clocks": clk,
+    }
+    s.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_serve_workload(args):
     """The serving trace through the continuous-batching server and through
     the plain FIFO single-grid FP32 baseline; p50/p99 time-to-result and
@@ -829,10 +900,12 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--storage", default="f32", choices=list(BYTES_PER_LU) + ["mixed"])
     ap.add_argument("--workload", default="sweep2048",
-                    choices=["sweep2048", "fourier8192", "batch", "serve"])
+                    choices=["sweep2048", "fourier8192", "batch", "serve", "slab"])
     ap.add_argument("--rounding", default="nearest", choices=["nearest", "stochastic"],
                     help="rounding of 16-bit stores")
     ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--slab-n", type=int, default=8192,
+                    help="side of the grid the slab workload splits over the ranks")
     ap.add_argument("--batch-rows", type=int, default=0)
     ap.add_argument("--walk16", default=None, choices=["auto", "v8", "v4", "v4pf2"],
                     help="walk of 16-bit grids in batch kernels (default: the library's)")
@@ -895,6 +968,8 @@ def main():
         run_batch_workload(args)
     elif args.workload == "serve":
         run_serve_workload(args)
+    elif args.workload == "slab":
+        run_slab_workload(args)
     else:
         if args.storage == "mixed":
             ap.error("--storage mixed applies to the batch workload")
