@@ -38,8 +38,6 @@ struct lbm_batch {
         BatchKernel kernel = nullptr;
         FlowKernel fkernel = nullptr;  // flow schedule
         int max_blocks_per_sm = 1;
-        int gbegin = 0, gcount = 0;    // flow: the group's grids in d_gidx
-        int blocks = 0;                // flow: blocks of this call's launch
     };
     std::vector<Group> groups;
     int walk16 = LBM_WALK16_AUTO;  // walk of 16-bit grids (lbm_batch_set_walk16)
@@ -83,17 +81,8 @@ struct lbm_batch {
     unsigned long long *d_ctl = nullptr;
     int *d_prog = nullptr;
     size_t prog_cap = 0;
-    int *d_nwork = nullptr;  // per flow group
+    int *d_nwork = nullptr;
     int *h_nwork = nullptr;
-    // Flow groups: grid indices per group, ticket words per group, and the
-    // streams and events of the groups launched beside the first one.
-    int *d_gidx = nullptr;
-    unsigned *d_fglob = nullptr;
-    std::vector<cudaStream_t> aux;
-    std::vector<cudaEvent_t> joins;
-    cudaEvent_t fork = nullptr;
-    std::vector<int> graph_split;  // blocks per flow group of the captured graph
-    std::vector<int> flow_gidx;    // host copy of d_gidx
 };
 
 static int bfail(int code, const std::string &m) {
@@ -155,41 +144,21 @@ static int upload_worklist(lbm_batch *b, const std::vector<GridDesc> &gd,
 static int build_worklist(lbm_batch *b) {
     std::vector<GridDesc> gd(b->grids.size());
     std::vector<Tile> tiles;
-    // Flow schedule: one group per kind with a specialised flow kernel, the
-    // other kinds together in the general kernel; the groups launch side by
-    // side.  The warps they keep resident set each grid's tile height below.
-    std::vector<lbm_batch::Group> fgroups;
-    std::vector<int> gidx;
+    // Flow schedule: the kernel for the grids' kinds and the warps it keeps
+    // resident, which set each grid's tile height below.
+    FlowKernel fk = nullptr;
+    int flow_bps = 1;
     long long flow_warps = 0;
     if (b->schedule == LBM_SCHEDULE_FLOW) {
         std::vector<int> kinds;
         for (const lbm_grid *g : b->grids)
             kinds.push_back(kind_code(g->storage, batch_vec(b, g), g->rounding ? 1 : 0,
                                       g->a15f ? 1 : 0));
-        std::vector<int> order;  // group keys: a kind, or -1 for the general kernel
-        for (int kd : kinds) {
-            const int key = flow_kernel_for({kd}, b->walk16) == (FlowKernel)k_flow ? -1 : kd;
-            if (std::find(order.begin(), order.end(), key) == order.end()) order.push_back(key);
-        }
-        int bps_min = 1 << 30;
-        for (int key : order) {
-            lbm_batch::Group gr;
-            gr.gbegin = (int)gidx.size();
-            for (size_t k = 0; k < kinds.size(); ++k) {
-                const int kk = flow_kernel_for({kinds[k]}, b->walk16) == (FlowKernel)k_flow ? -1
-                                                                                          : kinds[k];
-                if (kk == key) gidx.push_back((int)k);
-            }
-            gr.gcount = (int)gidx.size() - gr.gbegin;
-            gr.fkernel = key == -1 ? (FlowKernel)k_flow : flow_kernel_for({key}, b->walk16);
-            BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &gr.max_blocks_per_sm, (const void *)gr.fkernel, 32 * kBatchWarps, 0));
-            if (gr.max_blocks_per_sm < 1)
-                return bfail(LBM_ECUDA, "flow kernel cannot be resident");
-            bps_min = std::min(bps_min, gr.max_blocks_per_sm);
-            fgroups.push_back(gr);
-        }
-        const int per = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, bps_min) : bps_min;
+        fk = flow_kernel_for(kinds, b->walk16);
+        BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&flow_bps, (const void *)fk,
+                                                          32 * kBatchWarps, 0));
+        if (flow_bps < 1) return bfail(LBM_ECUDA, "flow kernel cannot be resident");
+        const int per = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, flow_bps) : flow_bps;
         flow_warps = (long long)per * b->sms * kBatchWarps;
     }
     for (size_t k = 0; k < b->grids.size(); ++k) {
@@ -237,23 +206,15 @@ static int build_worklist(lbm_batch *b) {
                                      (seg & 1) ? -1 : 1});
     }
     if (b->schedule == LBM_SCHEDULE_FLOW) {
-        // Tiles grid by grid in their order; the groups list their grids.
-        b->groups = fgroups;
-        b->flow_gidx = gidx;
-        if (!b->d_gidx) BCK(cudaMalloc(&b->d_gidx, sizeof(int) * b->grids.size()));
-        BCK(cudaMemcpy(b->d_gidx, gidx.data(), sizeof(int) * gidx.size(),
-                       cudaMemcpyHostToDevice));
-        if (!b->d_fglob)
-            BCK(cudaMalloc(&b->d_fglob, sizeof(unsigned) * 64 * (b->grids.size() + 1)));
-        while (b->aux.size() + 1 < fgroups.size()) {
-            cudaStream_t st = nullptr;
-            cudaEvent_t ev = nullptr;
-            BCK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-            BCK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-            b->aux.push_back(st);
-            b->joins.push_back(ev);
-        }
-        if (!b->fork) BCK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+        // One launch over every grid, tiles grid by grid in their order.
+        b->groups.clear();
+        lbm_batch::Group gr;
+        gr.begin = 0;
+        gr.count = (int)tiles.size();
+        gr.kernel = nullptr;
+        gr.fkernel = fk;
+        gr.max_blocks_per_sm = flow_bps;
+        b->groups.push_back(gr);
         if (tiles.size() > b->prog_cap) {
             cudaFree(b->d_prog);
             b->d_prog = nullptr;
@@ -336,11 +297,6 @@ extern "C" int lbm_batch_destroy(lbm_batch_t b) {
     cudaFree(b->d_prog);
     cudaFree(b->d_nwork);
     if (b->h_nwork) cudaFreeHost(b->h_nwork);
-    cudaFree(b->d_gidx);
-    cudaFree(b->d_fglob);
-    for (cudaStream_t st : b->aux) cudaStreamDestroy(st);
-    for (cudaEvent_t ev : b->joins) cudaEventDestroy(ev);
-    if (b->fork) cudaEventDestroy(b->fork);
     if (b->h_limit) cudaFreeHost(b->h_limit);
     if (b->h_parity) cudaFreeHost(b->h_parity);
     if (b->h_t0) cudaFreeHost(b->h_t0);
@@ -383,8 +339,8 @@ extern "C" int lbm_batch_create(const lbm_t *grids, int n, lbm_batch_t *out) {
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_parity, sizeof(int) * n);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_t0, sizeof(uint32_t) * n);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_status, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_nwork, sizeof(int) * (n + 1));
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_nwork, sizeof(int) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_nwork, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_nwork, sizeof(int));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
@@ -428,32 +384,17 @@ static cudaError_t enqueue(lbm_batch *b, long long n, cudaStream_t st) {
     int *status = b->d_status;
     unsigned long long to = b->timeout_ns;
     if (b->schedule == LBM_SCHEDULE_FLOW) {
-        const int ngr = (int)b->groups.size();
-        e = cudaMemcpyAsync(b->d_nwork, b->h_nwork, sizeof(int) * ngr, cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(b->d_nwork, b->h_nwork, sizeof(int), cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess)
             e = cudaMemsetAsync(b->d_ctl, 0,
                                 sizeof(unsigned long long) * kFlowCtlWords * ng, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(b->d_prog, 0, sizeof(int) * b->ntiles, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_fglob, 0, sizeof(unsigned) * 64 * ngr, st);
-        if (e == cudaSuccess && ngr > 1) e = cudaEventRecord(b->fork, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned) * kBarWords, st);
         if (e != cudaSuccess) return e;
-        // Group 0 on the batch's stream, the others on streams of their own
-        // (after the zeroing above, joined back before the call returns): the
-        // groups' grids are disjoint and their waits never cross groups.
-        for (int i = 0; i < ngr && e == cudaSuccess; ++i) {
-            const lbm_batch::Group &gr = b->groups[i];
-            if (gr.blocks == 0) continue;  // no steps for this group's grids
-            cudaStream_t si = i == 0 ? st : b->aux[i - 1];
-            if (i > 0) e = cudaStreamWaitEvent(si, b->fork, 0);
-            if (e != cudaSuccess) break;
-            gr.fkernel<<<gr.blocks, 32 * kBatchWarps, 0, si>>>(
-                grids, gr.gcount, b->d_gidx + gr.gbegin, b->d_tiles, lim, par, t0, b->d_ctl,
-                b->d_prog, b->d_fglob + 64 * i, b->d_nwork + i, status, to);
-            e = cudaGetLastError();
-            if (e == cudaSuccess && i > 0) e = cudaEventRecord(b->joins[i - 1], si);
-            if (e == cudaSuccess && i > 0) e = cudaStreamWaitEvent(st, b->joins[i - 1], 0);
-        }
-        return e;
+        b->groups[0].fkernel<<<grid_blocks(b, b->groups[0]), 32 * kBatchWarps, 0, st>>>(
+            grids, ng, b->d_tiles, lim, par, t0, b->d_ctl, b->d_prog, bar, b->d_nwork, status,
+            to);
+        return cudaGetLastError();
     }
     // The groups hold disjoint grids: each launch advances its grids by all n
     // steps.  Barrier words and tile counters start at zero for every launch.
@@ -472,73 +413,19 @@ static cudaError_t enqueue(lbm_batch *b, long long n, cudaStream_t st) {
     return cudaSuccess;
 }
 
-// Flow schedule: the grids with steps in this call per group (h_nwork) and
-// each group's blocks (the resident blocks of the lightest-budget kernel on
-// every SM, shared in proportion to the bytes the group's grids move in this
-// call, at least a quarter of the SM count each, in quarters of the SM count
-// so that few distinct splits, and graphs, arise).  `split` lists them.
-static void flow_split(lbm_batch *b, std::vector<int> &split) {
-    const int ngr = (int)b->groups.size();
-    std::vector<double> work(ngr, 0.0);
-    double total = 0.0;
-    int bps = 1 << 30;
-    for (int i = 0; i < ngr; ++i) {
-        const lbm_batch::Group &gr = b->groups[i];
-        bps = std::min(bps, gr.max_blocks_per_sm);
-        int nw = 0;
-        for (int j = gr.gbegin; j < gr.gbegin + gr.gcount; ++j) {
-            const int k = b->flow_gidx[j];
-            const lbm_grid *g = b->grids[k];
-            const long long lim = b->h_limit[k];
-            nw += lim > 0;
-            work[i] += (double)lim * g->nx * (g->ny - 2 * g->slab) *
-                       ((g->storage == ST_F32 ? 72.0 : 36.0) + (g->a15f ? 4.0 : 0.0));
-        }
-        b->h_nwork[i] = nw;
-        total += work[i];
-    }
-    if (b->blocks_per_sm > 0) bps = std::min(bps, b->blocks_per_sm);
-    const int cap = bps * b->sms;
-    const int quarter = std::max(1, b->sms / 4);
-    split.assign(ngr, 0);
-    if (ngr == 1) {
-        split[0] = cap;
-    } else {
-        // Groups without steps in this call are not launched.
-        int used = 0, busiest = 0;
-        for (int i = 0; i < ngr; ++i) {
-            if (!b->h_nwork[i]) continue;
-            const double share = total > 0 ? cap * work[i] / total : (double)cap / ngr;
-            const int nb = std::max(quarter, (int)(share / quarter + 0.5) * quarter);
-            split[i] = nb;
-            used += nb;
-            if (work[i] > work[busiest] || !b->h_nwork[busiest]) busiest = i;
-        }
-        // Trim the largest share until the groups fit side by side; give
-        // what is left over to the group with the most work.
-        while (used > cap) {
-            int big = (int)(std::max_element(split.begin(), split.end()) - split.begin());
-            if (split[big] <= quarter) break;
-            split[big] -= quarter;
-            used -= quarter;
-        }
-        if (used < cap && b->h_nwork[busiest]) split[busiest] += cap - used;
-    }
-    for (int i = 0; i < ngr; ++i) b->groups[i].blocks = split[i];
-}
-
 static int run_batch(lbm_batch *b, long long n, const long long *limits, bool advance) {
     int ng = (int)b->grids.size();
     // The previous call's copies must have read the pinned arrays first.
     BCK(cudaEventSynchronize(b->copied));
+    int nwork = 0;
     for (int k = 0; k < ng; ++k) {
         long long lim = limits ? std::max(0LL, std::min(n, limits[k])) : n;
         b->h_limit[k] = lim;
         b->h_parity[k] = b->grids[k]->cur;
         b->h_t0[k] = (uint32_t)b->grids[k]->t;
+        nwork += lim > 0;
     }
-    std::vector<int> split;
-    if (b->schedule == LBM_SCHEDULE_FLOW) flow_split(b, split);
+    *b->h_nwork = nwork;
     // Work already queued on the members' own streams (an lbm_init, a step
     // call) runs before the batch's launches.
     int nxs = 0;
@@ -562,7 +449,7 @@ static int run_batch(lbm_batch *b, long long n, const long long *limits, bool ad
                             (b->launch_mode == LBM_LAUNCH_AUTO && !b->capture_failed);
     bool graphed = false;
     if (want_graph) {
-        if (b->graph_n != n || b->graph_split != split) {
+        if (b->graph_n != n) {
             drop_graph(b);
             cudaStream_t cs;
             BCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -585,7 +472,6 @@ static int run_batch(lbm_batch *b, long long n, const long long *limits, bool ad
                 b->capture_failed = true;
             } else {
                 b->graph_n = n;
-                b->graph_split = split;
             }
         }
         if (b->graph) {

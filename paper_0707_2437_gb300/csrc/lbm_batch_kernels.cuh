@@ -302,7 +302,6 @@ __device__ __forceinline__ bool flow_wait(const GridDesc &g, const int *prog, in
 // The flow loop of one warp; run_tile(g, par, tile, step) runs a tile.
 template <class RunTile>
 __device__ __forceinline__ void flow_loop(const GridDesc *__restrict__ grids, int ngrids,
-                                          const int *__restrict__ gidx,
                                           const Tile *__restrict__ tiles,
                                           const long long *__restrict__ limit,
                                           const int *__restrict__ parity0,
@@ -329,7 +328,7 @@ __device__ __forceinline__ void flow_loop(const GridDesc *__restrict__ grids, in
             } else {
                 const unsigned start = atomicAdd(glob + kFlowRR, 1u);
                 for (int j = 0; j < ngrids && gsel == -1; ++j) {
-                    const int cand = gidx[(start + (unsigned)j) % (unsigned)ngrids];
+                    const int cand = (int)((start + (unsigned)j) % (unsigned)ngrids);
                     const GridDesc &G = grids[cand];
                     const unsigned long long total =
                         (unsigned long long)limit[cand] * (unsigned long long)G.ntile;
@@ -395,12 +394,11 @@ __device__ __forceinline__ void flow_loop(const GridDesc *__restrict__ grids, in
 
 // Flow kernel for any mix of walks (out of line, as in k_batch).
 __global__ void __launch_bounds__(32 * kBatchWarps, 3)
-    k_flow(const GridDesc *__restrict__ grids, int ngrids, const int *__restrict__ gidx,
-           const Tile *__restrict__ tiles,
+    k_flow(const GridDesc *__restrict__ grids, int ngrids, const Tile *__restrict__ tiles,
            const long long *__restrict__ limit, const int *__restrict__ parity0,
            const uint32_t *__restrict__ t0, unsigned long long *ctl, int *prog, unsigned *glob,
            const int *__restrict__ nwork_p, int *status, unsigned long long timeout_ns) {
-    flow_loop(grids, ngrids, gidx, tiles, limit, parity0, t0, ctl, prog, glob, nwork_p, status,
+    flow_loop(grids, ngrids, tiles, limit, parity0, t0, ctl, prog, glob, nwork_p, status,
               timeout_ns, [](const GridDesc &g, int par, const Tile &t, uint32_t step) {
                   any_tile(g, par, t, step);
               });
@@ -411,15 +409,14 @@ __global__ void __launch_bounds__(32 * kBatchWarps, 3)
 // without spills although the flow loop's state costs a few bytes of spill).
 template <int S, int V, int PD, int RND, int VA = 0>
 __global__ void __launch_bounds__(32 * kBatchWarps, PD == 2 ? 3 : 4)
-    k_flow_one(const GridDesc *__restrict__ grids, int ngrids, const int *__restrict__ gidx,
-               const Tile *__restrict__ tiles,
+    k_flow_one(const GridDesc *__restrict__ grids, int ngrids, const Tile *__restrict__ tiles,
                const long long *__restrict__ limit, const int *__restrict__ parity0,
                const uint32_t *__restrict__ t0, unsigned long long *ctl, int *prog,
                unsigned *glob, const int *__restrict__ nwork_p, int *status,
                unsigned long long timeout_ns) {
     __shared__ uint4 rowbuf[(S != ST_F32 && V == 8) ? kBatchWarps : 1][2 * 9 * 32];
     (void)rowbuf;
-    flow_loop(grids, ngrids, gidx, tiles, limit, parity0, t0, ctl, prog, glob, nwork_p, status,
+    flow_loop(grids, ngrids, tiles, limit, parity0, t0, ctl, prog, glob, nwork_p, status,
               timeout_ns, [&](const GridDesc &g, int par, const Tile &t, uint32_t step) {
                   Walker<S, V, LD_CG, RND, VA> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P,
                                                  t.x0);
@@ -437,13 +434,39 @@ __global__ void __launch_bounds__(32 * kBatchWarps, PD == 2 ? 3 : 4)
               });
 }
 
-using FlowKernel = void (*)(const GridDesc *, int, const int *, const Tile *, const long long *,
-                            const int *, const uint32_t *, unsigned long long *, int *,
-                            unsigned *, const int *, int *, unsigned long long);
+// Flow kernel for the serving mix: FP32 grids (4 sites per lane) and 16-bit
+// grids of storage S2 and rounding RND2 (8 sites per lane), both walks
+// inlined; 12 warps per SM (at 16 both walks together spill heavily).
+template <int S2, int RND2>
+__global__ void __launch_bounds__(32 * kBatchWarps, 3)
+    k_flow_two(const GridDesc *__restrict__ grids, int ngrids, const Tile *__restrict__ tiles,
+               const long long *__restrict__ limit, const int *__restrict__ parity0,
+               const uint32_t *__restrict__ t0, unsigned long long *ctl, int *prog,
+               unsigned *glob, const int *__restrict__ nwork_p, int *status,
+               unsigned long long timeout_ns) {
+    __shared__ uint4 rowbuf[kBatchWarps][2 * 9 * 32];
+    flow_loop(grids, ngrids, tiles, limit, parity0, t0, ctl, prog, glob, nwork_p, status,
+              timeout_ns, [&](const GridDesc &g, int par, const Tile &t, uint32_t step) {
+                  const Coef c = g.c;
+                  if (g.kind == kind_code(ST_F32, 4, 0)) {
+                      Walker<ST_F32, 4, LD_CG> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P,
+                                                 t.x0);
+                      w.run(t.y0, t.y1, t.dir, c);
+                  } else {
+                      Walker<S2, 8, LD_CG, RND2> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P,
+                                                   t.x0);
+                      if constexpr (RND2) w.set_step(step);
+                      w.run_async(t.y0, t.y1, t.dir, c, &rowbuf[threadIdx.x >> 5][0]);
+                  }
+              });
+}
 
-// The flow kernel for a set of kinds: specialised when they are one walk,
-// else the general k_flow.  (A batch of several walks runs one flow launch
-// per walk side by side.)
+using FlowKernel = void (*)(const GridDesc *, int, const Tile *, const long long *, const int *,
+                            const uint32_t *, unsigned long long *, int *, unsigned *,
+                            const int *, int *, unsigned long long);
+
+// The flow kernel for a batch's kinds: specialised when all grids share one
+// walk, else the general k_flow.
 FlowKernel flow_kernel_for(const std::vector<int> &kinds, int walk16) {
     bool same = true;
     for (int k : kinds) same = same && k == kinds[0];
@@ -466,6 +489,28 @@ FlowKernel flow_kernel_for(const std::vector<int> &kinds, int walk16) {
                 return two ? k_flow_one<ST_BF16, 4, 2, 0> : k_flow_one<ST_BF16, 4, 1, 0>;
             case kind_code(ST_F32, 4, 0, 1):
                 return k_flow_one<ST_F32, 4, 0, 0, 1>;
+            default:
+                break;
+        }
+    }
+    // FP32 (4 sites per lane) with one 16-bit kind of 8 sites per lane.
+    int other = -1;
+    bool pair = !kinds.empty();
+    for (int k : kinds) {
+        if (k == kind_code(ST_F32, 4, 0)) continue;
+        if (other == -1) other = k;
+        pair = pair && k == other;
+    }
+    if (pair && other != -1) {
+        switch (other) {
+            case kind_code(ST_F16, 8, 0):
+                return k_flow_two<ST_F16, 0>;
+            case kind_code(ST_BF16, 8, 0):
+                return k_flow_two<ST_BF16, 0>;
+            case kind_code(ST_F16, 8, 1):
+                return k_flow_two<ST_F16, 1>;
+            case kind_code(ST_BF16, 8, 1):
+                return k_flow_two<ST_BF16, 1>;
             default:
                 break;
         }
