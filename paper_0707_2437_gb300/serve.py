@@ -15,12 +15,13 @@ memory frees up, and their work overlaps on the device.
 ``serve_fifo`` is the plain baseline: one grid at a time, in arrival order,
 with the single-grid FP32 kernel.
 
-Two schedules (``Server(schedule=...)``).  ``lockstep``: each launch advances
+Schedules (``Server(schedule=...)``).  ``lockstep``: each launch advances
 every resident grid by up to `quantum` steps together, a barrier across the
 batch between steps, so a small grid waits as many batch-wide steps as a large
 one.  ``flow``: each launch shares a budget of lattice updates equally between
 the grids (a small grid gets many steps, a large one few) and runs them with
-the batch's flow schedule, where each grid advances on its own.
+the batch's flow schedule, where each grid advances on its own.  ``auto``:
+flow while at most `auto_grids` grids are resident, lockstep above.
 
 Two policies (``Server(policy=...)``) pick the grids that step in a launch:
 ``fair`` steps every resident grid; ``srpt`` steps the grids with the least
@@ -104,16 +105,18 @@ class Server:
                  max_slots: int = 512, keep_fields: bool = False, stream=None,
                  overlap: bool = True, schedule: str = "lockstep",
                  flow_updates: float = 1e9, flow_max_steps: int = 1024,
-                 flow_weight: float = 0.5, policy: str = "fair", srpt_sites: float = 4e6):
+                 flow_weight: float = 0.5, policy: str = "fair", srpt_sites: float = 4e6,
+                 auto_grids: int = 24):
         self.quantum = quantum
         self.reserve = reserve_bytes
         self.max_slots = max_slots
         self.keep_fields = keep_fields
         self.stream = stream
         self.overlap = overlap
-        if schedule not in ("lockstep", "flow"):
+        if schedule not in ("lockstep", "flow", "auto"):
             raise ValueError(f"unknown schedule {schedule!r}")
         self.schedule = schedule
+        self.auto_grids = auto_grids
         self.flow_updates = flow_updates
         self.flow_max_steps = flow_max_steps
         self.flow_weight = flow_weight
@@ -142,7 +145,15 @@ class Server:
                 break
         return sel
 
-    def _limits(self, active):
+    def _schedule_for(self, active) -> str:
+        """'auto': the flow schedule while at most `auto_grids` grids are
+        resident (each grid's time-to-result then follows its own size), the
+        lockstep schedule above (a backlog: throughput sets the latencies)."""
+        if self.schedule != "auto":
+            return self.schedule
+        return "flow" if len(active) <= self.auto_grids else "lockstep"
+
+    def _limits(self, active, schedule=None):
         """Steps each resident grid takes in the next launch.  Lockstep:
         every grid up to `quantum` steps (all advance together).  Flow: the
         launch's budget of `flow_updates` lattice updates is shared between
@@ -153,7 +164,7 @@ class Server:
         them without a barrier across grids."""
         sel = self._selected(active)
         run = [a for a, s_ in zip(active, sel) if s_]
-        if self.schedule == "lockstep":
+        if (schedule or self._schedule_for(active)) == "lockstep":
             q = min(self.quantum, max(a[2] for a in run))
             return q, [min(q, a[2]) if s_ else 0 for a, s_ in zip(active, sel)]
         wts = [(a[0].nx * a[0].ny) ** self.flow_weight for a in run]
@@ -181,6 +192,7 @@ class Server:
         stats = ServeStats()
         ph = stats.phase_s
         batch = None
+        batch_sched = "lockstep"
         members = None
         main = self.stream
         if self.overlap and main is None:
@@ -225,15 +237,18 @@ class Server:
             limits = None
             if active:
                 tb = time.perf_counter()
+                sched = self._schedule_for(active)
                 if batch is None or members != [id(a[1]) for a in active]:
                     if batch is not None:
                         batch.close()
                     batch = lbm.Batch([a[1] for a in active])
-                    if self.schedule == "flow":
-                        batch.set_schedule("flow")
+                    batch_sched = "lockstep"
                     members = [id(a[1]) for a in active]
+                if sched != batch_sched:
+                    batch.set_schedule(sched)
+                    batch_sched = sched
                 stats.max_active = max(stats.max_active, len(active))
-                q, limits = self._limits(active)
+                q, limits = self._limits(active, sched)
                 batch.step(q, limits)
                 ph["batch"] += time.perf_counter() - tb
             if self.overlap:

@@ -221,6 +221,21 @@ def test_flow_schedule_shares_updates_equally(monkeypatch):
     assert by_size[0][1] >= by_size[-1][1]
 
 
+def test_auto_schedule_switches_with_the_resident_count(monkeypatch):
+    """'auto' steps in the flow schedule while few grids are resident and in
+    lockstep once more than auto_grids are; requests still run their steps."""
+    dev = _FakeDevice(total=1 << 40)
+    monkeypatch.setattr(serve, "lbm", _fake_lbm(dev))
+    reqs = _requests(n=16)
+    stats = serve.Server(reserve_bytes=0, schedule="auto", auto_grids=6).run(reqs, realtime=False)
+    assert len(stats.results) == len(reqs) and dev.live == 0
+    for q, g in zip(reqs, dev.created):
+        assert g.steps_at_close == q.steps
+    scheds = {(sch, len(calls) > 6) for sch, calls in dev.steps}
+    assert ("lockstep", True) in scheds and ("flow", False) in scheds
+    assert ("flow", True) not in scheds and ("lockstep", False) not in scheds
+
+
 def test_unknown_schedule_is_refused():
     with pytest.raises(ValueError):
         serve.Server(schedule="eager")
