@@ -165,6 +165,7 @@ def serve_comparison(args, stream=None):
     warm = serve.scaled_trace(8, 1000.0, seed=99, hi=256, steps_hi=2000)
     server().run(warm, realtime=False)
     server("flow").run(warm, realtime=False)
+    # The reference server steps every resident grid in lockstep.
     srv = server().run(trace, realtime=True).summary()
     out = {"trace": f"{args.serve_count} requests, Poisson {args.serve_rate}/s, sites "
                     f"log-uniform 128^2..2048^2, steps U{{1000..{args.serve_steps_hi}}}, "
@@ -190,10 +191,13 @@ def serve_comparison(args, stream=None):
             trace07, realtime=True).summary()
     if not args.serve_no_flow:
         # The same two traces with the flow schedule (each grid advances on
-        # its own; launches share a budget of lattice updates equally).
-        out["continuous_batching_flow"] = server("flow").run(trace, realtime=True).summary()
-        out["at_0.7_capacity"]["continuous_batching_flow"] = server("flow").run(
-            trace07, realtime=True).summary()
+        # its own; launches share a budget of lattice updates by size^0.5),
+        # and with the server's default: flow while at most 24 grids are
+        # resident, lockstep above.
+        for name, sched in (("continuous_batching_flow", "flow"),
+                            ("continuous_batching_auto", "auto")):
+            out[name] = server(sched).run(trace, realtime=True).summary()
+            out["at_0.7_capacity"][name] = server(sched).run(trace07, realtime=True).summary()
         out["flow_updates_per_launch"] = args.serve_flow_updates
     if not (args.serve_no_fifo07 or args.serve_skip_fifo):
         fifo07 = serve.serve_fifo(trace07, realtime=True).summary()
@@ -956,6 +960,7 @@ def run_serve_workload(args):
                    "quantum_steps": args.serve_quantum},
         "served": srv, "fifo_f32": fifo, "at_0.7_capacity": cmp_["at_0.7_capacity"],
         "served_flow": cmp_.get("continuous_batching_flow"),
+        "served_auto": cmp_.get("continuous_batching_auto"),
         "served_srpt": cmp_.get("continuous_batching_srpt"),
         "clocks": clk,
     }

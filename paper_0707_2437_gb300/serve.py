@@ -103,7 +103,7 @@ class Server:
 
     def __init__(self, quantum: int = 256, reserve_bytes: int = 4 << 30,
                  max_slots: int = 512, keep_fields: bool = False, stream=None,
-                 overlap: bool = True, schedule: str = "lockstep",
+                 overlap: bool = True, schedule: str = "auto",
                  flow_updates: float = 1e9, flow_max_steps: int = 1024,
                  flow_weight: float = 0.5, policy: str = "fair", srpt_sites: float = 4e6,
                  auto_grids: int = 24):

@@ -25,12 +25,13 @@ def _trace():
                                                      (False, "lockstep", "fair"),
                                                      (True, "lockstep", "srpt"),
                                                      (True, "flow", "fair"),
-                                                     (True, "flow", "srpt")])
+                                                     (True, "flow", "srpt"),
+                                                     (True, "auto", "fair")])
 def test_served_results_equal_solo_runs(lbm, overlap, schedule, policy):
     reqs = _trace()
     srv = serve.Server(quantum=48, max_slots=3, keep_fields=True, reserve_bytes=0,
                        overlap=overlap, schedule=schedule, policy=policy,
-                       flow_updates=2e5, flow_max_steps=64, srpt_sites=8000)
+                       flow_updates=2e5, flow_max_steps=64, srpt_sites=8000, auto_grids=2)
     stats = srv.run(reqs, realtime=False)
     assert len(stats.results) == len(reqs)
     assert stats.max_active == 3

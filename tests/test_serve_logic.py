@@ -116,7 +116,7 @@ def test_every_request_runs_exactly_its_steps(monkeypatch):
     dev = _FakeDevice(total=1 << 40)
     monkeypatch.setattr(serve, "lbm", _fake_lbm(dev))
     reqs = _requests()
-    stats = serve.Server(quantum=256, reserve_bytes=0).run(reqs, realtime=False)
+    stats = serve.Server(quantum=256, reserve_bytes=0, schedule="lockstep").run(reqs, realtime=False)
     assert sorted(r.rid for r in stats.results) == [q.rid for q in reqs]
     by_rid = {g_rid: g for g_rid, g in zip([q.rid for q in reqs], dev.created)}
     for q in reqs:
@@ -133,7 +133,8 @@ def test_admission_is_bounded_by_free_memory(monkeypatch):
     reserve = 1000
     dev = _FakeDevice(total=reserve + 2 * need + need // 2)  # room for two at a time
     monkeypatch.setattr(serve, "lbm", _fake_lbm(dev))
-    stats = serve.Server(quantum=128, reserve_bytes=reserve).run(reqs, realtime=False)
+    stats = serve.Server(quantum=128, reserve_bytes=reserve, schedule="lockstep").run(
+        reqs, realtime=False)
     assert len(stats.results) == len(reqs)
     assert dev.max_live >= 2 and stats.max_active == dev.max_live
     assert dev.max_used <= dev.total - reserve   # the reserve is never touched
@@ -145,7 +146,8 @@ def test_slot_limit_and_arrival_order(monkeypatch):
     dev = _FakeDevice(total=1 << 40)
     monkeypatch.setattr(serve, "lbm", _fake_lbm(dev))
     reqs = _requests(n=10)
-    stats = serve.Server(quantum=64, reserve_bytes=0, max_slots=3).run(reqs, realtime=False)
+    stats = serve.Server(quantum=64, reserve_bytes=0, max_slots=3, schedule="lockstep").run(
+        reqs, realtime=False)
     assert stats.max_active == 3 and dev.max_live == 3
     admitted = sorted(stats.results, key=lambda r: (r.admitted_s, r.rid))
     assert [r.rid for r in admitted] == sorted(r.rid for r in stats.results)
@@ -157,7 +159,7 @@ def test_request_larger_than_the_device_is_refused(monkeypatch):
     dev = _FakeDevice(total=10)
     monkeypatch.setattr(serve, "lbm", _fake_lbm(dev))
     with pytest.raises(MemoryError):
-        serve.Server(quantum=64, reserve_bytes=0).run(reqs, realtime=False)
+        serve.Server(quantum=64, reserve_bytes=0, schedule="lockstep").run(reqs, realtime=False)
 
 
 def test_summary_percentiles():
@@ -181,7 +183,8 @@ def test_admission_overlaps_the_running_quantum(monkeypatch, overlap):
     dev = _FakeDevice(total=1 << 40)
     monkeypatch.setattr(serve, "lbm", _fake_lbm(dev))
     reqs = _requests(n=12)
-    srv = serve.Server(quantum=64, reserve_bytes=0, max_slots=4, overlap=overlap)
+    srv = serve.Server(quantum=64, reserve_bytes=0, max_slots=4, overlap=overlap,
+                       schedule="lockstep")
     stats = srv.run(reqs, realtime=False)
     assert len(stats.results) == len(reqs) and dev.live == 0
     made = [g.made_in_flight for g in dev.created]
@@ -249,7 +252,8 @@ def test_srpt_policy_steps_the_least_remaining_work_first(monkeypatch):
     monkeypatch.setattr(serve, "lbm", _fake_lbm(dev))
     reqs = _requests(n=16)
     thresh = 3 * 128 * 128
-    srv = serve.Server(quantum=128, reserve_bytes=0, policy="srpt", srpt_sites=thresh)
+    srv = serve.Server(quantum=128, reserve_bytes=0, policy="srpt", srpt_sites=thresh,
+                       schedule="lockstep")
     stats = srv.run(reqs, realtime=False)
     assert len(stats.results) == len(reqs) and dev.live == 0
     for q, g in zip(reqs, dev.created):
