@@ -189,15 +189,16 @@ def serve_comparison(args, stream=None):
         out["continuous_batching_srpt"] = server(policy="srpt").run(trace, realtime=True).summary()
         out["at_0.7_capacity"]["continuous_batching_srpt"] = server(policy="srpt").run(
             trace07, realtime=True).summary()
-    if not args.serve_no_flow:
-        # The same two traces with the flow schedule (each grid advances on
-        # its own; launches share a budget of lattice updates by size^0.5),
-        # and with the server's default: flow while at most 24 grids are
-        # resident, lockstep above.
-        for name, sched in (("continuous_batching_flow", "flow"),
-                            ("continuous_batching_auto", "auto")):
-            out[name] = server(sched).run(trace, realtime=True).summary()
-            out["at_0.7_capacity"][name] = server(sched).run(trace07, realtime=True).summary()
+    # The same two traces with the flow schedule (each grid advances on its
+    # own; launches share a budget of lattice updates by size^0.5), and with
+    # the server's default: flow while at most 24 grids are resident,
+    # lockstep above.
+    for sched in ("flow", "auto"):
+        if sched not in args.serve_schedules.split(","):
+            continue
+        name = f"continuous_batching_{sched}"
+        out[name] = server(sched).run(trace, realtime=True).summary()
+        out["at_0.7_capacity"][name] = server(sched).run(trace07, realtime=True).summary()
         out["flow_updates_per_launch"] = args.serve_flow_updates
     if not (args.serve_no_fifo07 or args.serve_skip_fifo):
         fifo07 = serve.serve_fifo(trace07, realtime=True).summary()
@@ -1002,8 +1003,9 @@ def main():
                     help="batch schedule on the batch paths (flow: no barrier across grids)")
     ap.add_argument("--serve-srpt", action="store_true",
                     help="also run the least-remaining-work-first server in the serving comparison")
-    ap.add_argument("--serve-no-flow", action="store_true",
-                    help="skip the flow-schedule server in the serving comparison")
+    ap.add_argument("--serve-schedules", default="flow,auto",
+                    help="server schedules run beside lockstep in the serving comparison "
+                         "(comma-separated: flow, auto; empty for none)")
     ap.add_argument("--serve-flow-updates", type=float, default=1e9,
                     help="lattice updates per launch shared by the flow-schedule server")
     ap.add_argument("--serve-no-overlap", action="store_true",
