@@ -311,6 +311,14 @@ int lbm_batch_tune(lbm_batch_t b);
  * whether every kind group runs a specialised kernel rather than the general
  * one. */
 int lbm_batch_get_config(lbm_batch_t b, int *rows, int *blocks_per_sm, int *specialised);
+/* The work-list as last built (at creation, by a configuration, schedule or
+ * walk change, or by a step call that found a grid's field or rounding
+ * changed): *tiles = warp walks per time step, *paired = how many of them
+ * walk two segments of a narrow grid, a half-warp each (lockstep kind groups
+ * of one 8-site 16-bit kind under LBM_WALK16_AUTO pair the tiles of grids at
+ * most 128 columns wide when those are at least a fifth of the group's tiles;
+ * results are bitwise those of single walks).  Either pointer may be NULL. */
+int lbm_batch_get_tiles(lbm_batch_t b, int *tiles, int *paired);
 
 /* Number of persistent launches one lbm_batch_step makes (kind groups).  The
  * grids of one walk (storage kind, sites per lane, rounding; nx a multiple of

@@ -83,6 +83,8 @@ struct lbm_batch {
     size_t prog_cap = 0;
     int *d_nwork = nullptr;
     int *h_nwork = nullptr;
+    // Paired tiles (split walk) in the lockstep work-list.
+    int paired = 0;
 };
 
 static int bfail(int code, const std::string &m) {
@@ -144,6 +146,7 @@ static int upload_worklist(lbm_batch *b, const std::vector<GridDesc> &gd,
 static int build_worklist(lbm_batch *b) {
     std::vector<GridDesc> gd(b->grids.size());
     std::vector<Tile> tiles;
+    b->paired = 0;
     // Flow schedule: the kernel for the grids' kinds and the warps it keeps
     // resident, which set each grid's tile height below.
     FlowKernel fk = nullptr;
@@ -254,16 +257,54 @@ static int build_worklist(lbm_batch *b) {
     std::vector<Tile> ordered;
     ordered.reserve(tiles.size());
     b->groups.clear();
+    // A group of one 8-site 16-bit kind (automatic walk) pairs the tiles of
+    // its grids at most kSplitCols wide: consecutive segments share one warp,
+    // a half-warp each (the split walk), where a single walk leaves half of
+    // the lanes or more idle.  An odd one out stays single.  The kernel
+    // instance with the split walk runs the whole-warp walk a few per cent
+    // slower (its register allocation), and pairing the narrow last strip of
+    // a wider grid measured no faster, so a group pairs only whole narrow
+    // grids, and only when their tiles are at least kSplitMinShare of its
+    // tiles.
     auto add_group = [&](const std::vector<int> &kinds_in) -> int {
         lbm_batch::Group gr;
         gr.begin = (int)ordered.size();
+        auto in_group = [&](const Tile &t) {
+            return std::find(kinds_in.begin(), kinds_in.end(), gd[t.grid].kind) != kinds_in.end();
+        };
+        auto narrow = [&](const Tile &t) { return gd[t.grid].nx <= kSplitCols; };
+        bool split = kinds_in.size() == 1 && kind_splits(kinds_in[0]) &&
+                     b->walk16 == LBM_WALK16_AUTO;
+        if (split) {
+            long long n_all = 0, n_narrow = 0;
+            for (const Tile &t : tiles)
+                if (in_group(t)) {
+                    ++n_all;
+                    n_narrow += narrow(t);
+                }
+            split = n_narrow > 0 && (double)n_narrow >= kSplitMinShare * (double)n_all;
+        }
+        const int paired0 = b->paired;
+        std::vector<int> pending(b->grids.size(), -1);
         for (const Tile &t : tiles) {
-            int kd = gd[t.grid].kind;
-            if (std::find(kinds_in.begin(), kinds_in.end(), kd) != kinds_in.end())
-                ordered.push_back(t);
+            if (!in_group(t)) continue;
+            if (split && narrow(t)) {
+                int &p = pending[t.grid];
+                if (p >= 0) {
+                    Tile &a = ordered[p];
+                    a.y0b = t.y0;
+                    a.y1b = t.y1;
+                    a.dirb = t.dir;
+                    p = -1;
+                    ++b->paired;
+                    continue;
+                }
+                p = (int)ordered.size();
+            }
+            ordered.push_back(t);
         }
         gr.count = (int)ordered.size() - gr.begin;
-        gr.kernel = kernel_for(kinds_in, b->walk16);
+        gr.kernel = kernel_for(kinds_in, b->walk16, b->paired > paired0);
         BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gr.max_blocks_per_sm,
                                                           (const void *)gr.kernel,
                                                           32 * kBatchWarps, 0));
@@ -671,6 +712,13 @@ extern "C" int lbm_batch_get_launch(lbm_batch_t b, int *mode, int *last, int *ca
     if (mode) *mode = b->launch_mode;
     if (last) *last = b->last_launch;
     if (capture_failed) *capture_failed = b->capture_failed ? 1 : 0;
+    return LBM_OK;
+}
+
+extern "C" int lbm_batch_get_tiles(lbm_batch_t b, int *tiles, int *paired) {
+    if (!b) return bfail(LBM_EINVAL, "lbm_batch_get_tiles: NULL batch");
+    if (tiles) *tiles = b->ntiles;
+    if (paired) *paired = b->paired;
     return LBM_OK;
 }
 

@@ -40,8 +40,14 @@ struct GridDesc {
     int tile0, ntile, nstrips, nsegs, dseg, dstrip;
 };
 
-struct Tile {
+// A tile: one strip (x0) of one segment (rows y0 .. y1-1, walked in
+// direction dir) of a grid.  A paired tile (y1b > y0b; lockstep kernels of
+// 8-site 16-bit walks only) adds a second segment, rows y0b .. y1b-1 in
+// direction dirb, of a grid at most 16*8 columns wide: the two halves of the
+// warp walk one segment each (the split walk).
+struct __align__(16) Tile {
     int grid, x0, y0, y1, dir;
+    int y0b, y1b, dirb;
 };
 
 // A grid's walk in the batch kernels: storage kind, sites per lane (1, 4 or
@@ -518,12 +524,37 @@ FlowKernel flow_kernel_for(const std::vector<int> &kinds, int walk16) {
     return k_flow;
 }
 
+// Walks whose lockstep kernel takes paired tiles (the split walk): 8-site
+// 16-bit walks without a c2 field.  kind_splits is the same test on a kind
+// code, for the work-list builder.
+template <int S, int V, int VA>
+constexpr bool kSplitWalk = S != ST_F32 && V == 8 && VA == 0;
+constexpr bool kind_splits(int kd) {
+    return kd == kind_code(ST_F16, 8, 0) || kd == kind_code(ST_BF16, 8, 0) ||
+           kd == kind_code(ST_F16, 8, 1) || kd == kind_code(ST_BF16, 8, 1);
+}
+constexpr int kSplitCols = 16 * 8;     // widest grid a half-warp walks
+constexpr double kSplitMinShare = 0.2;  // of a group's tiles, for the split kernel
+
+// A paired tile: each half-warp walks its own segment of the grid.  Inlined:
+// out of line, the call made both walks slower (measured).
+template <int S, int RND>
+__device__ __forceinline__ void split_tile(const GridDesc &g, int par, const Tile &t,
+                                           uint32_t step, uint4 *buf) {
+    Walker<S, 8, LD_CG, RND, 0, 16> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P, t.x0);
+    if constexpr (RND) w.set_step(step);
+    const bool hi = (threadIdx.x & 16) != 0;
+    const int K = max(t.y1 - t.y0, t.y1b - t.y0b) + 2;
+    const Coef c = g.c;
+    w.run_async_split(hi ? t.y0b : t.y0, hi ? t.y1b : t.y1, hi ? t.dirb : t.dir, K, c, buf);
+}
+
 // Specialised persistent kernel for a batch whose grids all use one walk
 // (storage, vec, rounding, rows of loads in flight PD = 0, 1 or 2): the walk is
 // inlined, so the kernel keeps the single-grid kernel's register budget (128,
 // 16 warps per SM; 170 and 12 warps per SM for the two-row prefetch) instead
 // of paying for calls.  Same time-step loop and bounded barrier as k_batch.
-template <int S, int V, int PD, int RND, int VA = 0>
+template <int S, int V, int PD, int RND, int VA = 0, bool SPLIT = false>
 __global__ void __launch_bounds__(32 * kBatchWarps, PD == 2 ? 3 : 4)
     k_batch_one(const GridDesc *__restrict__ grids, const Tile *__restrict__ tiles, int ntiles,
                 const long long *__restrict__ limit, const int *__restrict__ parity0,
@@ -543,6 +574,14 @@ __global__ void __launch_bounds__(32 * kBatchWarps, PD == 2 ? 3 : 4)
             // run-time parity would live in local memory.
             const GridDesc &g = grids[t.grid];
             const int par = (parity0[t.grid] + (int)(k & 1)) & 1;
+            if constexpr (SPLIT) {
+                static_assert(kSplitWalk<S, V, VA>, "paired tiles need the 8-site 16-bit walk");
+                if (t.y1b > t.y0b) {
+                    split_tile<S, RND>(g, par, t, t0[t.grid] + (uint32_t)k,
+                                       &rowbuf[threadIdx.x >> 5][0]);
+                    continue;
+                }
+            }
             const Coef c = g.c;
             Walker<S, V, LD_CG, RND, VA> w(g.buf[par], g.buf[par ^ 1], g.nx, g.ny, g.P, t.x0);
             if constexpr (VA) w.a15f = g.a15f;
@@ -567,7 +606,9 @@ using BatchKernel = void (*)(const GridDesc *, const Tile *, int, const long lon
 // The kernel for a set of kinds: a specialised one when every grid has the
 // same kind, else the general k_batch.  `walk16` picks the prefetch depth of
 // the 16-bit vec 4 walks (LBM_WALK16_V4: one row, LBM_WALK16_V4_PF2: two).
-BatchKernel kernel_for(const std::vector<int> &kinds, int walk16) {
+// `split`: the tiles include paired ones (8-site 16-bit kinds only), run by
+// the kernel instance that has the split walk.
+BatchKernel kernel_for(const std::vector<int> &kinds, int walk16, bool split = false) {
     bool same = true;
     for (int k : kinds) same = same && k == kinds[0];
     if (!kinds.empty() && same) {
@@ -576,13 +617,15 @@ BatchKernel kernel_for(const std::vector<int> &kinds, int walk16) {
             case kind_code(ST_F32, 4, 0):
                 return k_batch_one<ST_F32, 4, 0, 0>;
             case kind_code(ST_F16, 8, 0):
-                return k_batch_one<ST_F16, 8, 0, 0>;
+                return split ? k_batch_one<ST_F16, 8, 0, 0, 0, true> : k_batch_one<ST_F16, 8, 0, 0>;
             case kind_code(ST_BF16, 8, 0):
-                return k_batch_one<ST_BF16, 8, 0, 0>;
+                return split ? k_batch_one<ST_BF16, 8, 0, 0, 0, true>
+                             : k_batch_one<ST_BF16, 8, 0, 0>;
             case kind_code(ST_F16, 8, 1):
-                return k_batch_one<ST_F16, 8, 0, 1>;
+                return split ? k_batch_one<ST_F16, 8, 0, 1, 0, true> : k_batch_one<ST_F16, 8, 0, 1>;
             case kind_code(ST_BF16, 8, 1):
-                return k_batch_one<ST_BF16, 8, 0, 1>;
+                return split ? k_batch_one<ST_BF16, 8, 0, 1, 0, true>
+                             : k_batch_one<ST_BF16, 8, 0, 1>;
             case kind_code(ST_F16, 4, 0):
                 return two ? k_batch_one<ST_F16, 4, 2, 0> : k_batch_one<ST_F16, 4, 1, 0>;
             case kind_code(ST_BF16, 4, 0):

@@ -452,11 +452,16 @@ __device__ __forceinline__ void pair_out(float hi, float hopp, float ej, float e
 //                  (the left neighbour value lane 0 needs for its pull)
 //   lanes 16..24 : pulled f_i at the column after the strip, i = lane - 16
 //   lanes 25..27 : f_i at that column for the directions with e_x = -1
-template <int S, int V, int LD = LD_NC, int RND = 0, int VA = 0>
+// SEG = 32: the warp walks one strip of 32*V columns.  SEG = 16 (split walk):
+// each half-warp walks its own segment of a strip at most 16*V columns wide,
+// so that two narrow pieces of work fill one warp; every shuffle stays within
+// the half, and each lane serves one halo role on each side.
+template <int S, int V, int LD = LD_NC, int RND = 0, int VA = 0, int SEG = 32>
 struct Walker {
     static constexpr int NW = Pack<S, V>::NW;
     using T = typename StoreT<S>::T;
     static_assert(RND == 0 || S != ST_F32, "stochastic rounding applies to 16-bit storage");
+    static_assert(SEG == 32 || SEG == 16, "a strip is walked by a warp or a half-warp");
     uint32_t rkey = 0;  // sr_step_key of the step number (stochastic rounding)
     __device__ __forceinline__ void set_step(uint32_t step) { rkey = sr_step_key(step); }
     // Spatially varying sound speed (VA = 1): 1.5 alpha per site, [ny][nx].
@@ -466,10 +471,12 @@ struct Walker {
     T *__restrict__ fout;
     int nx, ny;
     size_t P;
-    int x0, wa, nact, lane, xs;
+    int x0, wa, nact, lane, sl, xs;
     bool act;
     // helper lane: direction, column offset from x0 (unwrapped), wrapped column
     int gdir, goff, gcol, gey;
+    // split walk: the lane's right-side role (direction, wrapped column, e_y)
+    int gdir2, gcol2, gey2;
 
     __device__ __forceinline__ Walker(const void *fin_, void *fout_, int nx_, int ny_, size_t P_,
                                       int x0_)
@@ -480,26 +487,41 @@ struct Walker {
           P(P_),
           x0(x0_) {
         lane = threadIdx.x & 31;
-        wa = min(32 * V, nx - x0);
+        sl = lane & (SEG - 1);
+        wa = min(SEG * V, nx - x0);
         nact = wa / V;
-        act = lane < nact;
-        xs = x0 + lane * V;
-        // Helper lane roles, read from packed per-lane tables without
-        // branches: direction (4 bits per lane) and kind (2 bits per lane).
-        //   kind 0: pulled f at the left halo site x0-1   (column x0-1-e_x)
-        //   kind 1: f at column x0-1 (left edge value; lanes without a
-        //           role also take kind 1, direction 0, and ignore it)
-        //   kind 2: pulled f at the right halo site x0+wa (column x0+wa-e_x)
-        //   kind 3: f at column x0+wa (right edge value)
-        const unsigned long long dir_tab = (lane < 16) ? 0x851876543210ULL : 0x763876543210ULL;
-        gdir = (int)((dir_tab >> (4 * (lane & 15))) & 15ULL);
-        const int kind = (int)((0x55feaaaa55540000ULL >> (2 * lane)) & 3ULL);
-        const int ex = (int)((0x20919u >> (2 * gdir)) & 3u) - 1;  // e_x of gdir
-        const int base = (kind < 2) ? -1 : wa;
-        goff = base - (((kind & 1) == 0) ? ex : 0);
-        gcol = ((x0 + goff) % nx + nx) % nx;
-        gey = (int)((0x2865u >> (2 * gdir)) & 3u) - 1;  // e_y of gdir
+        act = sl < nact;
+        xs = x0 + sl * V;
+        if constexpr (SEG == 32) {
+            helper_role(lane, gdir, goff, gcol, gey);
+        } else {
+            // Sub-lanes 0..11 of each half: the left roles of lanes 0..11 of a
+            // whole-warp strip, and the right roles of lanes 16..27.
+            int goff2;
+            helper_role(sl, gdir, goff, gcol, gey);
+            helper_role(sl + 16, gdir2, goff2, gcol2, gey2);
+        }
         __syncwarp();
+    }
+
+    // Helper roles of lane `r` of a whole-warp strip, read from packed per-lane
+    // tables without branches: direction (4 bits per lane) and kind (2 bits
+    // per lane).
+    //   kind 0: pulled f at the left halo site x0-1   (column x0-1-e_x)
+    //   kind 1: f at column x0-1 (left edge value; lanes without a
+    //           role also take kind 1, direction 0, and ignore it)
+    //   kind 2: pulled f at the right halo site x0+wa (column x0+wa-e_x)
+    //   kind 3: f at column x0+wa (right edge value)
+    __device__ __forceinline__ void helper_role(int r, int &dir, int &off, int &col,
+                                                int &ey) const {
+        const unsigned long long dir_tab = (r < 16) ? 0x851876543210ULL : 0x763876543210ULL;
+        dir = (int)((dir_tab >> (4 * (r & 15))) & 15ULL);
+        const int kind = (int)((0x55feaaaa55540000ULL >> (2 * r)) & 3ULL);
+        const int ex = (int)((0x20919u >> (2 * dir)) & 3u) - 1;  // e_x of dir
+        const int base = (kind < 2) ? -1 : wa;
+        off = base - (((kind & 1) == 0) ? ex : 0);
+        col = ((x0 + off) % nx + nx) % nx;
+        ey = (int)((0x2865u >> (2 * dir)) & 3u) - 1;  // e_y of dir
     }
 
     // Pulls row q (source rows qm = q-1, q0 = q, qp = q+1, already wrapped):
@@ -588,19 +610,23 @@ struct Walker {
     }
 
     // Shifts of the e_x = +-1 directions, drho of the lane's sites, and drho
-    // of the two halo sites, from the raw rows `w` and the helper value `g`.
+    // of the two halo sites, from the raw rows `w` and the helper value `g`
+    // (split walk: `g` of the lane's left role, `g2` of its right role).
     __device__ __forceinline__ void finish_pull(uint32_t (&w)[9][NW], uint32_t g, float (&d)[V],
-                                                float &dl, float &dr) const {
+                                                float &dl, float &dr, uint32_t g2 = 0u) const {
+        // The right edge values: lanes 25..27 of the warp, or 9..11 of a half.
+        const uint32_t gr = (SEG == 32) ? g : g2;
+        constexpr int RE = (SEG == 32) ? 25 : 9;
         // e_x = +1 directions take the left neighbour's last element.
         {
-            uint32_t e1 = __shfl_sync(FULL, g, 9);
-            uint32_t e5 = __shfl_sync(FULL, g, 10);
-            uint32_t e8 = __shfl_sync(FULL, g, 11);
+            uint32_t e1 = __shfl_sync(FULL, g, 9, SEG);
+            uint32_t e5 = __shfl_sync(FULL, g, 10, SEG);
+            uint32_t e8 = __shfl_sync(FULL, g, 11, SEG);
             constexpr bool HI = (S != ST_F32 && V > 1);  // incoming element in the high half
-            uint32_t p1 = __shfl_up_sync(FULL, w[1][NW - 1], 1);
-            uint32_t p5 = __shfl_up_sync(FULL, w[5][NW - 1], 1);
-            uint32_t p8 = __shfl_up_sync(FULL, w[8][NW - 1], 1);
-            if (lane == 0) {
+            uint32_t p1 = __shfl_up_sync(FULL, w[1][NW - 1], 1, SEG);
+            uint32_t p5 = __shfl_up_sync(FULL, w[5][NW - 1], 1, SEG);
+            uint32_t p8 = __shfl_up_sync(FULL, w[8][NW - 1], 1, SEG);
+            if (sl == 0) {
                 p1 = HI ? (e1 << 16) : e1;
                 p5 = HI ? (e5 << 16) : e5;
                 p8 = HI ? (e8 << 16) : e8;
@@ -611,13 +637,13 @@ struct Walker {
         }
         // e_x = -1 directions take the right neighbour's first element.
         {
-            uint32_t e3 = __shfl_sync(FULL, g, 25);
-            uint32_t e6 = __shfl_sync(FULL, g, 26);
-            uint32_t e7 = __shfl_sync(FULL, g, 27);
-            uint32_t n3 = __shfl_down_sync(FULL, w[3][0], 1);
-            uint32_t n6 = __shfl_down_sync(FULL, w[6][0], 1);
-            uint32_t n7 = __shfl_down_sync(FULL, w[7][0], 1);
-            if (lane == nact - 1) {
+            uint32_t e3 = __shfl_sync(FULL, gr, RE, SEG);
+            uint32_t e6 = __shfl_sync(FULL, gr, RE + 1, SEG);
+            uint32_t e7 = __shfl_sync(FULL, gr, RE + 2, SEG);
+            uint32_t n3 = __shfl_down_sync(FULL, w[3][0], 1, SEG);
+            uint32_t n6 = __shfl_down_sync(FULL, w[6][0], 1, SEG);
+            uint32_t n7 = __shfl_down_sync(FULL, w[7][0], 1, SEG);
+            if (sl == nact - 1) {
                 n3 = e3;
                 n6 = e6;
                 n7 = e7;
@@ -641,8 +667,12 @@ struct Walker {
         // same order: lanes 1, 3, 5, 7 add their right neighbour (h1+h2,
         // h3+h4, h5+h6, h7+h8), lanes 1 and 5 then add the pair two lanes on
         // ((h1+h2)+(h3+h4), (h5+h6)+(h7+h8)), and lane 0 (16) combines them
-        // with h0 as delta_rho does.
-        {
+        // with h0 as delta_rho does.  Split walk: the same sums within each
+        // half, once over the left roles and once over the right ones.
+        if constexpr (SEG == 16) {
+            dl = halo_drho16(g);
+            dr = halo_drho16(g2);
+        } else {
             const float v = elem_to_f<S>(g);
             const float t = __fadd_rn(v, __shfl_down_sync(FULL, v, 1));
             const float u = __fadd_rn(t, __shfl_down_sync(FULL, t, 2));
@@ -654,20 +684,34 @@ struct Walker {
             dr = __shfl_sync(FULL, dh, 16);
         }
     }
+    __device__ __forceinline__ static float halo_drho16(uint32_t g) {
+        const float v = elem_to_f<S>(g);
+        const float t = __fadd_rn(v, __shfl_down_sync(FULL, v, 1, 16));
+        const float u = __fadd_rn(t, __shfl_down_sync(FULL, t, 2, 16));
+        const float sa = __shfl_sync(FULL, u, 1, 16);
+        const float sd = __shfl_sync(FULL, u, 5, 16);
+        const float dh = __fmaf_rn(VSS_W0, v, __fmaf_rn(VSS_W1, sa, __fmul_rn(VSS_W5, sd)));
+        return __shfl_sync(FULL, dh, 0, 16);
+    }
 
     // Collides row r and stores it.  w: the row's packed pulled values (the
     // outputs are written back into it, site by site, and then stored); d:
     // drho of the row; dym / dyp: drho of rows r-1 / r+1; dl / dr: drho of
-    // the halo sites left and right of the strip.
+    // the halo sites left and right of the strip; keep = false computes the
+    // row without storing it (the shorter half of a split walk); swap_y
+    // exchanges dym and dyp (the halves of a split walk walk in opposite
+    // directions: selecting the rows per lane keeps the warp on one path,
+    // where a branch would run the halves one after the other).
     __device__ __forceinline__ void collide_store(int r, uint32_t (&w)[9][NW], const float (&d)[V],
                                                   const float (&dym)[V], const float (&dyp)[V],
-                                                  float dl, float dr, const Coef &c) const {
+                                                  float dl, float dr, const Coef &c,
+                                                  bool keep = true, bool swap_y = false) const {
         // x neighbours of drho: inside the lane, then the adjacent lanes, then
         // the halo sites at the strip edges.
-        float lft = __shfl_up_sync(FULL, d[V - 1], 1);
-        float rgt = __shfl_down_sync(FULL, d[0], 1);
-        if (lane == 0) lft = dl;
-        if (lane == nact - 1) rgt = dr;
+        float lft = __shfl_up_sync(FULL, d[V - 1], 1, SEG);
+        float rgt = __shfl_down_sync(FULL, d[0], 1, SEG);
+        if (sl == 0) lft = dl;
+        if (sl == nact - 1) rgt = dr;
         // 1.5 alpha of the lane's sites: the grid's constant, or the field.
         float a15v[V];
         if constexpr (VA) {
@@ -697,7 +741,9 @@ struct Walker {
                 const float dxp = (v == V - 1) ? rgt : d[v + 1];
                 float *hs = h[s];
                 const SiteQ q = site_quantities(hs[1], hs[2], hs[3], hs[4], hs[5], hs[6], hs[7],
-                                                hs[8], d[v], dxm, dxp, dym[v], dyp[v], c,
+                                                hs[8], d[v], dxm, dxp,
+                                                swap_y ? dyp[v] : dym[v],
+                                                swap_y ? dym[v] : dyp[v], c,
                                                 a15v[v]);
                 float o[9];
                 o[0] = __fmaf_rn(c.om1, hs[0], q.wB);                           // rest
@@ -712,7 +758,7 @@ struct Walker {
             }
             pack_sites(w, v0, h, r);
         }
-        if (!act) return;
+        if (!act || !keep) return;
         const size_t row = (size_t)r * nx + xs;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -786,6 +832,12 @@ struct Walker {
         const size_t gidx = (size_t)gdir * P + (size_t)gsr * nx + gcol;
         return load_elem<S, LD>(fin + gidx);
     }
+    // Split walk: the value of the lane's right-side role.
+    __device__ __forceinline__ uint32_t load_helper2(int qm, int q0, int qp) const {
+        const int gsr = (gey2 > 0) ? qm : ((gey2 < 0) ? qp : q0);
+        const size_t gidx = (size_t)gdir2 * P + (size_t)gsr * nx + gcol2;
+        return load_elem<S, LD>(fin + gidx);
+    }
 
     // As run(), with the rows moved through shared memory so that one row of
     // loads is in flight while the warp computes, without holding it in
@@ -850,6 +902,87 @@ struct Walker {
                     collide_store(r, wc, d1, d2, d0, l1, r1, c);
                 else
                     collide_store(r, wc, d1, d0, d2, l1, r1, c);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    stash[i * 32 + lane] = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                d2[v] = d1[v];
+                d1[v] = d0[v];
+            }
+            l1 = l0;
+            r1 = r0;
+        }
+    }
+
+    // run_async for the split walk (SEG == 16): y0, y1 and dir are the
+    // lane's half's segment; K is the larger half's row count plus two, the
+    // pulls both halves make.  The shorter half pulls rows past its segment
+    // (wrapped, so in range) and stores none of them.  The rows differ
+    // between the halves, so they are per-lane values here: only the pulled
+    // row q is kept (its neighbours and the collided row are derived from it).
+    __device__ __forceinline__ void run_async_split(int y0, int y1, int dir, int K,
+                                                    const Coef &c, uint4 *buf) const {
+        static_assert(NW == 4 && SEG == 16, "8-site 16-bit split walk");
+        uint4 *land = buf;
+        uint4 *stash = buf + 9 * 32;
+        const int n = y1 - y0;
+        int q = dir > 0 ? ((y0 == 0) ? ny - 1 : y0 - 1) : (y1 == ny ? 0 : y1);
+
+        float d2[V], d1[V], d0[V];
+        float l1 = 0.f, r1 = 0.f, l0, r0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            d2[v] = 0.f;
+            d1[v] = 0.f;
+        }
+        uint32_t gnext, gnext2;
+        {
+            const int qm = (q == 0) ? ny - 1 : q - 1, qp = (q + 1 == ny) ? 0 : q + 1;
+            issue_row_async(qm, q, qp, land);
+            gnext = load_helper(qm, q, qp);
+            gnext2 = load_helper2(qm, q, qp);
+        }
+        for (int k = 0; k < K; ++k) {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            uint32_t w[9][NW];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const uint4 u = land[i * 32 + lane];
+                w[i][0] = u.x;
+                w[i][1] = u.y;
+                w[i][2] = u.z;
+                w[i][3] = u.w;
+            }
+            const uint32_t g = gnext, g2 = gnext2;
+            q += dir;
+            if (q < 0) q += ny;
+            if (q >= ny) q -= ny;
+            finish_pull(w, g, d0, l0, r0, g2);
+            if (k + 1 < K) {
+                const int qm = (q == 0) ? ny - 1 : q - 1, qp = (q + 1 == ny) ? 0 : q + 1;
+                issue_row_async(qm, q, qp, land);
+                gnext = load_helper(qm, q, qp);
+                gnext2 = load_helper2(qm, q, qp);
+            }
+            if (k >= 2) {
+                uint32_t wc[9][NW];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const uint4 u = stash[i * 32 + lane];
+                    wc[i][0] = u.x;
+                    wc[i][1] = u.y;
+                    wc[i][2] = u.z;
+                    wc[i][3] = u.w;
+                    stash[i * 32 + lane] = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+                }
+                // The collided row was pulled two rows before the next one, q.
+                int r = q - 2 * dir;
+                if (r < 0) r += ny;
+                if (r >= ny) r -= ny;
+                collide_store(r, wc, d1, d2, d0, l1, r1, c, k - 2 < n, dir < 0);
             } else {
 #pragma unroll
                 for (int i = 0; i < 9; ++i)

@@ -87,6 +87,7 @@ def load() -> ctypes.CDLL:
             "lbm_batch_get_groups": ([vp, ctypes.POINTER(i)], i),
             "lbm_batch_get_config": ([vp, ctypes.POINTER(i), ctypes.POINTER(i),
                                       ctypes.POINTER(i)], i),
+            "lbm_batch_get_tiles": ([vp, ctypes.POINTER(i), ctypes.POINTER(i)], i),
             "lbm_batch_set_timeout_us": ([vp, ll], i),
             "lbm_batch_set_launch": ([vp, i], i),
             "lbm_batch_set_schedule": ([vp, i], i),
@@ -436,8 +437,12 @@ class Batch:
         _check(self.lib.lbm_batch_get_walk16(self.b, ctypes.byref(wk)), "lbm_batch_get_walk16")
         ng = ctypes.c_int()
         _check(self.lib.lbm_batch_get_groups(self.b, ctypes.byref(ng)), "lbm_batch_get_groups")
+        nt, npair = ctypes.c_int(), ctypes.c_int()
+        _check(self.lib.lbm_batch_get_tiles(self.b, ctypes.byref(nt), ctypes.byref(npair)),
+               "lbm_batch_get_tiles")
         return {"rows": r.value, "blocks_per_sm": b.value, "specialised": bool(sp.value),
-                "walk16": WALK16_NAMES[wk.value], "groups": ng.value}
+                "walk16": WALK16_NAMES[wk.value], "groups": ng.value, "tiles": nt.value,
+                "paired_tiles": npair.value}
 
     def set_walk16(self, walk: str):
         """Walk of the batch's 16-bit grids: 'auto' (the default, 'v8'), 'v8'
