@@ -110,14 +110,14 @@ static void drop_graph(lbm_batch *b) {
 }
 
 // Sites per lane of a grid's walk.  FP32: 4 (128-bit loads) when nx is a
-// multiple of 4.  16-bit without a c2 field: 8 (128-bit loads, rows through
-// shared memory) when nx is a multiple of 8 and the walk is LBM_WALK16_AUTO
-// or LBM_WALK16_V8; else 4 (64-bit loads, one row prefetched in registers)
-// when nx is a multiple of 4.  Any other nx: 1.  (Measured on GB300: 8 sites
+// multiple of 4.  16-bit: 8 (128-bit loads, rows and any c2 field's values
+// through shared memory) when nx is a multiple of 8 and the walk is
+// LBM_WALK16_AUTO or LBM_WALK16_V8; else 4 (64-bit loads, one row prefetched
+// in registers) when nx is a multiple of 4.  Any other nx: 1.  (Measured on GB300: 8 sites
 // per lane run 15 % faster than 4 with nearest rounding and 10 % faster with
 // stochastic rounding.)
 static int batch_vec(const lbm_batch *b, const lbm_grid *g) {
-    const bool eight = !g->a15f && (b->walk16 == LBM_WALK16_V8 || b->walk16 == LBM_WALK16_AUTO);
+    const bool eight = b->walk16 == LBM_WALK16_V8 || b->walk16 == LBM_WALK16_AUTO;
     if (g->storage != ST_F32 && eight && g->nx % 8 == 0) return 8;
     return g->nx % 4 == 0 ? 4 : 1;
 }

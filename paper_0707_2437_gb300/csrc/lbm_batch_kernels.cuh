@@ -146,6 +146,21 @@ __device__ __noinline__ void do_tile(const GridDesc &g, int par, const Tile &t, 
         w.run(t.y0, t.y1, t.dir, g.c);
 }
 
+// A 256-column tile of an 8-site 16-bit grid with a c2 field, in the general
+// kernel: two 4-site walks of 128 columns (the register walk at 8 sites with
+// the field's eight values spills heavily out of line; the results are the
+// same bit for bit).
+template <int S>
+__device__ __forceinline__ void field_tile8(const GridDesc &g, int par, const Tile &t,
+                                            uint32_t step) {
+    do_tile<S, 4, true, 0, 1>(g, par, t, step);
+    if (t.x0 + 128 < g.nx) {
+        Tile u = t;
+        u.x0 = t.x0 + 128;
+        do_tile<S, 4, true, 0, 1>(g, par, u, step);
+    }
+}
+
 // One tile of any kind (the walks out of line: one kernel for every mix).
 __device__ __forceinline__ void any_tile(const GridDesc &g, int par, const Tile &t,
                                          uint32_t step) {
@@ -198,11 +213,17 @@ __device__ __forceinline__ void any_tile(const GridDesc &g, int par, const Tile 
         case kind_code(ST_F32, 1, 0, 1):
             do_tile<ST_F32, 1, false, 0, 1>(g, par, t, step);
             break;
+        case kind_code(ST_F16, 8, 0, 1):
+            field_tile8<ST_F16>(g, par, t, step);
+            break;
         case kind_code(ST_F16, 4, 0, 1):
             do_tile<ST_F16, 4, true, 0, 1>(g, par, t, step);
             break;
         case kind_code(ST_F16, 1, 0, 1):
             do_tile<ST_F16, 1, false, 0, 1>(g, par, t, step);
+            break;
+        case kind_code(ST_BF16, 8, 0, 1):
+            field_tile8<ST_BF16>(g, par, t, step);
             break;
         case kind_code(ST_BF16, 4, 0, 1):
             do_tile<ST_BF16, 4, true, 0, 1>(g, par, t, step);
@@ -420,7 +441,7 @@ __global__ void __launch_bounds__(32 * kBatchWarps, PD == 2 ? 3 : 4)
                const uint32_t *__restrict__ t0, unsigned long long *ctl, int *prog,
                unsigned *glob, const int *__restrict__ nwork_p, int *status,
                unsigned long long timeout_ns) {
-    __shared__ uint4 rowbuf[(S != ST_F32 && V == 8) ? kBatchWarps : 1][2 * 9 * 32];
+    __shared__ uint4 rowbuf[(S != ST_F32 && V == 8) ? kBatchWarps : 1][(2 * 9 + (VA ? 4 : 0)) * 32];
     (void)rowbuf;
     flow_loop(grids, ngrids, tiles, limit, parity0, t0, ctl, prog, glob, nwork_p, status,
               timeout_ns, [&](const GridDesc &g, int par, const Tile &t, uint32_t step) {
@@ -561,8 +582,9 @@ __global__ void __launch_bounds__(32 * kBatchWarps, PD == 2 ? 3 : 4)
                 const uint32_t *__restrict__ t0, long long nsteps, unsigned *bar, int *status,
                 unsigned long long timeout_ns) {
     // Row buffers of the 8-site 16-bit walks: per warp a landing slot and a
-    // stash of 9 x 32 16-byte vectors each (36 KiB per block).
-    __shared__ uint4 rowbuf[(S != ST_F32 && V == 8) ? kBatchWarps : 1][2 * 9 * 32];
+    // stash of 9 x 32 16-byte vectors each (36 KiB per block), and with a c2
+    // field two slots of 2 x 32 vectors for its values (44 KiB per block).
+    __shared__ uint4 rowbuf[(S != ST_F32 && V == 8) ? kBatchWarps : 1][(2 * 9 + (VA ? 4 : 0)) * 32];
     (void)rowbuf;
     for (long long k = 0; k < nsteps; ++k) {
         reset_counter(bar, k);
@@ -636,6 +658,10 @@ BatchKernel kernel_for(const std::vector<int> &kinds, int walk16, bool split = f
                 return two ? k_batch_one<ST_BF16, 4, 2, 1> : k_batch_one<ST_BF16, 4, 1, 1>;
             case kind_code(ST_F32, 4, 0, 1):
                 return k_batch_one<ST_F32, 4, 0, 0, 1>;
+            case kind_code(ST_F16, 8, 0, 1):
+                return k_batch_one<ST_F16, 8, 0, 0, 1>;
+            case kind_code(ST_BF16, 8, 0, 1):
+                return k_batch_one<ST_BF16, 8, 0, 0, 1>;
             case kind_code(ST_F16, 4, 0, 1):
                 return k_batch_one<ST_F16, 4, 1, 0, 1>;
             case kind_code(ST_BF16, 4, 0, 1):

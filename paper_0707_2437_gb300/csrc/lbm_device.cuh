@@ -705,16 +705,44 @@ struct Walker {
     __device__ __forceinline__ void collide_store(int r, uint32_t (&w)[9][NW], const float (&d)[V],
                                                   const float (&dym)[V], const float (&dyp)[V],
                                                   float dl, float dr, const Coef &c,
-                                                  bool keep = true, bool swap_y = false) const {
+                                                  bool keep = true, bool swap_y = false,
+                                                  const uint4 *aslot = nullptr) const {
         // x neighbours of drho: inside the lane, then the adjacent lanes, then
         // the halo sites at the strip edges.
         float lft = __shfl_up_sync(FULL, d[V - 1], 1, SEG);
         float rgt = __shfl_down_sync(FULL, d[0], 1, SEG);
         if (sl == 0) lft = dl;
         if (sl == nact - 1) rgt = dr;
-        // 1.5 alpha of the lane's sites: the grid's constant, or the field.
+        // 1.5 alpha of the lane's sites: the grid's constant, or the field
+        // (8-site walks: staged in shared memory by run_async, `aslot`, or
+        // read as two 16-byte vectors).
         float a15v[V];
-        if constexpr (VA) {
+        if constexpr (VA && V == 8) {
+            if (aslot) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint4 u = aslot[h * 32 + lane];
+                    a15v[4 * h + 0] = __uint_as_float(u.x);
+                    a15v[4 * h + 1] = __uint_as_float(u.y);
+                    a15v[4 * h + 2] = __uint_as_float(u.z);
+                    a15v[4 * h + 3] = __uint_as_float(u.w);
+                }
+            } else {
+                const size_t aidx = (size_t)r * nx + (act ? xs : x0);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t aw[4];
+                    if (VSS_IN_BOUNDS(aidx + 4 * h, 4, (size_t)nx * ny)) {
+                        load_words<ST_F32, 4, LD>(a15f + aidx + 4 * h, aw);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) aw[v] = 0u;
+                    }
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) a15v[4 * h + v] = __uint_as_float(aw[v]);
+                }
+            }
+        } else if constexpr (VA) {
             const size_t aidx = (size_t)r * nx + (act ? xs : x0);
             uint32_t aw[V];
             if (VSS_IN_BOUNDS(aidx, V, (size_t)nx * ny)) {
@@ -853,6 +881,12 @@ struct Walker {
         static_assert(NW == 4, "the row buffers hold four words per lane and direction");
         uint4 *land = buf;
         uint4 *stash = buf + 9 * 32;
+        // c2 field: two slots of the lane's eight 1.5-alpha values ([2][32]
+        // 16-byte vectors each) after the stash.  The values a row's collision
+        // needs are copied with the pulled row before it, in the same commit
+        // group, into the slot the previous collision did not read.
+        uint4 *aslots = buf + 18 * 32;
+        (void)aslots;
         int q0 = dir > 0 ? ((y0 == 0) ? ny - 1 : y0 - 1) : (y1 == ny ? 0 : y1);
         int qm = (q0 == 0) ? ny - 1 : q0 - 1;
         int qp = (q0 + 1 == ny) ? 0 : q0 + 1;
@@ -883,6 +917,20 @@ struct Walker {
             advance(qm, q0, qp, dir);
             finish_pull(w, g, d0, l0, r0);
             if (k + 1 < K) {
+                if constexpr (VA) {
+                    if (k >= 1) {
+                        // alpha of the row collided at k + 1 (segment row k - 1)
+                        const int ra = dir > 0 ? y0 + (k - 1) : y1 - 1 - (k - 1);
+                        const float *src = a15f + (size_t)ra * nx + (act ? xs : x0);
+                        uint4 *dst = aslots + ((k + 1) & 1) * 64 + lane;
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)
+                            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                                             (uint32_t)__cvta_generic_to_shared(dst + h * 32)),
+                                         "l"(src + 4 * h)
+                                         : "memory");
+                    }
+                }
                 issue_row_async(qm, q0, qp, land);
                 gnext = load_helper(qm, q0, qp);
             }
@@ -898,10 +946,11 @@ struct Walker {
                     stash[i * 32 + lane] = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
                 }
                 const int r = dir > 0 ? y0 + (k - 2) : y1 - 1 - (k - 2);
+                const uint4 *as = VA ? aslots + (k & 1) * 64 : nullptr;
                 if (dir > 0)
-                    collide_store(r, wc, d1, d2, d0, l1, r1, c);
+                    collide_store(r, wc, d1, d2, d0, l1, r1, c, true, false, as);
                 else
-                    collide_store(r, wc, d1, d0, d2, l1, r1, c);
+                    collide_store(r, wc, d1, d0, d2, l1, r1, c, true, false, as);
             } else {
 #pragma unroll
                 for (int i = 0; i < 9; ++i)
