@@ -106,6 +106,7 @@ def test_every_handle_call_rejects_null_before_device_work():
         lambda: lib.lbm_batch_tune(None),
         lambda: lib.lbm_batch_get_config(None, ctypes.byref(i), ctypes.byref(i), ctypes.byref(i)),
         lambda: lib.lbm_batch_get_groups(None, ctypes.byref(i)),
+        lambda: lib.lbm_batch_get_tiles(None, ctypes.byref(i), ctypes.byref(i)),
         lambda: lib.lbm_batch_set_walk16(None, 0),
         lambda: lib.lbm_batch_get_walk16(None, ctypes.byref(i)),
         lambda: lib.lbm_batch_set_timeout_us(None, 1000),
