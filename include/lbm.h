@@ -213,7 +213,10 @@ size_t lbm_bytes_required(int nx, int ny, int storage);
 int lbm_mem_info(size_t *free_bytes, size_t *total_bytes);
 
 /* Checkpoint: the raw stored distributions (9 planes of nx*ny elements of the
- * storage type, plane-major, each plane [ny][nx]) of the current state.
+ * storage type, plane-major, each plane [ny][nx]) of the current state.  The
+ * steps pull, so a buffer holds values at the site they stream from: plane i
+ * at site x is the value the next step reads as f_i(x + e_i), stored as
+ * h_i = (f_i - w_i rho0)/w_i.
  * lbm_state_bytes gives the size; lbm_get_state copies it to host memory and
  * the step counter to *t (may be NULL); lbm_set_state restores both.  A run
  * resumed from a checkpoint is bitwise identical to an uninterrupted one. */
@@ -258,6 +261,21 @@ int lbm_get_pipeline(lbm_t h, int *stages, int *active);
 int lbm_set_rounding(lbm_t h, int mode);
 int lbm_get_rounding(lbm_t h, int *mode);
 
+/* Discretisation of grad(rho) in the force (Section 4).
+ *   LBM_GRAD_CENTRAL  the default and the paper's scheme:
+ *                     (rho(x+1) - rho(x-1))/2 along x and y
+ *   LBM_GRAD_FORWARD  rho(x+1) - rho(x) along x and y, the scheme the paper
+ *                     found unstable as c_e approaches 1; for reproducing that
+ *                     instability.  FP32 storage without a c2 field only; the
+ *                     grid then steps with the one-site-per-lane step kernel
+ *                     (no persistent launch) and cannot join a batch.
+ * Waits for the handle's stream.  LBM_EINVAL for other modes, 16-bit storage,
+ * a grid with a c2 field or a slab. */
+#define LBM_GRAD_CENTRAL 0
+#define LBM_GRAD_FORWARD 1
+int lbm_set_gradient(lbm_t h, int mode);
+int lbm_get_gradient(lbm_t h, int *mode);
+
 /* Autotuner: times the valid tile configurations on this grid (without
  * changing its state) and keeps the fastest.  If cache_path is not NULL the
  * choice is read from / stored in that JSON file, keyed by device, storage
@@ -293,7 +311,7 @@ int lbm_batch_destroy(lbm_batch_t b);
  * kernel stop and the next synchronising batch call return LBM_ETIMEOUT.
  * If a grid's c2 field or rounding mode changed since the batch was built,
  * the work-list is rebuilt first (the call then waits for the stream).
- * LBM_EINVAL if a grid has gained a drive. */
+ * LBM_EINVAL if a grid has gained a drive or the forward-difference gradient. */
 int lbm_batch_step(lbm_batch_t b, long long n, const long long *limits);
 
 /* Waits for the batch's stream and returns the kernel's status

@@ -375,9 +375,13 @@ static cudaError_t launch_drive(lbm_grid *h, void *out, const uint32_t *tdev, ui
 // One step launch from buf[cur] to buf[cur ^ 1] (no bookkeeping), followed
 // by the boundary columns when the channel is driven.
 static cudaError_t launch_one(lbm_grid *h, int from) {
-    cudaError_t e = launch_step(h->storage, h->cfg, h->buf[from], h->buf[from ^ 1], h->nx, h->ny,
-                                h->P, h->coef, status_ptr(h), h->rounding, nullptr,
-                                (uint32_t)h->t, h->a15f, h->stream);
+    cudaError_t e =
+        h->grad == LBM_GRAD_FORWARD
+            ? launch_step_forward(h->cfg, h->buf[from], h->buf[from ^ 1], h->nx, h->ny, h->P,
+                                  h->coef, h->stream)
+            : launch_step(h->storage, h->cfg, h->buf[from], h->buf[from ^ 1], h->nx, h->ny, h->P,
+                          h->coef, status_ptr(h), h->rounding, nullptr, (uint32_t)h->t, h->a15f,
+                          h->stream);
     if (e == cudaSuccess && h->drive)
         e = launch_drive(h, h->buf[from ^ 1], nullptr, (uint32_t)h->t, h->stream);
     return e;
@@ -400,10 +404,14 @@ static int build_graphs(lbm_grid *h) {
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             for (int k = 0; k < 2 * kGraphPairs && e == cudaSuccess; ++k) {
-                e = launch_step(h->storage, h->cfg, h->buf[(start + k) & 1],
-                                h->buf[(start + k + 1) & 1], h->nx, h->ny, h->P, h->coef,
-                                status_ptr(h), h->rounding, step_ptr(h), (uint32_t)k, h->a15f,
-                                cs);
+                e = h->grad == LBM_GRAD_FORWARD
+                        ? launch_step_forward(h->cfg, h->buf[(start + k) & 1],
+                                              h->buf[(start + k + 1) & 1], h->nx, h->ny, h->P,
+                                              h->coef, cs)
+                        : launch_step(h->storage, h->cfg, h->buf[(start + k) & 1],
+                                      h->buf[(start + k + 1) & 1], h->nx, h->ny, h->P, h->coef,
+                                      status_ptr(h), h->rounding, step_ptr(h), (uint32_t)k,
+                                      h->a15f, cs);
                 if (e == cudaSuccess && h->drive)
                     e = launch_drive(h, h->buf[(start + k + 1) & 1], step_ptr(h), (uint32_t)k, cs);
             }
@@ -449,7 +457,7 @@ extern "C" int lbm_step(lbm_t h, long long n) {
         return fail(LBM_EINVAL, "lbm_step: a slab takes one step at a time (its ghost rows "
                                 "are refreshed between steps)");
     const bool large = (long long)h->nx * h->ny >= kLargeSites;
-    if (h->slab || (h->persistent && !h->drive &&
+    if (h->slab || (h->persistent && !h->drive && h->grad == LBM_GRAD_CENTRAL &&
                     (n >= kPersistentMin || (large && n >= kPersistentMinLarge)))) {
         // Slabs always step here: the batch's tile list covers only their
         // own rows.
@@ -676,6 +684,8 @@ extern "C" int lbm_set_c2_field(lbm_t h, const double *c2, int on_device) {
         return LBM_OK;
     }
     if (h->rounding) return fail(LBM_EINVAL, "lbm_set_c2_field: needs nearest rounding");
+    if (h->grad != LBM_GRAD_CENTRAL)
+        return fail(LBM_EINVAL, "lbm_set_c2_field: needs the central-difference gradient");
     size_t n = (size_t)h->nx * h->ny;
     if (!on_device) {
         for (size_t s = 0; s < n; ++s)
@@ -735,6 +745,29 @@ extern "C" int lbm_set_rounding(lbm_t h, int mode) {
         if (h->cfg.stages >= 2) h->cfg.stages = 0;
     }
     CK(prepare_step(h->storage, h->cfg));
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_gradient(lbm_t h, int mode) {
+    if (!h) return fail(LBM_EINVAL, "lbm_set_gradient: NULL handle");
+    if (mode != LBM_GRAD_CENTRAL && mode != LBM_GRAD_FORWARD)
+        return fail(LBM_EINVAL, "lbm_set_gradient: unknown mode");
+    if (mode == LBM_GRAD_FORWARD) {
+        if (h->storage != ST_F32)
+            return fail(LBM_EINVAL, "lbm_set_gradient: the forward difference needs FP32 storage");
+        if (h->a15f) return fail(LBM_EINVAL, "lbm_set_gradient: not with a c2 field");
+        if (h->slab) return fail(LBM_EINVAL, "lbm_set_gradient: not on a slab");
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
+    drop_self_batch(h);
+    h->grad = mode;
+    return LBM_OK;
+}
+
+extern "C" int lbm_get_gradient(lbm_t h, int *mode) {
+    if (!h || !mode) return fail(LBM_EINVAL, "lbm_get_gradient: NULL argument");
+    *mode = h->grad;
     return LBM_OK;
 }
 

@@ -356,6 +356,9 @@ extern "C" int lbm_batch_create(const lbm_t *grids, int n, lbm_batch_t *out) {
         if (!grids[k]) return bfail(LBM_EINVAL, "lbm_batch_create: NULL grid");
         if (grids[k]->drive)
             return bfail(LBM_EINVAL, "lbm_batch_create: driven grids are not batched");
+        if (grids[k]->grad != LBM_GRAD_CENTRAL)
+            return bfail(LBM_EINVAL, "lbm_batch_create: the batch kernels use the central "
+                                     "difference (lbm_set_gradient)");
     }
     lbm_batch *b = new (std::nothrow) lbm_batch();
     if (!b) return bfail(LBM_ENOMEM, "lbm_batch_create: host allocation failed");
@@ -549,6 +552,8 @@ extern "C" int lbm_batch_step(lbm_batch_t b, long long n, const long long *limit
     for (size_t k = 0; k < b->grids.size(); ++k) {
         const lbm_grid *g = b->grids[k];
         if (g->drive) return bfail(LBM_EINVAL, "lbm_batch_step: a grid has a drive");
+        if (g->grad != LBM_GRAD_CENTRAL)
+            return bfail(LBM_EINVAL, "lbm_batch_step: a grid uses the forward difference");
         stale = stale || g->a15f != b->built_a15f[k] || g->rounding != b->built_rounding[k];
     }
     if (stale) {

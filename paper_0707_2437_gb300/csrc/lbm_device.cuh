@@ -456,7 +456,11 @@ __device__ __forceinline__ void pair_out(float hi, float hopp, float ej, float e
 // each half-warp walks its own segment of a strip at most 16*V columns wide,
 // so that two narrow pieces of work fill one warp; every shuffle stays within
 // the half, and each lane serves one halo role on each side.
-template <int S, int V, int LD = LD_NC, int RND = 0, int VA = 0, int SEG = 32>
+// GR = 1: the forward difference the paper tried before the central one
+// (Section 4): grad = rho(x+1) - rho(x) in x and y instead of half the central
+// difference, for the instability it shows as c_e approaches 1.  Only the
+// FP32 single-grid step kernel instantiates it.
+template <int S, int V, int LD = LD_NC, int RND = 0, int VA = 0, int SEG = 32, int GR = 0>
 struct Walker {
     static constexpr int NW = Pack<S, V>::NW;
     using T = typename StoreT<S>::T;
@@ -765,14 +769,17 @@ struct Walker {
 #pragma unroll
             for (int s = 0; s < SP; ++s) {
                 const int v = v0 + s;
-                const float dxm = (v == 0) ? lft : d[v - 1];
+                // Forward difference: the site itself in place of the x-1 and
+                // y-1 neighbours, and twice the factor that holds the central
+                // difference's 1/2 (exact in FP32).
+                const float dxm = GR ? d[v] : ((v == 0) ? lft : d[v - 1]);
                 const float dxp = (v == V - 1) ? rgt : d[v + 1];
                 float *hs = h[s];
                 const SiteQ q = site_quantities(hs[1], hs[2], hs[3], hs[4], hs[5], hs[6], hs[7],
                                                 hs[8], d[v], dxm, dxp,
-                                                swap_y ? dyp[v] : dym[v],
+                                                GR ? d[v] : (swap_y ? dyp[v] : dym[v]),
                                                 swap_y ? dym[v] : dyp[v], c,
-                                                a15v[v]);
+                                                GR ? __fmul_rn(2.f, a15v[v]) : a15v[v]);
                 float o[9];
                 o[0] = __fmaf_rn(c.om1, hs[0], q.wB);                           // rest
                 pair_out(hs[1], hs[3], q.jx, q.ux, q.Ax, q.wB, c, o[1], o[3]);  // e = (1, 0)

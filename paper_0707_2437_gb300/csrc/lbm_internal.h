@@ -68,6 +68,9 @@ Coef make_coef(double tau, double c2, double rho0);
 Err launch_step(int storage, const TileCfg &cfg, const void *fin, void *fout, int nx, int ny,
                 size_t P, const Coef &c, int *status, int rnd, const uint32_t *tdev, uint32_t toff,
                 const float *a15f, cudaStream_t st);
+// The forward-difference gradient (lbm_set_gradient): FP32, one site per lane.
+Err launch_step_forward(const TileCfg &cfg, const void *fin, void *fout, int nx, int ny, size_t P,
+                        const Coef &c, cudaStream_t st);
 Err launch_a15_from_c2(const double *c2, float *a15, long long n, cudaStream_t st);
 Err launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t st);
 // Sets the kernel attributes a configuration needs (dynamic shared memory);
@@ -111,6 +114,7 @@ struct lbm_grid {
     vss::TileCfg cfg{};
     int rounding = 0;             // 1: stochastic rounding of 16-bit stores
     float *a15f = nullptr;        // spatially varying alpha: 1.5 alpha per site
+    int grad = 0;                 // LBM_GRAD_CENTRAL or LBM_GRAD_FORWARD
     // Slab of a grid decomposed in y (lbm_slab_create): this many ghost rows
     // at each end of the local buffer, which steps read but never compute
     // (0 for an ordinary periodic grid).

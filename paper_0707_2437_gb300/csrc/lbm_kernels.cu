@@ -70,7 +70,7 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned 
 // ---------------------------------------------------------------------------
 // Fused step: one warp per (strip, row segment) tile.
 
-template <int S, int V, bool PF, int RND = 0, int VA = 0>
+template <int S, int V, bool PF, int RND = 0, int VA = 0, int GR = 0>
 __global__ void __launch_bounds__(256, 2)
     k_step(const void *__restrict__ fin, void *__restrict__ fout, int nx, int ny, size_t P,
            int nstrips, long long ntiles, int rows, Coef c, const uint32_t *tdev,
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(256, 2)
     int x0 = strip * 32 * V;
     int y0 = seg * rows;
     int y1 = min(ny, y0 + rows);
-    Walker<S, V, LD_NC, RND, VA> w(fin, fout, nx, ny, P, x0);
+    Walker<S, V, LD_NC, RND, VA, 32, GR> w(fin, fout, nx, ny, P, x0);
     if constexpr (VA) w.a15f = a15f;
     // Stochastic rounding is seeded by the step being computed: a device
     // counter (set before each graph replay) plus this launch's offset.
@@ -324,6 +324,19 @@ static Err launch_step_s(const TileCfg &cfg, const void *fin, void *fout, int nx
         default:
             return cudaErrorInvalidValue;
     }
+}
+
+Err launch_step_forward(const TileCfg &cfg, const void *fin, void *fout, int nx, int ny, size_t P,
+                        const Coef &c, cudaStream_t st) {
+    // One site per lane (any nx), the configured tile height and block size.
+    TileCfg c1 = cfg;
+    c1.vec = 1;
+    c1.stages = 0;
+    StepGeom g = step_geom(nx, ny, c1);
+    long long blocks = (g.ntiles + c1.warps - 1) / c1.warps;
+    return launch_pdl(k_step<ST_F32, 1, false, 0, 0, 1>, (unsigned)blocks, 32u * c1.warps, 0, st,
+                      fin, fout, nx, ny, P, g.nstrips, g.ntiles, c1.rows, c,
+                      (const uint32_t *)nullptr, 0u, (const float *)nullptr);
 }
 
 Err launch_step(int storage, const TileCfg &cfg, const void *fin, void *fout, int nx, int ny,

@@ -88,6 +88,8 @@ def load() -> ctypes.CDLL:
             "lbm_batch_get_config": ([vp, ctypes.POINTER(i), ctypes.POINTER(i),
                                       ctypes.POINTER(i)], i),
             "lbm_batch_get_tiles": ([vp, ctypes.POINTER(i), ctypes.POINTER(i)], i),
+            "lbm_set_gradient": ([vp, i], i),
+            "lbm_get_gradient": ([vp, ctypes.POINTER(i)], i),
             "lbm_batch_set_timeout_us": ([vp, ll], i),
             "lbm_batch_set_launch": ([vp, i], i),
             "lbm_batch_set_schedule": ([vp, i], i),
@@ -311,6 +313,17 @@ class Grid:
         """'nearest' or 'stochastic' (16-bit storage only)."""
         _check(self.lib.lbm_set_rounding(self.h, {"nearest": 0, "stochastic": 1}[mode]),
                "lbm_set_rounding")
+
+    def set_gradient(self, mode: str):
+        """'central' (the default, Section 4's scheme) or 'forward' (the
+        forward difference, for its instability; FP32 without a c2 field)."""
+        _check(self.lib.lbm_set_gradient(self.h, {"central": 0, "forward": 1}[mode]),
+               "lbm_set_gradient")
+
+    def get_gradient(self) -> str:
+        m = ctypes.c_int()
+        _check(self.lib.lbm_get_gradient(self.h, ctypes.byref(m)), "lbm_get_gradient")
+        return ["central", "forward"][m.value]
 
     def get_rounding(self) -> str:
         m = ctypes.c_int()
