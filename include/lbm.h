@@ -179,11 +179,13 @@ int lbm_set_drive(lbm_t h, int on, double amplitude, double period);
  * [ny][nx] array of c_e^2 > 0 (host if on_device == 0, else device; host
  * values are checked); the force at site x uses alpha(x) = 1/3 - c2(x) in
  * Eq. 5.  NULL returns to the grid's uniform c2.  The field costs one more
- * 4-byte read per site and step.  While a field is set the walks use at most
- * 4 sites per lane, no bulk-copy pipeline and nearest rounding (an FP32 grid
- * configured for 4 sites per lane steps with 2 sites per lane and one row of
- * loads prefetched: as fast, and within the register budget); the grid can
- * join a batch and long lbm_step calls still run one persistent launch. */
+ * 4-byte read per site and step.  While a field is set the single-grid step
+ * kernel uses at most 4 sites per lane, no bulk-copy pipeline and nearest
+ * rounding (an FP32 grid configured for 4 sites per lane steps with 2 sites
+ * per lane and one row of loads prefetched, its tile height raised to fill
+ * one wave of resident warps where that helps); the grid can join a batch,
+ * and long lbm_step calls still run one persistent launch, where 16-bit grids
+ * with nx a multiple of 8 take the 8-site walk. */
 int lbm_set_c2_field(lbm_t h, const double *c2, int on_device);
 
 /* Steps taken since lbm_init / lbm_set_state. */
