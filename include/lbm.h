@@ -116,19 +116,30 @@ int lbm_init(lbm_t h, const double *rho, const double *ux, const double *uy,
              int on_device);
 
 /* Queues n >= 0 time steps of Eq. 5 (stream, moments, central grad(rho),
- * collide with force) on the handle's stream.  From 64 steps on, or from 8
- * on grids of at least 2^20 sites (while persistent mode is on, the default,
- * and without a drive), the steps run as one persistent launch:
- * the batched kernel (see lbm_batch_create) with this grid alone, warps taking
- * tiles dynamically, a bounded grid barrier between steps.  Other calls
- * launch the step kernel with the handle's tile configuration, replayed from
- * CUDA graphs from 8 steps on.  All forms give bitwise the same result.
+ * collide with force) on the handle's stream.  Calls either launch the step
+ * kernel once per step with the handle's tile configuration (replayed from
+ * CUDA graphs from 8 steps on), or run all n steps as one persistent launch:
+ * the batched kernel (see lbm_batch_create) with this grid alone, warps
+ * taking tiles dynamically, a bounded grid barrier between steps.  Which one
+ * is set by lbm_set_persistent; by default (LBM_PERSISTENT_AUTO) calls of 8
+ * steps or more on 16-bit grids of at least 2^24 sites without a c2 field run
+ * persistent, where its 8-site walk is the faster, and all other calls launch
+ * the step kernel, the faster for every FP32 grid and for smaller 16-bit grids
+ * (measured on 64^2 to 8192^2).  A slab always steps persistent; a driven grid or the
+ * forward-difference gradient never.  All forms give bitwise the same result.
  * Asynchronous: errors of the kernels surface at the next synchronising call
  * (LBM_ETIMEOUT if a bounded wait ran out). */
 int lbm_step(lbm_t h, long long n);
 
-/* Persistent mode of lbm_step (on by default); off: every call uses the step
- * kernel with the tile configuration. */
+/* Persistent mode of lbm_step:
+ *   LBM_PERSISTENT_OFF   every call uses the step kernel
+ *   LBM_PERSISTENT_ON    calls of 64 steps or more, or of 8 or more on grids
+ *                        of at least 2^20 sites, run one persistent launch
+ *   LBM_PERSISTENT_AUTO  the default: as described at lbm_step
+ * LBM_EINVAL for other values. */
+#define LBM_PERSISTENT_OFF 0
+#define LBM_PERSISTENT_ON 1
+#define LBM_PERSISTENT_AUTO 2
 int lbm_set_persistent(lbm_t h, int on);
 
 /* Writes rho, ux, uy (Eq. 3) of the current state, computed in FP64 from the
@@ -231,7 +242,12 @@ int lbm_set_state(lbm_t h, const void *src_host, long long t);
  * adjacent sites per lane (vectorised loads of vec elements): 1, 2 or 4 for
  * any storage, 8 for the 16-bit storages; nx must be a multiple of vec.
  * rows in [1, 4096], warps in {1, 2, 4, 8}.  The result of a step does
- * not depend on the configuration (bitwise). */
+ * not depend on the configuration (bitwise).  Until this is called (or
+ * lbm_tune), a grid has the default configuration (rows 16), whose register
+ * walks adapt the tile height at launch to the resident warps: fewer rows
+ * (down to 2) when the grid has too few tiles to occupy them, more (up to
+ * 32) when its tiles need between one and two waves; lbm_get_config reports
+ * the configured 16. */
 int lbm_set_config(lbm_t h, int vec, int rows, int warps);
 int lbm_get_config(lbm_t h, int *vec, int *rows, int *warps);
 
@@ -324,12 +340,15 @@ int lbm_batch_sync(lbm_batch_t b);
  * blocks per SM as fit) of the batch kernels; lbm_batch_tune picks the tile
  * height and the 16-bit walk from timed dry steps (the grids' states and step
  * counts are unchanged; on an error the previous configuration is restored
- * and the error returned). */
+ * and the error returned).  Until one of them is called, a lockstep batch
+ * whose tiles at 16 rows would fill less than 3/4 of the resident warps
+ * (16 per SM) takes shorter tiles, down to 2 rows, as many as those warps
+ * hold. */
 int lbm_batch_set_config(lbm_batch_t b, int rows, int blocks_per_sm);
 int lbm_batch_tune(lbm_batch_t b);
-/* Current tile height, resident blocks per SM of the first kind group, and
- * whether every kind group runs a specialised kernel rather than the general
- * one. */
+/* Current tile height (of the lockstep work-list as built), resident blocks
+ * per SM of the first kind group, and whether every kind group runs a
+ * specialised kernel rather than the general one. */
 int lbm_batch_get_config(lbm_batch_t b, int *rows, int *blocks_per_sm, int *specialised);
 /* The work-list as last built (at creation, by a configuration, schedule or
  * walk change, or by a step call that found a grid's field or rounding

@@ -394,6 +394,14 @@ static const long long kPersistentMin = 64;  // persistent launch from this many
 static const long long kPersistentMinLarge = 8;
 static const long long kLargeSites = 1LL << 20;
 static const long long kGraphMin = 8; // use graphs from this many steps on
+// LBM_PERSISTENT_AUTO: 16-bit grids of at least this many sites step
+// persistent (measured per step, 256-step calls: 4096^2 FP16-delta 108.6 us
+// persistent against 111.8 us for the step kernel, 8192^2 385.2 against 405.7;
+// at 2048^2 30.8 against 29.8, and FP32 grids from 64^2 to 8192^2 ran faster
+// on the step kernel: 2048^2 49.6 against 52.2 us, 64^2 3.5 against 6.1 us).
+// With a c2 field the 16-bit step kernel was the faster at 4096^2 too (125.7
+// against 131.2 us).
+static const long long kAutoSites16 = 1LL << 24;
 
 static int build_graphs(lbm_grid *h) {
     drop_graphs(h);
@@ -456,9 +464,14 @@ extern "C" int lbm_step(lbm_t h, long long n) {
     if (h->slab && n != 1)
         return fail(LBM_EINVAL, "lbm_step: a slab takes one step at a time (its ghost rows "
                                 "are refreshed between steps)");
-    const bool large = (long long)h->nx * h->ny >= kLargeSites;
-    if (h->slab || (h->persistent && !h->drive && h->grad == LBM_GRAD_CENTRAL &&
-                    (n >= kPersistentMin || (large && n >= kPersistentMinLarge)))) {
+    const long long sites = (long long)h->nx * h->ny;
+    bool persistent = false;
+    if (h->persistent == LBM_PERSISTENT_ON)
+        persistent = n >= kPersistentMin || (sites >= kLargeSites && n >= kPersistentMinLarge);
+    else if (h->persistent == LBM_PERSISTENT_AUTO)
+        persistent = h->storage != ST_F32 && !h->a15f && sites >= kAutoSites16 &&
+                     n >= kPersistentMinLarge;
+    if (h->slab || (persistent && !h->drive && h->grad == LBM_GRAD_CENTRAL)) {
         // Slabs always step here: the batch's tile list covers only their
         // own rows.
         // One persistent launch of all n steps (dynamic tile scheduling,
@@ -495,9 +508,11 @@ extern "C" int lbm_step(lbm_t h, long long n) {
 
 extern "C" int lbm_set_persistent(lbm_t h, int on) {
     if (!h) return fail(LBM_EINVAL, "lbm_set_persistent: NULL handle");
+    if (on != LBM_PERSISTENT_OFF && on != LBM_PERSISTENT_ON && on != LBM_PERSISTENT_AUTO)
+        return fail(LBM_EINVAL, "lbm_set_persistent: unknown mode");
     CK(cudaStreamSynchronize(h->stream));
-    h->persistent = on != 0;
-    if (!h->persistent) drop_self_batch(h);
+    h->persistent = on;
+    if (on == LBM_PERSISTENT_OFF) drop_self_batch(h);
     return LBM_OK;
 }
 
@@ -654,6 +669,7 @@ extern "C" int lbm_set_config(lbm_t h, int vec, int rows, int warps) {
     h->cfg.vec = vec;
     h->cfg.rows = rows;
     h->cfg.warps = warps;
+    h->cfg.fit_rows = false;
     CK(prepare_step(h->storage, h->cfg));
     return LBM_OK;
 }
@@ -847,6 +863,7 @@ static void write_cache(const char *path, const std::map<std::string, TileCfg> &
 static int time_cfg(lbm_grid *h, const TileCfg &c, int reps, float *ms_out) {
     TileCfg saved = h->cfg;
     h->cfg = c;
+    h->cfg.fit_rows = false;  // time the candidate's own tile height
     cudaError_t e = prepare_step(h->storage, c);
     if (e == cudaSuccess) e = launch_one(h, h->cur);  // warm-up
     if (e == cudaSuccess) e = cudaEventRecord(h->ev[0], h->stream);

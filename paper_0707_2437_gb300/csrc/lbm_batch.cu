@@ -29,6 +29,8 @@ struct lbm_batch {
     cudaStream_t stream = nullptr;
     int device = 0;
     int rows = 16;
+    bool fit_rows = true;   // default: lockstep work-lists may use shorter tiles
+    int lock_rows = 16;     // tile height of the lockstep work-list as built
     int blocks_per_sm = 0;  // 0: the occupancy limit
     // Kind groups: consecutive ranges of the tile list, each run by its own
     // persistent launch (a specialised k_batch_one, or k_batch for the rest),
@@ -164,6 +166,28 @@ static int build_worklist(lbm_batch *b) {
         const int per = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, flow_bps) : flow_bps;
         flow_warps = (long long)per * b->sms * kBatchWarps;
     }
+    // Lockstep, default configuration: every warp walks its tiles one after
+    // another within a step, so a batch with fewer tiles than about the
+    // resident warps (16 per SM in the specialised kernels) spends each step
+    // on a whole walk with warps idle.  Such a batch gets shorter tiles, down
+    // to 2 rows, as many as one wave holds.  Batches of at least 3/4 of a
+    // wave of tiles keep the configured height.
+    int lock_rows = b->rows;
+    if (b->schedule == LBM_SCHEDULE_LOCKSTEP && b->fit_rows) {
+        const int bps = b->blocks_per_sm > 0 ? b->blocks_per_sm : 4;
+        const long long wave = (long long)bps * b->sms * kBatchWarps;
+        auto tiles_at = [&](int r) {
+            long long t = 0;
+            for (const lbm_grid *g : b->grids) {
+                const int w = 32 * batch_vec(b, g);
+                t += (long long)((g->nx + w - 1) / w) * ((g->ny - 2 * g->slab + r - 1) / r);
+            }
+            return t;
+        };
+        if (4 * tiles_at(lock_rows) < 3 * wave)
+            while (lock_rows > 2 && tiles_at(lock_rows - 1) <= wave) --lock_rows;
+    }
+    b->lock_rows = lock_rows;
     for (size_t k = 0; k < b->grids.size(); ++k) {
         lbm_grid *g = b->grids[k];
         GridDesc &d = gd[k];
@@ -182,7 +206,7 @@ static int build_worklist(lbm_batch *b) {
         // with fewer tiles than its share of the resident warps (the warps
         // split evenly between the grids) uses tiles a quarter as tall: four
         // times the tiles, each walk a quarter as long.
-        int rows = b->rows;
+        int rows = lock_rows;
         if (b->schedule == LBM_SCHEDULE_FLOW) {
             const long long tiles_tall =
                 (long long)((g->nx + w - 1) / w) * ((g->ny - 2 * g->slab + b->rows - 1) / b->rows);
@@ -586,8 +610,9 @@ extern "C" int lbm_batch_set_config(lbm_batch_t b, int rows, int blocks_per_sm) 
         return bfail(LBM_EINVAL, "lbm_batch_set_config: bad argument");
     BCK(cudaStreamSynchronize(b->stream));
     b->blocks_per_sm = blocks_per_sm;
-    if (rows != b->rows) {
+    if (rows != b->rows || b->fit_rows) {
         b->rows = rows;
+        b->fit_rows = false;
         return build_worklist(b);
     }
     drop_graph(b);
@@ -673,6 +698,7 @@ extern "C" int lbm_batch_tune(lbm_batch_t b) {
         return bcuda(e, "cudaEventCreate");
     }
     const int rows0 = b->rows, walk0 = b->walk16, bps0 = b->blocks_per_sm;
+    const bool fit0 = b->fit_rows;
     int best_rows = rows0, best_walk = walk0;
     int rc = tune_candidates(b, e0, e1, &best_rows, &best_walk);
     cudaEventDestroy(e0);
@@ -681,6 +707,10 @@ extern "C" int lbm_batch_tune(lbm_batch_t b) {
         // The configuration in force before the call is put back.
         lbm_batch_set_walk16(b, walk0);
         lbm_batch_set_config(b, rows0, bps0);
+        if (fit0) {
+            b->fit_rows = true;
+            build_worklist(b);
+        }
         return rc;
     }
     rc = lbm_batch_set_walk16(b, best_walk);
@@ -730,7 +760,7 @@ extern "C" int lbm_batch_get_tiles(lbm_batch_t b, int *tiles, int *paired) {
 extern "C" int lbm_batch_get_config(lbm_batch_t b, int *rows, int *blocks_per_sm,
                                     int *specialised) {
     if (!b) return bfail(LBM_EINVAL, "lbm_batch_get_config: NULL batch");
-    if (rows) *rows = b->rows;
+    if (rows) *rows = b->schedule == LBM_SCHEDULE_LOCKSTEP ? b->lock_rows : b->rows;
     if (blocks_per_sm)
         *blocks_per_sm = b->groups.empty() ? 0 : grid_blocks(b, b->groups[0]) / b->sms;
     if (specialised) {

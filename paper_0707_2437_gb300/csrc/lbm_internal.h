@@ -7,6 +7,7 @@
 
 #include <string>
 
+#include "../../include/lbm.h"
 #include "lbm_device.cuh"
 
 namespace vss {
@@ -22,6 +23,10 @@ struct TileCfg {
                      // when vec is 16 bytes of elements); 1: register walk with
                      // one row of loads prefetched (used when vec is 8 bytes of
                      // elements); 0: register walk
+    // The default configuration: the register walks may change the tile
+    // height at launch to fit the grid's tiles to the resident warps
+    // (lbm_set_config and the tuner fix it).
+    bool fit_rows = true;
 };
 
 // Sites per lane of the bulk-copy pipeline (16 bytes of elements).
@@ -129,7 +134,7 @@ struct lbm_grid {
     int graph_pairs = 0;
     // Long step calls run as one persistent launch through a batch holding
     // only this grid (created on first use, dropped when the tiling changes).
-    bool persistent = true;
+    int persistent = LBM_PERSISTENT_AUTO;
     struct lbm_batch *self_batch = nullptr;
     // timing
     bool timing = false;

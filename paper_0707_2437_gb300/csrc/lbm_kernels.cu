@@ -2,6 +2,9 @@
 // and the FP64 reductions (grid totals and Fourier coefficients).
 #include <math.h>
 
+#include <mutex>
+#include <vector>
+
 #include "lbm_internal.h"
 
 namespace vss {
@@ -141,52 +144,117 @@ __global__ void __launch_bounds__(256, 2)
     w.run(y0, y1, (seg & 1) ? -1 : 1, c, status);
 }
 
+// Resident warps of a step kernel with blocks of `warps` warps on the
+// current device, found once per kernel, block size and device.
+static long long resident_warps(const void *fn, int warps) {
+    struct Entry {
+        const void *fn;
+        int warps, dev;
+        long long w;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (const Entry &e : cache)
+            if (e.fn == fn && e.warps == warps && e.dev == dev) return e.w;
+    }
+    int blocks = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, 32 * warps, 0) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    const long long w = (long long)blocks * warps * sms;
+    std::lock_guard<std::mutex> lk(mu);
+    cache.push_back(Entry{fn, warps, dev, w});
+    return w;
+}
+
+// Tile height of a register-walk launch in the default configuration.  Each
+// warp walks its tile's rows one after another, so a grid with fewer tiles
+// than resident warps leaves warps idle and its step takes a whole tile
+// walk however small the grid, and a grid whose tiles need between one and
+// two waves runs its second wave partly empty.  So, with the configured
+// height r0 (16):
+//   tiles at r0 >= 2 waves        -> r0;
+//   between one and two waves     -> the lowest height up to 2 r0 at which
+//                                    one wave holds every tile (else r0);
+//   at least 3/4 of one wave      -> r0;
+//   fewer                         -> the lowest height down to 2 at which the
+//                                    tiles still fit one wave (more, shorter
+//                                    tiles; the extra rows each pulls come
+//                                    mostly from L2).
+// Measured on 2048^2: the FP32 c2-field walk (2-site, 4096 tiles at 16 rows)
+// 63.2 -> 58.9 us per launch at 27 rows; 1024^2 FP32 and FP16-delta steps
+// took a whole 16-row walk (31 and 25 us per launch for 512 tiles).
+static TileCfg fit_tile(const TileCfg &cfg, const void *fn, int nx, int ny) {
+    if (!cfg.fit_rows) return cfg;
+    const long long wave = resident_warps(fn, cfg.warps);
+    if (wave <= 0) return cfg;
+    const long long nstrips = (nx + 32LL * cfg.vec - 1) / (32LL * cfg.vec);
+    auto tiles = [&](int r) { return nstrips * ((ny + r - 1) / r); };
+    const int r0 = cfg.rows;
+    TileCfg c = cfg;
+    const long long t0 = tiles(r0);
+    if (t0 >= 2 * wave || 4 * t0 >= 3 * wave && t0 <= wave) return c;
+    if (t0 > wave) {
+        for (int r = r0 + 1; r <= 2 * r0; ++r)
+            if (tiles(r) <= wave) {
+                c.rows = r;
+                return c;
+            }
+        return c;
+    }
+    int r = r0;
+    while (r > 2 && tiles(r - 1) <= wave) --r;
+    c.rows = r;
+    return c;
+}
+
 template <int S, int V, int RND>
 static Err launch_step_t(const TileCfg &cfg, const void *fin, void *fout, int nx, int ny, size_t P,
                          const Coef &c, const uint32_t *tdev, uint32_t toff, const float *a15f,
                          cudaStream_t st) {
-    StepGeom g = step_geom(nx, ny, cfg);
-    long long blocks = (g.ntiles + cfg.warps - 1) / cfg.warps;
-    const unsigned nb = (unsigned)blocks, nt = 32u * cfg.warps;
+    // Launches `kernel` over the grid's tiles at the fitted tile height.
+    auto go = [&](auto kernel, auto... extra) -> Err {
+        const TileCfg t = fit_tile(cfg, (const void *)kernel, nx, ny);
+        const StepGeom g = step_geom(nx, ny, t);
+        const unsigned nb = (unsigned)((g.ntiles + t.warps - 1) / t.warps);
+        return launch_pdl(kernel, nb, 32u * t.warps, 0, st, fin, fout, nx, ny, P, g.nstrips,
+                          g.ntiles, t.rows, c, extra...);
+    };
     if (a15f) {
         // Spatially varying alpha: the register walks (prefetching at 64-bit
         // vectors for 16-bit storage), nearest rounding.
         if constexpr (RND == 0 && V <= 4) {
             if (uses_prefetch(S, cfg)) {
                 if constexpr (Pack<S, V>::BYTES == 8)
-                    return launch_pdl(k_step<S, V, true, 0, 1>, nb, nt, 0, st, fin, fout, nx, ny,
-                                      P, g.nstrips, g.ntiles, cfg.rows, c, tdev, toff, a15f);
+                    return go(k_step<S, V, true, 0, 1>, tdev, toff, a15f);
                 else
                     return cudaErrorInvalidValue;
             } else if constexpr (S == ST_F32 && V == 4) {
                 return cudaErrorInvalidValue;  // launch_step_s runs the 2-site walk instead
             } else {
-                return launch_pdl(k_step<S, V, false, 0, 1>, nb, nt, 0, st, fin, fout, nx, ny, P,
-                                  g.nstrips, g.ntiles, cfg.rows, c, tdev, toff, a15f);
+                return go(k_step<S, V, false, 0, 1>, tdev, toff, a15f);
             }
-            return cudaGetLastError();
         } else {
             return cudaErrorInvalidValue;
         }
     }
     if (uses_prefetch(S, cfg) && V == 8) {
         if constexpr (S != ST_F32 && V == 8 && RND == 0)
-            return launch_pdl(k_step_wide<S>, nb, nt, 0, st, fin, fout, nx, ny, P, g.nstrips,
-                              g.ntiles, cfg.rows, c);
+            return go(k_step_wide<S>);
         else
             return cudaErrorInvalidValue;
     } else if (uses_prefetch(S, cfg)) {
         if constexpr (Pack<S, V>::BYTES == 8)
-            return launch_pdl(k_step<S, V, true, RND>, nb, nt, 0, st, fin, fout, nx, ny, P,
-                              g.nstrips, g.ntiles, cfg.rows, c, tdev, toff,
-                              (const float *)nullptr);
+            return go(k_step<S, V, true, RND>, tdev, toff, (const float *)nullptr);
         else
             return cudaErrorInvalidValue;
     } else {
-        return launch_pdl(k_step<S, V, false, RND>, nb, nt, 0, st, fin, fout, nx, ny, P,
-                          g.nstrips, g.ntiles, cfg.rows, c, tdev, toff, (const float *)nullptr);
+        return go(k_step<S, V, false, RND>, tdev, toff, (const float *)nullptr);
     }
-    return cudaGetLastError();
 }
 
 template <int S, int NST>
@@ -235,37 +303,6 @@ Err prepare_step(int storage, const TileCfg &cfg) {
     }
 }
 
-// Tile height of the FP32 c2-field walk.  That walk is the 2-site one, so it
-// has twice the tiles of the 4-site configuration it replaces.  When the tiles
-// at the configured height need more than one wave of the resident warps but
-// at most two, the last wave runs partly empty.  The height is then raised, by
-// at most 2x, to the lowest height at which one wave holds every tile.  On
-// 2048^2 this takes 16 rows to 27: 2432 tiles on 2432 warps, 58.5 us per
-// launch against 63.2 (measured).
-static int field_rows_f32(const TileCfg &cfg, int nx, int ny) {
-    // Resident warps per device and block size (1..8 warps), found once.
-    static int resident[64][9] = {};
-    int dev = 0;
-    if (cfg.warps < 1 || cfg.warps > 8) return cfg.rows;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cfg.rows;
-    if (!resident[dev][cfg.warps]) {
-        int blocks = 0, sms = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_step<ST_F32, 2, true, 0, 1>,
-                                                          32 * cfg.warps, 0) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            return cfg.rows;
-        resident[dev][cfg.warps] = blocks * cfg.warps * sms;
-    }
-    const long long wave = resident[dev][cfg.warps];
-    if (wave <= 0) return cfg.rows;
-    const long long nstrips = (nx + 63) / 64;
-    auto tiles = [&](int r) { return nstrips * ((ny + r - 1) / r); };
-    if (tiles(cfg.rows) <= wave || tiles(cfg.rows) > 2 * wave) return cfg.rows;
-    for (int r = cfg.rows + 1; r <= 2 * cfg.rows; ++r)
-        if (tiles(r) <= wave) return r;
-    return cfg.rows;
-}
-
 template <int S>
 static Err launch_step_s(const TileCfg &cfg, const void *fin, void *fout, int nx, int ny, size_t P,
                          const Coef &c, int *status, int rnd, const uint32_t *tdev,
@@ -278,7 +315,6 @@ static Err launch_step_s(const TileCfg &cfg, const void *fin, void *fout, int nx
         TileCfg c2 = cfg;
         c2.vec = 2;
         c2.stages = 1;
-        c2.rows = field_rows_f32(cfg, nx, ny);
         return launch_step_t<S, 2, 0>(c2, fin, fout, nx, ny, P, c, tdev, toff, a15f, st);
     }
     if (rnd) {
@@ -332,6 +368,7 @@ Err launch_step_forward(const TileCfg &cfg, const void *fin, void *fout, int nx,
     TileCfg c1 = cfg;
     c1.vec = 1;
     c1.stages = 0;
+    c1 = fit_tile(c1, (const void *)k_step<ST_F32, 1, false, 0, 0, 1>, nx, ny);
     StepGeom g = step_geom(nx, ny, c1);
     long long blocks = (g.ntiles + c1.warps - 1) / c1.warps;
     return launch_pdl(k_step<ST_F32, 1, false, 0, 0, 1>, (unsigned)blocks, 32u * c1.warps, 0, st,

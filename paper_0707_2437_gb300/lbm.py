@@ -343,8 +343,11 @@ class Grid:
         _check(self.lib.lbm_tune(self.h, cache_path.encode() if cache_path else None), "lbm_tune")
         return self.get_config() + (self.get_pipeline()[0],)
 
-    def set_persistent(self, on: bool):
-        _check(self.lib.lbm_set_persistent(self.h, 1 if on else 0), "lbm_set_persistent")
+    def set_persistent(self, on):
+        """True (long calls run one persistent launch), False (never), or
+        'auto' (the default: persistent for large 16-bit grids only)."""
+        mode = 2 if on == "auto" else (1 if on else 0)
+        _check(self.lib.lbm_set_persistent(self.h, mode), "lbm_set_persistent")
 
     def set_timing(self, on: bool):
         _check(self.lib.lbm_set_timing(self.h, 1 if on else 0), "lbm_set_timing")

@@ -404,6 +404,9 @@ def test_batch_barrier_timeout_reports_status(lbm):
     for g in grids:
         g.init(*workloads.sine_wave(1024, 1024))
     b = lbm.Batch(grids)
+    # 16-row tiles: 1024 of them, one walk of about 30 us each, so blocks
+    # without a tile wait at the barrier far longer than the limit.
+    b.set_config(16, 0)
     b.set_timeout_us(1)
     b.step(20)
     with pytest.raises(lbm.LbmError) as ei:
