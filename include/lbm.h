@@ -194,9 +194,9 @@ int lbm_set_drive(lbm_t h, int on, double amplitude, double period);
  * kernel uses at most 4 sites per lane, no bulk-copy pipeline and nearest
  * rounding (an FP32 grid configured for 4 sites per lane steps with 2 sites
  * per lane and one row of loads prefetched, its tile height raised to fill
- * one wave of resident warps where that helps); the grid can join a batch,
- * and long lbm_step calls still run one persistent launch, where 16-bit grids
- * with nx a multiple of 8 take the 8-site walk. */
+ * one wave of resident warps where that helps).  The grid can join a batch,
+ * where 16-bit grids with nx a multiple of 8 take the 8-site walk, and with
+ * LBM_PERSISTENT_ON long lbm_step calls run that batch kernel. */
 int lbm_set_c2_field(lbm_t h, const double *c2, int on_device);
 
 /* Steps taken since lbm_init / lbm_set_state. */
