@@ -121,12 +121,10 @@ int lbm_init(lbm_t h, const double *rho, const double *ux, const double *uy,
  * CUDA graphs from 8 steps on), or run all n steps as one persistent launch:
  * the batched kernel (see lbm_batch_create) with this grid alone, warps
  * taking tiles dynamically, a bounded grid barrier between steps.  Which one
- * is set by lbm_set_persistent; by default (LBM_PERSISTENT_AUTO) calls of 8
- * steps or more on 16-bit grids of at least 2^24 sites without a c2 field run
- * persistent, where its 8-site walk is the faster, and all other calls launch
- * the step kernel, the faster for every FP32 grid and for smaller 16-bit grids
- * (measured on 64^2 to 8192^2).  A slab always steps persistent; a driven grid or the
- * forward-difference gradient never.  All forms give bitwise the same result.
+ * is set by lbm_set_persistent; by default (LBM_PERSISTENT_AUTO) every call
+ * launches the step kernel, measured the faster for single grids of 64^2 to
+ * 8192^2 in every storage.  A slab always steps persistent; a driven grid or
+ * the forward-difference gradient never.  All forms give bitwise the same result.
  * Asynchronous: errors of the kernels surface at the next synchronising call
  * (LBM_ETIMEOUT if a bounded wait ran out). */
 int lbm_step(lbm_t h, long long n);
@@ -135,7 +133,8 @@ int lbm_step(lbm_t h, long long n);
  *   LBM_PERSISTENT_OFF   every call uses the step kernel
  *   LBM_PERSISTENT_ON    calls of 64 steps or more, or of 8 or more on grids
  *                        of at least 2^20 sites, run one persistent launch
- *   LBM_PERSISTENT_AUTO  the default: as described at lbm_step
+ *   LBM_PERSISTENT_AUTO  the default: as described at lbm_step (the step
+ *                        kernel, except for slabs)
  * LBM_EINVAL for other values. */
 #define LBM_PERSISTENT_OFF 0
 #define LBM_PERSISTENT_ON 1
@@ -241,8 +240,11 @@ int lbm_set_state(lbm_t h, const void *src_host, long long t);
  * columns down `rows` rows; blocks hold `warps` warps.  vec is the number of
  * adjacent sites per lane (vectorised loads of vec elements): 1, 2 or 4 for
  * any storage, 8 for the 16-bit storages; nx must be a multiple of vec.
- * rows in [1, 4096], warps in {1, 2, 4, 8}.  The result of a step does
- * not depend on the configuration (bitwise).  Until this is called (or
+ * rows in [1, 4096], warps in {1, 2, 4, 8}.  At vec 8 with 4 warps and no
+ * pipeline (lbm_set_pipeline 0) rows move through shared memory (cp.async),
+ * as in the batch kernels; the default for 16-bit grids with nx a multiple of
+ * 8 and enough tiles.  The result of a step does not depend on the
+ * configuration (bitwise).  Until this is called (or
  * lbm_tune), a grid has the default configuration (rows 16), whose register
  * walks adapt the tile height at launch to the resident warps: fewer rows
  * (down to 2) when the grid has too few tiles to occupy them, more (up to
@@ -269,8 +271,10 @@ int lbm_get_pipeline(lbm_t h, int *stages, int *active);
  * fraction (as many random bits as dropped bits: 13 for FP16, 16 for BF16),
  * so each stored value is the FP32 result in expectation; the random bits are
  * a hash of (pair of sites, direction, step), so runs stay deterministic and
- * independent of the tile configuration and of batching.  Stochastic rounding uses the register walks (vec 1, 2 or 4; it
- * moves a vec of 8 to 4 and turns the bulk-copy pipeline off).  FP32 storage
+ * independent of the tile configuration and of batching.  Stochastic rounding
+ * uses the register walks (vec 1, 2 or 4) and the shared-memory walk at vec 8
+ * with 4 warps; it moves other vec-8 configurations to 4 and turns the
+ * bulk-copy pipeline off.  FP32 storage
  * accepts only LBM_ROUND_NEAREST.  Because the dither differs from site to
  * site, it breaks symmetries a deterministic rounding keeps exactly: above c2
  * of about 1.16 (c_e > 1.08) a grid started uniform in y has transverse modes

@@ -71,12 +71,15 @@ extern "C" const char *lbm_last_error(void) { return g_last_error.c_str(); }
 
 static size_t state_bytes(const lbm_grid *h) { return 9 * h->P * (size_t)elem_bytes(h->storage); }
 
-// Defaults from the measured sweep on 2048^2 (profiles/): FP32 runs fastest as
-// the plain register walk with 128-bit vectors; the 16-bit kinds as the
-// prefetching register walk with 64-bit vectors.  Narrower vectors serve grids
-// whose nx they do not divide.
-static TileCfg default_cfg(int storage, int nx, int ny) {
-    (void)ny;
+// Defaults from measured steps: FP32 runs fastest as the plain register walk
+// with 128-bit vectors; the 16-bit kinds as the 8-site walk with rows through
+// shared memory when nx is a multiple of 8 and its 16-row tiles fill at least
+// a quarter of the resident warps (16 per SM), else as the prefetching
+// register walk with 64-bit vectors (per step, 256-step calls: 2048^2 FP16-delta
+// 25.4 us against 29.8, 8192^2 372.7 against 405.7; 1024^2 10.1 against 8.8,
+// its 8-site tiles fitting only at 2 rows).  Narrower vectors serve grids whose
+// nx they do not divide.
+static TileCfg default_cfg(int storage, int nx, int ny, int sms) {
     TileCfg c;
     c.rows = 16;
     c.warps = 4;
@@ -88,6 +91,9 @@ static TileCfg default_cfg(int storage, int nx, int ny) {
                 c.vec = v;
                 break;
             }
+    } else if (valid_vec(storage, nx, 8) &&
+               4LL * ((nx + 255) / 256) * ((ny + 15) / 16) >= 16LL * sms) {
+        c.vec = 8;  // k_step_async
     } else if (valid_vec(storage, nx, prefetch_vec(storage))) {
         c.vec = prefetch_vec(storage);
         c.stages = 1;
@@ -256,8 +262,10 @@ extern "C" int lbm_create_ex(int nx, int ny, double tau, double c2, double rho0,
     h->P = plane_elems(nx, ny);
     h->stream = (cudaStream_t)cuda_stream;
     h->coef = make_coef(tau, c2, rho0);
-    h->cfg = default_cfg(storage, nx, ny);
     cudaError_t e = cudaGetDevice(&h->device);
+    int sms = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    h->cfg = default_cfg(storage, nx, ny, sms > 0 ? sms : 1);
     size_t bytes = state_bytes(h);
     if (e == cudaSuccess) e = cudaMalloc(&h->buf[0], bytes);
     if (e == cudaSuccess) e = cudaMalloc(&h->buf[1], bytes);
@@ -394,14 +402,12 @@ static const long long kPersistentMin = 64;  // persistent launch from this many
 static const long long kPersistentMinLarge = 8;
 static const long long kLargeSites = 1LL << 20;
 static const long long kGraphMin = 8; // use graphs from this many steps on
-// LBM_PERSISTENT_AUTO: 16-bit grids of at least this many sites step
-// persistent (measured per step, 256-step calls: 4096^2 FP16-delta 108.6 us
-// persistent against 111.8 us for the step kernel, 8192^2 385.2 against 405.7;
-// at 2048^2 30.8 against 29.8, and FP32 grids from 64^2 to 8192^2 ran faster
-// on the step kernel: 2048^2 49.6 against 52.2 us, 64^2 3.5 against 6.1 us).
-// With a c2 field the 16-bit step kernel was the faster at 4096^2 too (125.7
-// against 131.2 us).
-static const long long kAutoSites16 = 1LL << 24;
+// LBM_PERSISTENT_AUTO steps every grid with the step kernel (except slabs):
+// per step over 256- and 1024-step calls it was the faster for FP32 grids from
+// 64^2 to 8192^2 (2048^2 49.6 us against 52.2 persistent, 64^2 3.5 against
+// 6.1), for 16-bit grids with its 8-site walk (2048^2 FP16-delta 25.4 against
+// 30.8, 8192^2 372.7 against 384.8) and with a c2 field (4096^2 FP16-delta
+// 125.7 against 131.2).
 
 static int build_graphs(lbm_grid *h) {
     drop_graphs(h);
@@ -468,9 +474,6 @@ extern "C" int lbm_step(lbm_t h, long long n) {
     bool persistent = false;
     if (h->persistent == LBM_PERSISTENT_ON)
         persistent = n >= kPersistentMin || (sites >= kLargeSites && n >= kPersistentMinLarge);
-    else if (h->persistent == LBM_PERSISTENT_AUTO)
-        persistent = h->storage != ST_F32 && !h->a15f && sites >= kAutoSites16 &&
-                     n >= kPersistentMinLarge;
     if (h->slab || (persistent && !h->drive && h->grad == LBM_GRAD_CENTRAL)) {
         // Slabs always step here: the batch's tile list covers only their
         // own rows.
@@ -657,8 +660,9 @@ extern "C" int lbm_set_config(lbm_t h, int vec, int rows, int warps) {
     if (!valid_vec(h->storage, h->nx, vec))
         return fail(LBM_EINVAL, "lbm_set_config: vec must be 1, 2, 4 (or 8 for 16-bit) and divide nx");
     if (rows < 1 || rows > 4096) return fail(LBM_EINVAL, "lbm_set_config: rows in [1, 4096]");
-    if ((h->rounding || h->a15f) && vec == 8)
-        return fail(LBM_EINVAL, "lbm_set_config: stochastic rounding and c2 fields use vec <= 4");
+    if (h->a15f && vec == 8) return fail(LBM_EINVAL, "lbm_set_config: c2 fields use vec <= 4");
+    if (h->rounding && vec == 8 && warps != 4)
+        return fail(LBM_EINVAL, "lbm_set_config: stochastic rounding at vec 8 needs 4 warps");
     if (warps != 1 && warps != 2 && warps != 4 && warps != 8)
         return fail(LBM_EINVAL, "lbm_set_config: warps in {1, 2, 4, 8}");
     if (h->cfg.vec != vec || h->cfg.rows != rows || h->cfg.warps != warps) {
@@ -708,7 +712,10 @@ extern "C" int lbm_set_c2_field(lbm_t h, const double *c2, int on_device) {
             if (!(c2[s] > 0.0) || !isfinite(c2[s]))
                 return fail(LBM_EINVAL, "lbm_set_c2_field: need c2 > 0 at every site");
     }
-    if (h->cfg.vec == 8) h->cfg.vec = 4;   // the field walks use vec <= 4
+    if (h->cfg.vec == 8) {  // the field walks use vec <= 4: 4 with a row prefetched
+        h->cfg.vec = 4;
+        h->cfg.stages = 1;
+    }
     if (h->cfg.stages >= 2) h->cfg.stages = 0;
     if (!h->a15f) CK(cudaMalloc(&h->a15f, n * sizeof(float)));
     std::vector<double *> owned;
@@ -756,8 +763,13 @@ extern "C" int lbm_set_rounding(lbm_t h, int mode) {
     drop_self_batch(h);
     h->rounding = mode;
     if (mode == LBM_ROUND_STOCHASTIC) {
-        // The stochastic-rounding walks are the register walks with vec <= 4.
-        if (h->cfg.vec == 8) h->cfg.vec = 4;
+        // Stochastic rounding runs on the register walks with vec <= 4 and on
+        // the shared-memory row walk at vec 8 with 4 warps per block; other
+        // vec-8 configurations move to 4 sites with a row prefetched.
+        if (h->cfg.vec == 8 && h->cfg.warps != 4) {
+            h->cfg.vec = 4;
+            h->cfg.stages = 1;
+        }
         if (h->cfg.stages >= 2) h->cfg.stages = 0;
     }
     CK(prepare_step(h->storage, h->cfg));

@@ -118,6 +118,30 @@ __global__ void __launch_bounds__(256, 1)
     w.run_prefetch(y0, y1, (seg & 1) ? -1 : 1, c);
 }
 
+// The 8-site 16-bit walk of the batch kernels in the step kernel: rows move
+// through shared memory with cp.async (a landing slot and a stash per warp,
+// 36.9 KB per block of 4 warps), one row in flight while the warp computes.
+// The default for 16-bit grids whose nx is a multiple of 8 and that have
+// enough tiles (see default_cfg), with either rounding.
+template <int S, int RND>
+__global__ void __launch_bounds__(128, 4)
+    k_step_async(const void *__restrict__ fin, void *__restrict__ fout, int nx, int ny, size_t P,
+                 int nstrips, long long ntiles, int rows, Coef c, const uint32_t *tdev,
+                 uint32_t toff) {
+    __shared__ uint4 rowbuf[4][2 * 9 * 32];
+    pdl_enter();
+    long long tile = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (tile >= ntiles) return;
+    int strip = (int)(tile % nstrips);
+    int seg = (int)(tile / nstrips);
+    int x0 = strip * 32 * 8;
+    int y0 = seg * rows;
+    int y1 = min(ny, y0 + rows);
+    Walker<S, 8, LD_NC, RND> w(fin, fout, nx, ny, P, x0);
+    if constexpr (RND) w.set_step((tdev ? *tdev : 0u) + toff);
+    w.run_async(y0, y1, (seg & 1) ? -1 : 1, c, &rowbuf[threadIdx.x >> 5][0]);
+}
+
 // Bulk-copy pipeline variant: one warp per tile, NST shared-memory stages per
 // warp (dynamic shared memory: barriers first, then the stages).
 constexpr unsigned long long kWaitLimitNs = 1000000000ULL;  // 1 s per wait
@@ -242,7 +266,14 @@ static Err launch_step_t(const TileCfg &cfg, const void *fin, void *fout, int nx
             return cudaErrorInvalidValue;
         }
     }
-    if (uses_prefetch(S, cfg) && V == 8) {
+    if (V == 8 && cfg.warps == 4 && (RND || !uses_prefetch(S, cfg))) {
+        // The shared-memory row walk (stochastic rounding: also in place of
+        // the register prefetch, which has no rounding variant at 8 sites).
+        if constexpr (S != ST_F32 && V == 8)
+            return go(k_step_async<S, RND>, tdev, toff);
+        else
+            return cudaErrorInvalidValue;
+    } else if (uses_prefetch(S, cfg) && V == 8) {
         if constexpr (S != ST_F32 && V == 8 && RND == 0)
             return go(k_step_wide<S>);
         else
@@ -318,11 +349,14 @@ static Err launch_step_s(const TileCfg &cfg, const void *fin, void *fout, int nx
         return launch_step_t<S, 2, 0>(c2, fin, fout, nx, ny, P, c, tdev, toff, a15f, st);
     }
     if (rnd) {
-        // Stochastic rounding: register walks with vec 1, 2 or 4.
+        // Stochastic rounding: register walks with vec 1, 2 or 4, and the
+        // shared-memory row walk at vec 8 (4 warps per block).
         if constexpr (S == ST_F32) {
             return cudaErrorInvalidValue;
         } else {
             switch (cfg.vec) {
+                case 8:
+                    return launch_step_t<S, 8, 1>(cfg, fin, fout, nx, ny, P, c, tdev, toff, nullptr, st);
                 case 1:
                     return launch_step_t<S, 1, 1>(cfg, fin, fout, nx, ny, P, c, tdev, toff, nullptr, st);
                 case 2:

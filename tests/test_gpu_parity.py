@@ -182,14 +182,44 @@ def test_rounding_mode_validation(lbm):
         with pytest.raises(lbm.LbmError):
             g.set_rounding("stochastic")
     with lbm.Grid(64, 8, 0.8, 0.2, "f16d") as g:
-        g.set_config(8, 16, 4)
+        g.set_config(8, 16, 8)  # 8 warps: no shared-memory walk at this block size
         g.set_rounding("stochastic")
         assert g.get_config()[0] == 4
         assert g.get_rounding() == "stochastic"
         with pytest.raises(lbm.LbmError):
-            g.set_config(8, 16, 4)
+            g.set_config(8, 16, 8)
+        g.set_config(8, 16, 4)  # the shared-memory walk takes stochastic rounding
+        assert g.get_config()[0] == 8
         with pytest.raises(lbm.LbmError):
             g.set_pipeline(3)
+
+
+@pytest.mark.parametrize("storage", ["f16d", "bf16d"])
+@pytest.mark.parametrize("rounding", ["nearest", "stochastic"])
+def test_step_kernel_8_site_walk_equals_other_walks(lbm, storage, rounding):
+    """The step kernel's 8-site walk with rows through shared memory leaves the
+    state bit for bit equal to the 4-site register walk and to the batch
+    kernel, with either rounding."""
+    nx, ny = 256, 40
+    f = _fields(nx, ny, seed=11)
+    out = []
+    for cfg in ((8, 16, 4), (8, 5, 4), (4, 16, 4), None):
+        with lbm.Grid(nx, ny, 0.7, 0.25, storage) as g:
+            if rounding != "nearest":
+                g.set_rounding(rounding)
+            g.init(*f)
+            if cfg is None:
+                b = lbm.Batch([g])
+                b.step(30)
+                assert b.sync() == 0
+                b.close()
+            else:
+                g.set_config(*cfg)
+                g.set_persistent(False)
+                g.step(30)
+            out.append(g.get_state()[0])
+    for o in out[1:]:
+        assert np.array_equal(out[0], o)
 
 
 @pytest.mark.parametrize("storage,rounding", [("f32", "nearest"), ("f16d", "nearest"),
