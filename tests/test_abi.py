@@ -98,6 +98,9 @@ def test_every_handle_call_rejects_null_before_device_work():
         lambda: lib.lbm_set_timing(None, 1),
         lambda: lib.lbm_kernel_ms(None, ctypes.byref(d), ctypes.byref(ll)),
         lambda: lib.lbm_set_persistent(None, 1),
+        lambda: lib.lbm_set_persistent(None, 2),
+        lambda: lib.lbm_set_gradient(None, 1),
+        lambda: lib.lbm_get_gradient(None, ctypes.byref(i)),
     ]
     batch_calls = [
         lambda: lib.lbm_batch_step(None, 1, None),
