@@ -14,7 +14,8 @@
  *     alpha = 1/3 - c2, so the sound speed is set independently of tau.
  *   Section 3, Eq. 7: viscosity nu = (2 tau - 1)/6, independent of alpha.
  *   Section 4: grad(rho) by central differences, (rho(x+1) - rho(x-1))/2 along
- *     x and y (the stable choice).
+ *     x and y (the stable choice; lbm_set_gradient selects the forward
+ *     difference the paper found unstable, for reproducing that result).
  *
  * Grids are periodic in x and y.  Fields passed in or out are row-major
  * [ny][nx] arrays of double (x fastest): element (x, y) is at index y*nx + x.
